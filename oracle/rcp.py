@@ -1,0 +1,181 @@
+"""Randomized CP decomposition (rCP-ALS), stated step by step in FP64.
+
+Follows Algorithm 1 (randomized tensor compression, Section 3.1), Algorithm 2
+(CP-ALS on the compressed tensor and recovery, Section 3.2.1) and the fit of
+Section 3.3.  Readings where the paper is silent or inconsistent:
+
+* Omega_n is Gaussian (Section 3.1 text), drawn from the counter-based
+  stream of ``oracle.philox`` (stream = mode n, purpose = sketch).
+* Every normalisation inside the power iterations (Algorithm 1 steps 8-9,
+  which the paper does with pivoted LU, and which Section 3.1 calls
+  re-orthonormalisation) and the final QR (step 12) use ``qr_pos``, the unique
+  thin QR whose R has a positive diagonal.  All of these differ from LU only by
+  a right factor, so the span of the final Q_n is the same in exact arithmetic.
+* The number of columns is l_n = min(k + p, I_n, J_n), so Y_n always has full
+  column rank for generic data.
+* The sketch of mode n is taken of the current compressed tensor
+  (Algorithm 1, "X <- B_n" after each mode).
+* ALS starts from seeded N(0,1) factors (stream = mode n, purpose = ALS init,
+  row-major l_n x R) for modes 2..N; mode 1 is computed first and needs none.
+* ``norm`` in Algorithm 2 is the column 2-norm, applied every sweep; lambda is
+  the column norms of the last mode.  A zero column stays zero, lambda_r = 0.
+* The fit is the paper's literal formula (Section 3.3), evaluated on the
+  compressed tensor that ALS sees:
+      rho = 1 - (|B|^2 + |Bhat|^2 - 2 <Bhat, B>) / |B|^2
+  and ALS stops after the first sweep j with |rho_j - rho_{j-1}| < tol
+  (rho_0 = 0) or when j reaches max_iters.
+* Recovery (Algorithm 2 steps 12-13): A_n = Q_n Atilde_n, re-normalised
+  columns, lambda_r multiplied by the product of the removed norms.
+"""
+
+import numpy as np
+
+from . import philox
+from .tensor import unfold, ttm, kr_except, kruskal, fro2
+
+
+def qr_pos(Y):
+    """Thin QR with a positive diagonal of R (Householder via LAPACK, then sign fix)."""
+    Q, R = np.linalg.qr(np.asarray(Y, dtype=np.float64), mode="reduced")
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :], R * s[:, None]
+
+
+def sketch_width(R, p, dims_current, n):
+    """l_n = min(R + p, I_n, J_n) for the current tensor shape and 1-based mode n."""
+    I_n = dims_current[n - 1]
+    J_n = int(np.prod([d for m, d in enumerate(dims_current) if m != n - 1]))
+    return min(R + p, I_n, J_n)
+
+
+def range_finder(T, n, l, q, seed):
+    """Basis Q_n for mode n of the current tensor T (Algorithm 1 steps 4-12).
+
+    Y = T_(n) Omega; q times: Q = qr+(Y), Z = qr+(T_(n)^T Q), Y = T_(n) Z;
+    then Q_n = qr+(Y).
+    """
+    Tn = unfold(T, n)
+    J = Tn.shape[1]
+    Omega = philox.gaussian_matrix(seed, n, philox.PURPOSE_SKETCH, J, l)
+    Y = Tn @ Omega
+    for _ in range(q):
+        Q, _r = qr_pos(Y)
+        Z, _r = qr_pos(Tn.T @ Q)
+        Y = Tn @ Z
+    Qn, _r = qr_pos(Y)
+    return Qn
+
+
+def compress(X, R, p, q, seed):
+    """Algorithm 1: returns the compressed tensor B and the bases [Q_1, ..., Q_N]."""
+    T = np.asarray(X, dtype=np.float64)
+    Qs = []
+    for n in range(1, T.ndim + 1):
+        l = sketch_width(R, p, T.shape, n)
+        Qn = range_finder(T, n, l, q, seed)
+        Qs.append(Qn)
+        T = ttm(T, Qn.T, n)
+    return T, Qs
+
+
+def als_init(dims, R, seed):
+    """Seeded N(0,1) initial factors for modes 2..N (mode 1 entry is None)."""
+    out = [None]
+    for n in range(2, len(dims) + 1):
+        out.append(philox.gaussian_matrix(seed, n, philox.PURPOSE_ALS_INIT, dims[n - 1], R))
+    return out
+
+
+def _colnorm(A):
+    return np.sqrt(np.sum(A * A, axis=0))
+
+
+def _safe_div(A, nu):
+    d = np.where(nu > 0, nu, 1.0)
+    return np.where(nu[None, :] > 0, A / d[None, :], 0.0)
+
+
+def fit(B, lam, factors):
+    """Section 3.3: rho = 1 - (|B|^2 + |Bhat|^2 - 2<Bhat, B>) / |B|^2 with Bhat formed explicitly."""
+    Bhat = kruskal(lam, factors)
+    nB = fro2(B)
+    return 1.0 - (nB + fro2(Bhat) - 2.0 * float(np.vdot(Bhat, B))) / nB
+
+
+def cp_als(B, R, tol, max_iters, seed, init=None):
+    """Algorithm 2 steps 3-11 on the compressed tensor B.
+
+    Each sweep updates modes 1..N in order with
+        A_n = B_(n) (KR of the other factors) (Hadamard product of their Grams)^dagger
+    normalises columns (lambda from the last mode), then evaluates the fit.
+    Returns (lam, factors, rho, iterations, rho_history).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    N = B.ndim
+    A = list(init) if init is not None else als_init(B.shape, R, seed)
+    A = [None if F is None else np.array(F, dtype=np.float64) for F in A]
+    lam = np.ones(R)
+    rho_prev = 0.0
+    hist = []
+    it = 0
+    for it in range(1, max_iters + 1):
+        for n in range(1, N + 1):
+            V = np.ones((R, R))
+            for m in range(1, N + 1):
+                if m != n:
+                    V = V * (A[m - 1].T @ A[m - 1])
+            An = unfold(B, n) @ kr_except(A, n) @ np.linalg.pinv(V)
+            nu = _colnorm(An)
+            if n < N:
+                A[n - 1] = _safe_div(An, nu)
+            else:
+                lam = nu
+                A[n - 1] = _safe_div(An, nu)
+        rho = fit(B, lam, A)
+        hist.append(rho)
+        if abs(rho - rho_prev) < tol:
+            break
+        rho_prev = rho
+    return lam, A, rho, it, hist
+
+
+def back_project(Qs, lam, factors):
+    """Algorithm 2 steps 12-13: A_n = Q_n Atilde_n, then re-normalise and update lambda."""
+    lam = np.array(lam, dtype=np.float64)
+    out = []
+    for Qn, At in zip(Qs, factors):
+        An = Qn @ At
+        nu = _colnorm(An)
+        out.append(_safe_div(An, nu))
+        lam = lam * nu
+    return lam, out
+
+
+def rcp_als(X, R, p, q, tol, max_iters, seed, init=None):
+    """The whole method: compress, ALS on B, recover.  Returns a dict of every intermediate."""
+    X = np.asarray(X, dtype=np.float64)
+    B, Qs = compress(X, R, p, q, seed)
+    lam_t, At, rho, iters, hist = cp_als(B, R, tol, max_iters, seed, init=init)
+    lam, A = back_project(Qs, lam_t, At)
+    nX2 = fro2(X)
+    nB2 = fro2(B)
+    # |X - Xhat|^2 = |X|^2 - |B|^2 + |B - Bhat|^2 (Xhat lies in the span of the Q_n)
+    res2 = nX2 - nB2 + nB2 * (1.0 - rho)
+    return dict(B=B, Q=Qs, lam_tilde=lam_t, A_tilde=At, fit=rho, iters=iters,
+                fit_history=hist, lam=lam, A=A, normX2=nX2, normB2=nB2,
+                rel_err_identity=float(np.sqrt(max(res2, 0.0) / nX2)))
+
+
+def rel_error(X, lam, factors):
+    """Section 4: |X - Xhat|_F / |X|_F with Xhat formed explicitly."""
+    X = np.asarray(X, dtype=np.float64)
+    return float(np.sqrt(fro2(X - kruskal(lam, factors)) / fro2(X)))
+
+
+def projection_residual(X, Qs):
+    """|X - X x_1 Q_1 Q_1^T ... x_N Q_N Q_N^T|_F / |X|_F (Theorem 1's error, relative)."""
+    T = np.asarray(X, dtype=np.float64)
+    for n, Qn in enumerate(Qs, start=1):
+        T = ttm(T, Qn @ Qn.T, n)
+    return float(np.sqrt(fro2(X - T) / fro2(X)))

@@ -1,0 +1,20 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long-running CPU statistics")
+
+
+@pytest.fixture(scope="session")
+def rcp_lib():
+    """The CUDA path's C-ABI library, loaded through the Python binding."""
+    from paper_1703_09074_gb300 import _lib
+    return _lib.load()
