@@ -1,0 +1,230 @@
+/*
+ * rcp.h -- C ABI of the GB300 randomized CP decomposition library (librcp.so).
+ *
+ * The library computes the randomized CP decomposition of Erichson, Manohar,
+ * Brunton & Kutz ("Randomized CP Tensor Decomposition", arXiv 1703.09074):
+ *
+ *   1. rcp_sketch   -- Algorithm 1 steps (4)-(12): for mode n, the sketch
+ *                      Y = T_(n) Omega_n with a Gaussian test matrix of
+ *                      l_n = min(R + p, I_n, J_n) columns (Eq. sampleMatrix),
+ *                      q normalised power iterations (Eq. IMPsampleMatrix,
+ *                      Algorithm 1 steps 7-11) and the QR Y = Q_n R.
+ *   2. rcp_compress -- Algorithm 1 step (13): T_{n+1} = T_n x_n Q_n^T
+ *                      (the n-mode product of Definition 1).
+ *   3. rcp_als      -- Algorithm 2 steps (2)-(11): CP-ALS on the compressed
+ *                      tensor B with the Khatri-Rao pseudo-inverse
+ *                      (Definition 2), column normalisation, and the fit
+ *                      test of Section 3.3.
+ *   4. rcp_project  -- Algorithm 2 steps (12)-(13) / Eq. (qbs): A_n = Q_n Atilde_n,
+ *                      re-normalised, with lambda updated.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Modes are numbered 1..N as in the paper.
+ * - Tensors use the Kolda & Bader layout: element (i_1, ..., i_N) sits at
+ *   linear index i_1 + I_1 (i_2 + I_2 (i_3 + ...)) -- mode 1 fastest.  A
+ *   C-contiguous array of shape (I_N, ..., I_1) holds exactly these bytes.
+ * - Matrices (Q_n, A_n, Atilde_n) are FP64, column-major, leading dimension
+ *   equal to their row count.
+ * - Device pointers are CUDA device addresses on the device that was current
+ *   when the plan was created; host pointers are ordinary process memory.
+ * - The caller owns the input tensor and every output buffer; the plan owns
+ *   its workspace (allocated once in rcp_plan, freed in rcp_plan_destroy) and
+ *   borrows the CUDA stream given to rcp_plan.  Work is enqueued on that
+ *   stream and is asynchronous unless an entry point says it synchronises.
+ *   The input tensor must stay valid until the enqueued work completes.
+ * - Argument errors are returned synchronously and enqueue nothing.  Errors
+ *   detected on the device (non-finite values, a singular Gram matrix that
+ *   even the shifted fallback cannot factor, a bounded wait that ran out) are
+ *   recorded in a device status word and returned by the next synchronising
+ *   call (rcp_result, rcp_last_error, or an rcp_als call with host outputs).
+ * - A plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef RCP_H
+#define RCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rcp_plan_s* rcp_plan_t;
+
+typedef enum {
+  RCP_OK = 0,
+  RCP_EINVAL = 1,      /* invalid argument or configuration                       */
+  RCP_ENOMEM = 2,      /* device or pinned-host allocation failed                  */
+  RCP_ECUDA = 3,       /* a CUDA runtime call failed                               */
+  RCP_ESINGULAR = 4,   /* a Gram matrix could not be factored even with a shift    */
+  RCP_ENAN = 5,        /* a non-finite value reached a reduction                   */
+  RCP_ETIMEOUT = 6,    /* a bounded device-side wait ran out                       */
+  RCP_EORDER = 7,      /* entry points called out of the order of Algorithm 1      */
+  RCP_ENOTCONV = 8     /* informational: ALS stopped at max_iters                  */
+} rcp_status;
+
+typedef enum {
+  RCP_DTYPE_F64 = 0,
+  RCP_DTYPE_F32 = 1
+} rcp_dtype;
+
+typedef enum {
+  /* Every step in FP64 on the CUDA cores (the plain method). */
+  RCP_PREC_F64 = 0,
+  /* Tensor sweeps (sketch, power iterations, mode products) on the tensor
+   * cores with FP32 accumulation; QR of each sketch and the R x R Gram solves
+   * of ALS stay in FP64.  Working tensors T_2..T_N and B are FP32. */
+  RCP_PREC_MIXED = 1
+} rcp_precision;
+
+/* Informational bits returned in rcp_result.info. */
+enum {
+  RCP_INFO_SHIFTED_QR = 1,     /* a sketch or power-iteration Gram needed the shifted fallback */
+  RCP_INFO_ALS_REGULARISED = 2 /* an ALS Gram solve needed a diagonal shift                    */
+};
+
+/* Flags for rcp_config.flags. */
+enum {
+  RCP_FLAG_HOST_STAGING = 1    /* reserve device buffers so rcp_decompose_host can run */
+};
+
+#define RCP_MAX_NDIM 8
+#define RCP_MAX_L 64      /* largest sketch width l_n = R + p supported */
+#define RCP_MAX_RANK 64   /* largest target rank R supported            */
+
+typedef struct {
+  int32_t ndim;                  /* N, 2..RCP_MAX_NDIM                               */
+  int64_t dims[RCP_MAX_NDIM];    /* I_1..I_N (each >= 1)                             */
+  int32_t in_dtype;              /* rcp_dtype of the input tensor X                  */
+  int32_t rank;                  /* target rank R, 1..RCP_MAX_RANK                   */
+  int32_t oversample;            /* p >= 0; l_n = min(R + p, I_n, J_n) <= RCP_MAX_L   */
+  int32_t power_iters;           /* q >= 0                                           */
+  double tol;                    /* ALS stops when |rho_j - rho_{j-1}| < tol         */
+  int32_t max_iters;             /* ALS sweep cap, >= 1                              */
+  uint64_t seed;                 /* key of the counter-based random streams          */
+  int32_t precision;             /* rcp_precision                                    */
+  int32_t flags;                 /* RCP_FLAG_* bits                                  */
+} rcp_config;
+
+/* Results of one decomposition, filled by rcp_result / rcp_decompose_host. */
+typedef struct {
+  double fit;             /* rho of Section 3.3 on the compressed tensor, last sweep    */
+  int32_t iters;          /* ALS sweeps run                                             */
+  int32_t info;           /* RCP_INFO_* bits                                            */
+  double norm_x2;         /* |X|_F^2 (accumulated by the mode-1 sketch sweep)           */
+  double norm_b2;         /* |B|_F^2                                                    */
+  double rel_err;         /* |X - Xhat|_F / |X|_F = sqrt((|X|^2 - rho |B|^2) / |X|^2)   */
+  int32_t device_status;  /* rcp_status recorded on the device                          */
+  int32_t widths[RCP_MAX_NDIM]; /* l_1..l_N                                             */
+} rcp_result;
+
+/* Create a plan for one tensor shape and parameter set (Algorithm 2 "Require"
+ * and "Optional" lines: tensor, target rank R, oversampling p, power
+ * iterations q; plus the ALS tolerance and cap of Section 3.3).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates the whole workspace on the current device; returns RCP_EINVAL
+ * for an unsupported configuration and RCP_ENOMEM when allocation fails.
+ * *out is set only on success. */
+rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out);
+
+/* Free the plan's workspace.  Synchronises the plan's stream first.
+ * NULL is accepted and ignored. */
+rcp_status rcp_plan_destroy(rcp_plan_t plan);
+
+/* Sketch width l_n of 1-based mode n (Algorithm 1 step 3, capped as in
+ * rcp_config.oversample), or -1 for an invalid plan or mode. */
+int32_t rcp_width(rcp_plan_t plan, int32_t mode);
+
+/* Algorithm 1 steps (4)-(12) for 1-based mode n: sketch the current tensor
+ * T_n (X itself when n = 1), run q power iterations, orthonormalise, and keep
+ * Q_n (I_n x l_n) in the plan.
+ * X: device pointer to the input tensor (read when n = 1; ignored and may be
+ *    NULL otherwise).
+ * Q_out: optional device pointer receiving a copy of Q_n, I_n x l_n,
+ *    column-major FP64; NULL skips the copy.
+ * Order: n = 1 first, and n > 1 only after rcp_compress(n - 1); otherwise
+ * RCP_EORDER.  Asynchronous. */
+rcp_status rcp_sketch(rcp_plan_t plan, const void* X, int32_t mode, double* Q_out);
+
+/* Algorithm 1 step (13): T_{n+1} = T_n x_n Q_n^T for 1-based mode n, after
+ * rcp_sketch(n) (else RCP_EORDER).  X as in rcp_sketch.  After mode N the
+ * plan holds the compressed tensor B (l_1 x ... x l_N).  Asynchronous. */
+rcp_status rcp_compress(rcp_plan_t plan, const void* X, int32_t mode);
+
+/* Replace the seeded N(0,1) initial factors of ALS (used when this is never
+ * called) by caller-supplied ones.  At_dev[n-1] for n = 2..N: device pointer
+ * to an l_n x R column-major FP64 matrix (At_dev[0] is ignored and may be
+ * NULL).  The factors are copied on the stream; the pointers may be released
+ * once that copy completes.  Applies to the next rcp_als call only. */
+rcp_status rcp_als_init(rcp_plan_t plan, const double* const* At_dev);
+
+/* Algorithm 2 steps (3)-(11) on the compressed tensor B: ALS sweeps over
+ * modes 1..N, each solving A_n = B_(n) (KR of the others) (Hadamard product of
+ * their Grams)^-1 and normalising columns (lambda from mode N), until the fit
+ * change falls below tol or max_iters sweeps have run.
+ * Requires rcp_compress(N) (else RCP_EORDER).
+ * lambda_host (R doubles), fit_host, iters_host: optional host outputs; when
+ * any is non-NULL the call synchronises the stream and returns the device
+ * status (RCP_ENOTCONV when the cap was reached without meeting tol). */
+rcp_status rcp_als(rcp_plan_t plan, double* lambda_host, double* fit_host, int32_t* iters_host);
+
+/* Algorithm 2 steps (12)-(13): A_n = Q_n Atilde_n for every mode, columns
+ * re-normalised and lambda_r multiplied by the removed norms.
+ * A_dev: host array of N device pointers, A_dev[n-1] -> I_n x R column-major
+ * FP64 output.  lambda_dev: device pointer to R doubles (output).
+ * Requires rcp_als (else RCP_EORDER).  Asynchronous. */
+rcp_status rcp_project(rcp_plan_t plan, double* const* A_dev, double* lambda_dev);
+
+/* All of the above in order for modes 1..N (asynchronous).  Arguments as in
+ * rcp_sketch (X) and rcp_project (A_dev, lambda_dev). */
+rcp_status rcp_decompose(rcp_plan_t plan, const void* X, double* const* A_dev, double* lambda_dev);
+
+/* End-to-end call on host buffers: copies X_host (pinned or pageable host
+ * memory, Kolda layout, cfg.in_dtype) to the device, runs rcp_decompose,
+ * and copies the factors and lambda back.  A_host: host array of N host
+ * pointers (I_n x R column-major FP64 each); lambda_host: R doubles;
+ * res: optional result record.  Requires RCP_FLAG_HOST_STAGING in the plan's
+ * flags (else RCP_EINVAL).  Synchronises. */
+rcp_status rcp_decompose_host(rcp_plan_t plan, const void* X_host, double* const* A_host,
+                              double* lambda_host, rcp_result* res);
+
+/* Synchronise the plan's stream and fill *out (may be NULL to only check).
+ * Returns the device status. */
+rcp_status rcp_result_get(rcp_plan_t plan, rcp_result* out);
+
+/* Copy the compressed tensor B (FP64, Kolda layout, l_1 x ... x l_N) to the
+ * device buffer B_dev.  Requires rcp_compress(N).  Asynchronous. */
+rcp_status rcp_get_core(rcp_plan_t plan, double* B_dev);
+
+/* Copy the compressed-space factors Atilde_n (l_n x R column-major FP64, last
+ * ALS state) to At_dev[n-1] (device pointers) and lambda (R doubles) to
+ * lambda_dev (may be NULL).  Requires rcp_als.  Asynchronous. */
+rcp_status rcp_get_compressed_factors(rcp_plan_t plan, double* const* At_dev, double* lambda_dev);
+
+/* Synchronise and return the device status word (also stored in *device_status
+ * when non-NULL). */
+rcp_status rcp_last_error(rcp_plan_t plan, int32_t* device_status);
+
+/* Static description of a status code. */
+const char* rcp_status_str(rcp_status s);
+
+/* Test-matrix generator (Section 3.1: Gaussian entries for Omega_n), exposed
+ * so that its counter-based stream can be checked against an independent
+ * implementation.  Writes out_dev[k] for k < count: the element (first + k) of
+ * the FP64 normal stream (seed, stream, purpose) -- Philox4x32-10 counter
+ * (g mod 2^32, g div 2^32, stream, purpose), g = element div 2, key (seed lo,
+ * seed hi), Box-Muller on 53-bit uniforms.  words_dev (optional, 4 uint32 per
+ * counter for counters first/2 .. (first+count-1)/2) receives the raw Philox
+ * output.  f32_out_dev (optional): the reduced-precision stream (four normals
+ * per counter) evaluated on the device.  cuda_stream: cudaStream_t.
+ * Asynchronous. */
+rcp_status rcp_test_normals(uint64_t seed, uint32_t stream, uint32_t purpose, int64_t first,
+                            int64_t count, double* out_dev, uint32_t* words_dev,
+                            float* f32_out_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RCP_H */

@@ -1,0 +1,8 @@
+"""GB300-native randomized CP decomposition (Erichson, Manohar, Brunton & Kutz, arXiv 1703.09074).
+
+The method's steps run in hand-written sm_103a CUDA kernels behind the C ABI of
+``include/rcp.h`` (``librcp.so``); this package only marshals arguments.
+"""
+
+from .api import Plan, decompose, test_normals  # noqa: F401
+from ._lib import RcpError, load  # noqa: F401

@@ -1,0 +1,101 @@
+"""ctypes declarations of the C ABI in include/rcp.h (argument marshalling only).
+
+``load()`` opens ``librcp.so`` built next to this file and raises if it is
+missing: there is no CPU fallback for any entry point.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librcp.so")
+
+MAX_NDIM = 8
+
+RCP_OK, RCP_EINVAL, RCP_ENOMEM, RCP_ECUDA, RCP_ESINGULAR, RCP_ENAN, RCP_ETIMEOUT, \
+    RCP_EORDER, RCP_ENOTCONV = range(9)
+RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
+RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
+RCP_FLAG_HOST_STAGING = 1
+RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED = 1, 2
+
+
+class RcpConfig(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * MAX_NDIM),
+                ("in_dtype", ctypes.c_int32),
+                ("rank", ctypes.c_int32),
+                ("oversample", ctypes.c_int32),
+                ("power_iters", ctypes.c_int32),
+                ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32),
+                ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class RcpResult(ctypes.Structure):
+    _fields_ = [("fit", ctypes.c_double),
+                ("iters", ctypes.c_int32),
+                ("info", ctypes.c_int32),
+                ("norm_x2", ctypes.c_double),
+                ("norm_b2", ctypes.c_double),
+                ("rel_err", ctypes.c_double),
+                ("device_status", ctypes.c_int32),
+                ("widths", ctypes.c_int32 * MAX_NDIM)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/rcp.h
+P = ctypes.c_void_p
+DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "rcp_plan": (ctypes.c_int, [ctypes.POINTER(RcpConfig), P, ctypes.POINTER(P)]),
+    "rcp_plan_destroy": (ctypes.c_int, [P]),
+    "rcp_width": (ctypes.c_int32, [P, ctypes.c_int32]),
+    "rcp_sketch": (ctypes.c_int, [P, P, ctypes.c_int32, P]),
+    "rcp_compress": (ctypes.c_int, [P, P, ctypes.c_int32]),
+    "rcp_als_init": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+    "rcp_als": (ctypes.c_int, [P, DP, DP, ctypes.POINTER(ctypes.c_int32)]),
+    "rcp_project": (ctypes.c_int, [P, ctypes.POINTER(P), P]),
+    "rcp_decompose": (ctypes.c_int, [P, P, ctypes.POINTER(P), P]),
+    "rcp_decompose_host": (ctypes.c_int, [P, P, ctypes.POINTER(P), DP, ctypes.POINTER(RcpResult)]),
+    "rcp_result_get": (ctypes.c_int, [P, ctypes.POINTER(RcpResult)]),
+    "rcp_get_core": (ctypes.c_int, [P, P]),
+    "rcp_get_compressed_factors": (ctypes.c_int, [P, ctypes.POINTER(P), P]),
+    "rcp_last_error": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+    "rcp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "rcp_test_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_int64, ctypes.c_int64, P, P, P, P]),
+}
+
+_LIB = None
+
+
+class RcpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _LIB.rcp_status_str(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+def load():
+    """Open librcp.so (built by ``paper_1703_09074_gb300.build``); no fallback."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librcp.so not found at {LIB_PATH}: build it with "
+                           "`python -m paper_1703_09074_gb300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def check(code, where, ok=(RCP_OK,)):
+    if code not in ok:
+        raise RcpError(code, where)
+    return code

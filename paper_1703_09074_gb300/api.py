@@ -1,0 +1,206 @@
+"""Python API over the C ABI: torch tensors in, torch tensors out.
+
+PyTorch provides device memory and the CUDA stream; every step of the method
+runs in the CUDA kernels of librcp.so.  Tensors are passed in the Kolda layout
+of the paper's Tensor-Toolbox convention: a C-contiguous torch tensor of shape
+(I_N, ..., I_1) holds X[i_1, ..., i_N] at i_1 + I_1 (i_2 + ...).
+"""
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import RcpConfig, RcpResult, check
+
+_DT = {torch.float32: _lib.RCP_DTYPE_F32, torch.float64: _lib.RCP_DTYPE_F64}
+_PREC = {"f64": _lib.RCP_PREC_F64, "mixed": _lib.RCP_PREC_MIXED}
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for k, t in enumerate(tensors):
+        arr[k] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Plan:
+    """One randomized-CP problem shape (Algorithm 2's inputs) bound to a CUDA stream."""
+
+    def __init__(self, dims, rank, oversample=10, power_iters=2, tol=1e-10, max_iters=50,
+                 seed=0, in_dtype=torch.float32, precision="f64", host_staging=False,
+                 stream=None):
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = len(self.dims)
+        self.R = int(rank)
+        self.in_dtype = in_dtype
+        cfg = RcpConfig()
+        cfg.ndim = self.N
+        for k, d in enumerate(self.dims):
+            cfg.dims[k] = d
+        cfg.in_dtype = _DT[in_dtype]
+        cfg.rank = self.R
+        cfg.oversample = int(oversample)
+        cfg.power_iters = int(power_iters)
+        cfg.tol = float(tol)
+        cfg.max_iters = int(max_iters)
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.precision = _PREC[precision]
+        cfg.flags = _lib.RCP_FLAG_HOST_STAGING if host_staging else 0
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.rcp_plan(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h)), "rcp_plan")
+        self.h = h
+        self.widths = [self.lib.rcp_width(self.h, n) for n in range(1, self.N + 1)]
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rcp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers
+    def _check_x(self, X):
+        if X is None:
+            return None
+        if not (X.is_cuda and X.dtype == self.in_dtype and X.is_contiguous()):
+            raise ValueError("X must be a contiguous CUDA tensor of the plan's dtype")
+        if tuple(reversed(X.shape)) != self.dims:
+            raise ValueError(f"X must have shape {tuple(reversed(self.dims))} (Kolda layout)")
+        return ctypes.c_void_p(X.data_ptr())
+
+    def _f64(self, *shape):
+        return torch.empty(shape, dtype=torch.float64, device=self.device)
+
+    # -- Algorithm 1
+    def sketch(self, X, mode, return_basis=False):
+        """Range finder of mode n (1-based); returns Q_n (I_n x l_n) when asked."""
+        Q = None
+        if return_basis:
+            Q = self._f64(self.widths[mode - 1], self.dims[mode - 1])  # column-major I_n x l_n
+        check(self.lib.rcp_sketch(self.h, self._check_x(X), mode,
+                                  None if Q is None else ctypes.c_void_p(Q.data_ptr())),
+              f"rcp_sketch({mode})")
+        return None if Q is None else Q.t()
+
+    def compress(self, X, mode):
+        check(self.lib.rcp_compress(self.h, self._check_x(X), mode), f"rcp_compress({mode})")
+
+    # -- Algorithm 2
+    def als_init(self, factors):
+        """Initial compressed factors for modes 2..N (each l_n x R); factors[0] is ignored."""
+        mats = [None] + [f.to(torch.float64).t().contiguous() for f in factors[1:]]  # column-major
+        self._init_keep = mats
+        check(self.lib.rcp_als_init(self.h, _ptr_array(mats)), "rcp_als_init")
+
+    def als(self, sync=True):
+        if not sync:
+            check(self.lib.rcp_als(self.h, None, None, None), "rcp_als")
+            return None
+        lam = (ctypes.c_double * self.R)()
+        fit = ctypes.c_double()
+        it = ctypes.c_int32()
+        check(self.lib.rcp_als(self.h, lam, ctypes.byref(fit), ctypes.byref(it)), "rcp_als",
+              ok=(_lib.RCP_OK, _lib.RCP_ENOTCONV))
+        return torch.tensor(list(lam), dtype=torch.float64), fit.value, it.value
+
+    def project(self):
+        A = [self._f64(self.R, I) for I in self.dims]   # column-major I_n x R storage
+        lam = self._f64(self.R)
+        check(self.lib.rcp_project(self.h, _ptr_array(A), ctypes.c_void_p(lam.data_ptr())),
+              "rcp_project")
+        return [a.t() for a in A], lam
+
+    def decompose(self, X):
+        """Whole method, asynchronous on the plan's stream; returns (factors, lambda) on the device."""
+        A = [self._f64(self.R, I) for I in self.dims]
+        lam = self._f64(self.R)
+        check(self.lib.rcp_decompose(self.h, self._check_x(X), _ptr_array(A),
+                                     ctypes.c_void_p(lam.data_ptr())), "rcp_decompose")
+        return [a.t() for a in A], lam
+
+    def decompose_host(self, X_host, A_host=None, lam_host=None):
+        """End to end on host buffers (copies inside the call); needs host_staging=True."""
+        if A_host is None:
+            A_host = [torch.empty((self.R, I), dtype=torch.float64, pin_memory=True)
+                      for I in self.dims]
+        if lam_host is None:
+            lam_host = torch.empty(self.R, dtype=torch.float64, pin_memory=True)
+        res = RcpResult()
+        code = self.lib.rcp_decompose_host(
+            self.h, ctypes.c_void_p(X_host.data_ptr()), _ptr_array(A_host),
+            ctypes.cast(lam_host.data_ptr(), _lib.DP), ctypes.byref(res))
+        check(code, "rcp_decompose_host")
+        return [a.t() for a in A_host], lam_host, _result_dict(res, self.N)
+
+    def result(self):
+        res = RcpResult()
+        code = self.lib.rcp_result_get(self.h, ctypes.byref(res))
+        check(code, "rcp_result_get")
+        return _result_dict(res, self.N)
+
+    def core(self):
+        """The compressed tensor B, FP64, Kolda layout (shape (l_N, ..., l_1))."""
+        B = self._f64(*reversed(self.widths))
+        check(self.lib.rcp_get_core(self.h, ctypes.c_void_p(B.data_ptr())), "rcp_get_core")
+        return B
+
+    def compressed_factors(self):
+        At = [self._f64(self.R, l) for l in self.widths]
+        lam = self._f64(self.R)
+        check(self.lib.rcp_get_compressed_factors(self.h, _ptr_array(At),
+                                                  ctypes.c_void_p(lam.data_ptr())),
+              "rcp_get_compressed_factors")
+        return [a.t() for a in At], lam
+
+    def last_error(self):
+        st = ctypes.c_int32()
+        self.lib.rcp_last_error(self.h, ctypes.byref(st))
+        return st.value
+
+
+def _result_dict(res, N):
+    return dict(fit=res.fit, iters=res.iters, info=res.info, norm_x2=res.norm_x2,
+                norm_b2=res.norm_b2, rel_err=res.rel_err, device_status=res.device_status,
+                widths=[res.widths[k] for k in range(N)])
+
+
+def decompose(X, rank, oversample=10, power_iters=2, tol=1e-10, max_iters=50, seed=0,
+              precision="f64"):
+    """Randomized CP decomposition of a Kolda-layout CUDA tensor; returns a dict."""
+    dims = tuple(reversed(X.shape))
+    with Plan(dims, rank, oversample, power_iters, tol, max_iters, seed, X.dtype, precision) as p:
+        A, lam = p.decompose(X)
+        out = p.result()
+    out.update(A=A, lam=lam)
+    return out
+
+
+def test_normals(seed, stream, purpose, first, count, device="cuda"):
+    """The device's Gaussian test-matrix stream: (fp64 normals, Philox words, fp32-stream normals)."""
+    lib = _lib.load()
+    z = torch.empty(count, dtype=torch.float64, device=device)
+    w = torch.empty(4 * count, dtype=torch.int32, device=device)
+    f = torch.empty(count, dtype=torch.float32, device=device)
+    s = torch.cuda.current_stream(device)
+    check(lib.rcp_test_normals(seed, stream, purpose, first, count, ctypes.c_void_p(z.data_ptr()),
+                               ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                               ctypes.c_void_p(s.cuda_stream)), "rcp_test_normals")
+    return z, w, f

@@ -1,0 +1,462 @@
+// Host side of the C ABI declared in include/rcp.h: plan creation and workspace
+// sizing, the order of Algorithm 1 and Algorithm 2, and the launch sequences.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "rcp_internal.cuh"
+
+namespace rcp {
+cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStream_t s);
+cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
+                        int round, int als_mode, cudaStream_t s);
+cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
+                          cudaStream_t s);
+cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s);
+cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
+                         cudaStream_t s);
+}  // namespace rcp
+
+using namespace rcp;
+
+namespace {
+
+#define RCP_TRY(call)                                  \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return RCP_ECUDA;           \
+  } while (0)
+
+bool valid_plan(rcp_plan_t p) { return p != nullptr && p->N >= 2; }
+
+template <typename T>
+rcp_status dalloc(T** ptr, int64_t elems) {
+  *ptr = nullptr;
+  if (elems <= 0) elems = 1;
+  if (cudaMalloc((void**)ptr, (size_t)elems * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return RCP_ENOMEM;
+  }
+  return RCP_OK;
+}
+
+void free_plan(rcp_plan_t p) {
+  if (!p) return;
+  cudaFree(p->bufT[0]);
+  cudaFree(p->bufT[1]);
+  for (int n = 0; n < kMaxN; ++n) {
+    cudaFree(p->Q[n]);
+    cudaFree(p->At[n]);
+    cudaFree(p->Gm[n]);
+    cudaFree(p->A_stage[n]);
+  }
+  cudaFree(p->Y);
+  cudaFree(p->part);
+  cudaFree(p->tmp);
+  cudaFree(p->gpart);
+  cudaFree(p->G);
+  cudaFree(p->Rinv);
+  cudaFree(p->RWinv);
+  cudaFree(p->normpart);
+  cudaFree(p->M);
+  cudaFree(p->lam);
+  cudaFree(p->Bcore_own);
+  cudaFree(p->dstate);
+  cudaFree(p->X_stage);
+  cudaFree(p->lam_stage);
+  delete p;
+}
+
+// Input of mode n (1-based): X for n = 1, else the buffer T_n was written to.
+const void* mode_input(rcp_plan_t p, const void* X, int n, int* dtype) {
+  if (n == 1) {
+    *dtype = p->cfg.in_dtype;
+    return X;
+  }
+  *dtype = RCP_DTYPE_F64;
+  return p->bufT[(n - 2) % 2];
+}
+
+double* mode_output(rcp_plan_t p, int n) { return (double*)p->bufT[(n - 1) % 2]; }
+
+rcp_status check_device(rcp_plan_t p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RCP_ECUDA;
+  if (dev != p->device && cudaSetDevice(p->device) != cudaSuccess) return RCP_ECUDA;
+  return RCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rcp_status_str(rcp_status s) {
+  switch (s) {
+    case RCP_OK: return "ok";
+    case RCP_EINVAL: return "invalid argument";
+    case RCP_ENOMEM: return "out of memory";
+    case RCP_ECUDA: return "CUDA runtime error";
+    case RCP_ESINGULAR: return "singular Gram matrix";
+    case RCP_ENAN: return "non-finite value";
+    case RCP_ETIMEOUT: return "device wait timed out";
+    case RCP_EORDER: return "calls out of order";
+    case RCP_ENOTCONV: return "ALS stopped at max_iters";
+  }
+  return "unknown status";
+}
+
+rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
+  if (!cfg || !out) return RCP_EINVAL;
+  const int N = cfg->ndim;
+  if (N < 2 || N > kMaxN) return RCP_EINVAL;
+  if (cfg->rank < 1 || cfg->rank > RCP_MAX_RANK) return RCP_EINVAL;
+  if (cfg->oversample < 0 || cfg->power_iters < 0 || cfg->max_iters < 1) return RCP_EINVAL;
+  if (!(cfg->tol >= 0.0)) return RCP_EINVAL;
+  if (cfg->in_dtype != RCP_DTYPE_F64 && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
+  if (cfg->precision != RCP_PREC_F64) return RCP_EINVAL;
+  for (int n = 0; n < N; ++n)
+    if (cfg->dims[n] < 1 || cfg->dims[n] > (1LL << 40)) return RCP_EINVAL;
+  {
+    // every l_n = min(R + p, I_n, J_n) must lie in [R, RCP_MAX_L] (checked before any CUDA call)
+    int64_t cur[kMaxN];
+    for (int n = 0; n < N; ++n) cur[n] = cfg->dims[n];
+    for (int n = 0; n < N; ++n) {
+      int64_t J = 1;
+      for (int m = 0; m < N; ++m)
+        if (m != n) J *= cur[m];
+      const int64_t l = std::min<int64_t>((int64_t)cfg->rank + cfg->oversample, std::min(cur[n], J));
+      if (l < cfg->rank || l > RCP_MAX_L) return RCP_EINVAL;
+      cur[n] = l;
+    }
+  }
+
+  rcp_plan_t p = new (std::nothrow) rcp_plan_s();
+  if (!p) return RCP_ENOMEM;
+  memset((void*)p, 0, sizeof(*p));
+  p->cfg = *cfg;
+  p->stream = (cudaStream_t)stream;
+  p->N = N;
+  p->R = cfg->rank;
+  p->prec = cfg->precision;
+  p->work_elem = 8;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return RCP_ECUDA;
+  }
+  if (cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    return RCP_ECUDA;
+  }
+
+  // widths l_n = min(R + p, I_n, J_n) over the shrinking tensor (Algorithm 1 step 3)
+  int64_t cur[kMaxN];
+  for (int n = 0; n < N; ++n) cur[n] = p->dims[n] = cfg->dims[n];
+  int64_t bufmax = 1, Imax = 1, part_max = 1, gpart_max = 1, norm_max = 1, red_max = 1;
+  for (int n = 0; n < N; ++n) {
+    int64_t J = 1, L = 1, Rt = 1;
+    for (int m = 0; m < N; ++m)
+      if (m != n) J *= cur[m];
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < N; ++m) Rt *= cur[m];
+    const int64_t l = std::min<int64_t>((int64_t)cfg->rank + cfg->oversample, std::min(cur[n], J));
+    if (l < cfg->rank || l > RCP_MAX_L) {
+      delete p;
+      return RCP_EINVAL;
+    }
+    p->l[n] = (int)l;
+    p->view[n] = ModeView{L, cur[n], Rt, J};
+    bufmax = std::max(bufmax, J * l);
+    Imax = std::max(Imax, cur[n]);
+    const int ns = sketch_splits(p->view[n], p->nsm);
+    part_max = std::max(part_max, (int64_t)ns * cur[n] * l);
+    red_max = std::max(red_max, cur[n] * l);
+    const int ng = project_grid(p->view[n], p->nsm);
+    gpart_max = std::max(gpart_max, (int64_t)ng * (l * (l + 1) / 2));
+    norm_max = std::max(norm_max, (int64_t)ns * ((cur[n] + 255) / 256));
+    cur[n] = l;
+  }
+  p->core_elems = 1;
+  for (int n = 0; n < N; ++n) p->core_elems *= p->l[n];
+  // ALS MTTKRP partials
+  for (int n = 0; n < N; ++n) {
+    ModeView v{1, p->l[n], 1, 0};
+    for (int m = 0; m < n; ++m) v.L *= p->l[m];
+    for (int m = n + 1; m < N; ++m) v.Rt *= p->l[m];
+    v.J = v.L * v.Rt;
+    part_max = std::max(part_max, (int64_t)sketch_splits(v, p->nsm) * p->l[n] * p->R);
+  }
+  p->bufT_elems = bufmax;
+  p->part_elems = part_max;
+  p->tmp_elems = std::max<int64_t>(16 * std::max(red_max, (int64_t)kMaxL * (kMaxL + 1) / 2),
+                                   (int64_t)kMaxN * RCP_MAX_RANK);
+  p->gpart_elems = gpart_max;
+  p->normpart_elems = std::max<int64_t>(norm_max, 4096);
+
+  rcp_status st = RCP_OK;
+  auto A = [&](rcp_status s) {
+    if (st == RCP_OK) st = s;
+  };
+  A(dalloc((double**)&p->bufT[0], bufmax));
+  A(dalloc((double**)&p->bufT[1], bufmax));
+  for (int n = 0; n < N; ++n) {
+    A(dalloc(&p->Q[n], p->dims[n] * p->l[n]));
+    A(dalloc(&p->At[n], (int64_t)p->l[n] * p->R));
+    A(dalloc(&p->Gm[n], (int64_t)p->R * p->R));
+  }
+  A(dalloc(&p->Y, Imax * kMaxL));
+  A(dalloc(&p->part, part_max));
+  A(dalloc(&p->tmp, p->tmp_elems));
+  A(dalloc(&p->gpart, gpart_max));
+  A(dalloc(&p->G, kMaxL * (kMaxL + 1) / 2));
+  A(dalloc(&p->Rinv, kMaxL * kMaxL));
+  A(dalloc(&p->RWinv, kMaxL * kMaxL));
+  A(dalloc(&p->normpart, p->normpart_elems));
+  A(dalloc(&p->M, (int64_t)kMaxL * p->R));
+  A(dalloc(&p->lam, p->R));
+  A(dalloc(&p->dstate, 1));
+  if (cfg->flags & RCP_FLAG_HOST_STAGING) {
+    int64_t nx = 1;
+    for (int n = 0; n < N; ++n) nx *= p->dims[n];
+    const int64_t esz = cfg->in_dtype == RCP_DTYPE_F32 ? 4 : 8;
+    A(dalloc((char**)&p->X_stage, nx * esz));
+    for (int n = 0; n < N; ++n) A(dalloc(&p->A_stage[n], p->dims[n] * p->R));
+    A(dalloc(&p->lam_stage, p->R));
+  }
+  if (st == RCP_OK && cudaMemsetAsync(p->dstate, 0, sizeof(DevState), p->stream) != cudaSuccess)
+    st = RCP_ECUDA;
+  if (st != RCP_OK) {
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return RCP_OK;
+}
+
+rcp_status rcp_plan_destroy(rcp_plan_t plan) {
+  if (!plan) return RCP_OK;
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return RCP_OK;
+}
+
+int32_t rcp_width(rcp_plan_t plan, int32_t mode) {
+  if (!valid_plan(plan) || mode < 1 || mode > plan->N) return -1;
+  return plan->l[mode - 1];
+}
+
+rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) {
+  if (!valid_plan(p) || mode < 1 || mode > p->N) return RCP_EINVAL;
+  if (mode == 1 && !X) return RCP_EINVAL;
+  if (mode == 1) {
+    p->sketched = p->compressed = 0;  // a new decomposition starts at mode 1
+  } else if (p->compressed != mode - 1) {
+    return RCP_EORDER;
+  }
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  cudaStream_t s = p->stream;
+  const int n0 = mode - 1;
+  const ModeView v = p->view[n0];
+  const int l = p->l[n0];
+  int dt = 0;
+  const void* T = mode_input(p, X, mode, &dt);
+  double* W = mode_output(p, mode);
+  const int nsplit = sketch_splits(v, p->nsm);
+  const int64_t ny = v.I * l;
+
+  if (mode == 1) {
+    RCP_TRY(cudaMemsetAsync(p->dstate, 0, sizeof(DevState), s));
+    p->als_done = false;
+  }
+  // Y = T_(n) Omega_n (Algorithm 1 step 6); mode 1 also accumulates |X|^2
+  double* normpart = (mode == 1) ? p->normpart : nullptr;
+  RCP_TRY(launch_sketch_f64(T, dt, v, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, p->part,
+                            normpart, s));
+  RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
+  if (mode == 1) {
+    const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
+    RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
+  }
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  // q normalised power iterations (Algorithm 1 steps 7-11)
+  const int ng = project_grid(v, p->nsm);
+  const int npairs = l * (l + 1) / 2;
+  for (int it = 0; it < p->cfg.power_iters; ++it) {
+    // W = T_(n)^T Q and its Gram (step 9)
+    RCP_TRY(launch_project_f64(T, dt, v, l, p->Y, W, p->gpart, ng, s));
+    RCP_TRY(launch_reduce(p->gpart, ng, npairs, p->G, p->tmp, p->tmp_elems, s));
+    RCP_TRY(launch_chol(p->G, l, p->RWinv, p->dstate, (double)v.J, -1, 0, s));
+    // Y = T_(n) W R_W^{-1} (step 10), then Q = qr(Y) (step 8 of the next iteration / step 12)
+    RCP_TRY(launch_sketch_f64(T, dt, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
+    RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
+    RCP_TRY(launch_trmm(p->Y, v.I, l, p->RWinv, p->Y, p->dstate, 0, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  }
+  RCP_TRY(cudaMemcpyAsync(p->Q[n0], p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
+  if (Q_out)
+    RCP_TRY(cudaMemcpyAsync(Q_out, p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
+  p->sketched = mode;
+  return RCP_OK;
+}
+
+rcp_status rcp_compress(rcp_plan_t p, const void* X, int32_t mode) {
+  if (!valid_plan(p) || mode < 1 || mode > p->N) return RCP_EINVAL;
+  if (mode == 1 && !X) return RCP_EINVAL;
+  if (p->sketched != mode || p->compressed != mode - 1) return RCP_EORDER;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  const int n0 = mode - 1;
+  int dt = 0;
+  const void* T = mode_input(p, X, mode, &dt);
+  RCP_TRY(launch_project_f64(T, dt, p->view[n0], p->l[n0], p->Q[n0], mode_output(p, mode), nullptr,
+                             project_grid(p->view[n0], p->nsm), p->stream));
+  p->compressed = mode;
+  if (mode == p->N) p->Bcore64 = mode_output(p, mode);
+  return RCP_OK;
+}
+
+rcp_status rcp_als_init(rcp_plan_t p, const double* const* At_dev) {
+  if (!valid_plan(p) || !At_dev) return RCP_EINVAL;
+  for (int n = 1; n < p->N; ++n)
+    if (!At_dev[n]) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  for (int n = 1; n < p->N; ++n)
+    RCP_TRY(cudaMemcpyAsync(p->At[n], At_dev[n], sizeof(double) * p->l[n] * p->R,
+                            cudaMemcpyDeviceToDevice, p->stream));
+  p->user_init = true;
+  return RCP_OK;
+}
+
+static rcp_status read_state(rcp_plan_t p, DevState* h) {
+  if (cudaMemcpyAsync(h, p->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream) !=
+      cudaSuccess)
+    return RCP_ECUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return RCP_ECUDA;
+  return RCP_OK;
+}
+
+rcp_status rcp_als(rcp_plan_t p, double* lambda_host, double* fit_host, int32_t* iters_host) {
+  if (!valid_plan(p)) return RCP_EINVAL;
+  if (p->compressed != p->N) return RCP_EORDER;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  cudaStream_t s = p->stream;
+  RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
+  RCP_TRY(launch_als_init(p, s));
+  p->user_init = false;
+  for (int it = 0; it < p->cfg.max_iters; ++it)
+    for (int n0 = 0; n0 < p->N; ++n0) RCP_TRY(launch_als_sweep(p, n0, s));
+  p->als_done = true;
+  if (lambda_host || fit_host || iters_host) {
+    if (lambda_host)
+      RCP_TRY(cudaMemcpyAsync(lambda_host, p->lam, sizeof(double) * p->R, cudaMemcpyDeviceToHost, s));
+    DevState h;
+    if (read_state(p, &h) != RCP_OK) return RCP_ECUDA;
+    if (fit_host) *fit_host = h.fit;
+    if (iters_host) *iters_host = h.als_iters;
+    if (h.status) return (rcp_status)h.status;
+    if (h.als_done == 2 && p->cfg.tol > 0.0) return RCP_ENOTCONV;
+  }
+  return RCP_OK;
+}
+
+rcp_status rcp_project(rcp_plan_t p, double* const* A_dev, double* lambda_dev) {
+  if (!valid_plan(p) || !A_dev || !lambda_dev) return RCP_EINVAL;
+  for (int n = 0; n < p->N; ++n)
+    if (!A_dev[n]) return RCP_EINVAL;
+  if (!p->als_done) return RCP_EORDER;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  RCP_TRY(launch_backproject(p, A_dev, lambda_dev, p->stream));
+  return RCP_OK;
+}
+
+rcp_status rcp_decompose(rcp_plan_t p, const void* X, double* const* A_dev, double* lambda_dev) {
+  if (!valid_plan(p) || !X || !A_dev || !lambda_dev) return RCP_EINVAL;
+  for (int n = 0; n < p->N; ++n)
+    if (!A_dev[n]) return RCP_EINVAL;
+  p->sketched = p->compressed = 0;
+  p->als_done = false;
+  for (int mode = 1; mode <= p->N; ++mode) {
+    rcp_status st = rcp_sketch(p, X, mode, nullptr);
+    if (st != RCP_OK) return st;
+    st = rcp_compress(p, X, mode);
+    if (st != RCP_OK) return st;
+  }
+  rcp_status st = rcp_als(p, nullptr, nullptr, nullptr);
+  if (st != RCP_OK) return st;
+  return rcp_project(p, A_dev, lambda_dev);
+}
+
+rcp_status rcp_result_get(rcp_plan_t p, rcp_result* out) {
+  if (!valid_plan(p)) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  DevState h;
+  if (read_state(p, &h) != RCP_OK) return RCP_ECUDA;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->fit = h.fit;
+    out->iters = h.als_iters;
+    out->info = h.info;
+    out->norm_x2 = h.norm_x2;
+    out->norm_b2 = h.norm_b2;
+    const double r2 = h.norm_x2 - h.fit * h.norm_b2;
+    out->rel_err = h.norm_x2 > 0.0 ? sqrt(std::max(r2, 0.0) / h.norm_x2) : 0.0;
+    out->device_status = h.status;
+    for (int n = 0; n < p->N; ++n) out->widths[n] = p->l[n];
+  }
+  return (rcp_status)h.status;
+}
+
+rcp_status rcp_decompose_host(rcp_plan_t p, const void* X_host, double* const* A_host,
+                              double* lambda_host, rcp_result* res) {
+  if (!valid_plan(p) || !X_host || !A_host || !lambda_host) return RCP_EINVAL;
+  if (!(p->cfg.flags & RCP_FLAG_HOST_STAGING) || !p->X_stage) return RCP_EINVAL;
+  for (int n = 0; n < p->N; ++n)
+    if (!A_host[n]) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  cudaStream_t s = p->stream;
+  int64_t nx = 1;
+  for (int n = 0; n < p->N; ++n) nx *= p->dims[n];
+  const size_t bytes = (size_t)nx * (p->cfg.in_dtype == RCP_DTYPE_F32 ? 4 : 8);
+  RCP_TRY(cudaMemcpyAsync(p->X_stage, X_host, bytes, cudaMemcpyHostToDevice, s));
+  rcp_status st = rcp_decompose(p, p->X_stage, p->A_stage, p->lam_stage);
+  if (st != RCP_OK) return st;
+  for (int n = 0; n < p->N; ++n)
+    RCP_TRY(cudaMemcpyAsync(A_host[n], p->A_stage[n], sizeof(double) * p->dims[n] * p->R,
+                            cudaMemcpyDeviceToHost, s));
+  RCP_TRY(cudaMemcpyAsync(lambda_host, p->lam_stage, sizeof(double) * p->R, cudaMemcpyDeviceToHost, s));
+  return rcp_result_get(p, res);
+}
+
+rcp_status rcp_get_core(rcp_plan_t p, double* B_dev) {
+  if (!valid_plan(p) || !B_dev) return RCP_EINVAL;
+  if (p->compressed != p->N) return RCP_EORDER;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  RCP_TRY(cudaMemcpyAsync(B_dev, p->Bcore64, sizeof(double) * p->core_elems,
+                          cudaMemcpyDeviceToDevice, p->stream));
+  return RCP_OK;
+}
+
+rcp_status rcp_get_compressed_factors(rcp_plan_t p, double* const* At_dev, double* lambda_dev) {
+  if (!valid_plan(p) || !At_dev) return RCP_EINVAL;
+  if (!p->als_done) return RCP_EORDER;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  for (int n = 0; n < p->N; ++n)
+    if (At_dev[n])
+      RCP_TRY(cudaMemcpyAsync(At_dev[n], p->At[n], sizeof(double) * p->l[n] * p->R,
+                              cudaMemcpyDeviceToDevice, p->stream));
+  if (lambda_dev)
+    RCP_TRY(cudaMemcpyAsync(lambda_dev, p->lam, sizeof(double) * p->R, cudaMemcpyDeviceToDevice,
+                            p->stream));
+  return RCP_OK;
+}
+
+rcp_status rcp_last_error(rcp_plan_t p, int32_t* device_status) {
+  if (!valid_plan(p)) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  DevState h;
+  if (read_state(p, &h) != RCP_OK) return RCP_ECUDA;
+  if (device_status) *device_status = h.status;
+  return (rcp_status)h.status;
+}
+
+}  // extern "C"

@@ -1,0 +1,273 @@
+// Small dense FP64 linear algebra on the device: deterministic split reductions,
+// the Gram matrix of a tall-skinny Y, Cholesky with the shifted fallback, and
+// the triangular right-multiplication Q = Y R^{-1}.
+//
+// Orthonormalisation of each sketch (Algorithm 1 step 12, and the normalised
+// power iterations of steps 7-11) uses CholeskyQR2: G = Y^T Y = R^T R,
+// Q = Y R^{-1}, repeated once.  When the first Cholesky meets a pivot below the
+// shift of shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang & Yamamoto,
+// SIAM J. Sci. Comput. 2020: s = 11 (m n + n (n + 1)) u |Y|^2) the first round
+// factors G + s I instead and a third round runs.  Every R has a positive
+// diagonal, so Q equals the thin QR factor with positive diag(R).
+#include <math.h>
+
+#include <algorithm>
+
+#include "rcp_internal.cuh"
+
+namespace rcp {
+namespace {
+
+constexpr int kRedChunks = 16;
+
+__global__ void k_reduce(const double* __restrict__ part, int64_t nsplit, int64_t n,
+                         int64_t s0, int64_t s1_stride, double* __restrict__ out) {
+  // out[chunk * n + e] = sum over s in this chunk of part[s * n + e], fixed order
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int64_t c = blockIdx.y;
+  const int64_t sa = c * s1_stride, sb = min(nsplit, sa + s1_stride);
+  double acc = 0.0;
+  for (int64_t s = sa; s < sb; ++s) acc += part[s * n + e];
+  out[c * n + e] = acc;
+  (void)s0;
+}
+
+__device__ double block_sum(double v, double* red) {
+  const int tid = threadIdx.x;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0) {
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += red[w];
+  }
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// One CTA per packed upper-triangular pair (c1 <= c2): G = Y^T Y.
+__global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
+                             double* __restrict__ Gp) {
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  int c1 = 0, rem = p;
+  while (rem >= l - c1) { rem -= l - c1; ++c1; }
+  const int c2 = c1 + rem;
+  const double* y1 = Y + I * c1;
+  const double* y2 = Y + I * c2;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) acc = fma(y1[i], y2[i], acc);
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) Gp[p] = s;
+}
+
+// Cholesky G = R^T R of a packed SPD matrix (one CTA, in place: the upper
+// triangle of A becomes R), then R^{-1} column by column.
+// shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
+// round < 0: unconditional; round == 2: only when an earlier round was shifted.
+__global__ void k_chol(const double* __restrict__ Gp, int l, double* __restrict__ Rinv,
+                       DevState* st, double shift_rows, int round, int als_mode) {
+  __shared__ double A[kMaxL][kMaxL + 1];
+  __shared__ int fail;
+  __shared__ double shift;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (round == 2 && !st->extra_round) return;
+  if (round == 0 && tid == 0) st->extra_round = 0;
+
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    __syncthreads();
+    for (int p = tid; p < l * (l + 1) / 2; p += nt) {
+      int c1 = 0, rem = p;
+      while (rem >= l - c1) { rem -= l - c1; ++c1; }
+      A[c1][c1 + rem] = Gp[p];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tr = 0.0;
+      int bad = 0;
+      for (int c = 0; c < l; ++c) {
+        tr += A[c][c];
+        for (int d = c; d < l; ++d)
+          if (!isfinite(A[c][d])) bad = 1;
+      }
+      fail = bad ? 2 : 0;
+      const double u = 1.1102230246251565e-16;
+      shift = 11.0 * (shift_rows * l + (double)l * (l + 1)) * u * tr;
+      if (attempt == 1) {
+        for (int c = 0; c < l; ++c) A[c][c] += shift;
+      }
+    }
+    __syncthreads();
+    if (fail == 2) {
+      if (tid == 0) set_status(st, RCP_ENAN);
+      return;
+    }
+    for (int k = 0; k < l; ++k) {
+      if (tid == 0) {
+        const double d = A[k][k];
+        const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
+        if (!(d > floor_) || !(d > 0.0)) fail = 1;
+        A[k][k] = (d > 0.0) ? sqrt(d) : 1.0;
+      }
+      __syncthreads();
+      if (fail) break;
+      const double rkk = A[k][k];
+      for (int j = k + 1 + tid; j < l; j += nt) A[k][j] /= rkk;
+      __syncthreads();
+      const int m = l - k - 1;
+      for (int q = tid; q < m * m; q += nt) {
+        const int i = k + 1 + q / m, j = k + 1 + q % m;
+        if (j >= i) A[i][j] -= A[k][i] * A[k][j];
+      }
+      __syncthreads();
+    }
+    if (!fail) break;
+    if (attempt == 0 && shift_rows > 0.0) {
+      if (tid == 0) {
+        atomicOr(&st->info, als_mode ? RCP_INFO_ALS_REGULARISED : RCP_INFO_SHIFTED_QR);
+        if (round == 0) st->extra_round = 1;
+      }
+      continue;
+    }
+    if (tid == 0) set_status(st, RCP_ESINGULAR);
+    return;
+  }
+  // R^{-1}: thread c solves R x = e_c by back substitution into column c
+  for (int c = tid; c < l; c += nt) {
+    for (int i = l - 1; i >= 0; --i) {
+      double v = 0.0;
+      if (i <= c) {
+        v = (i == c) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= c; ++k) v -= A[i][k] * Rinv[k + l * c];
+        v /= A[i][i];
+      }
+      Rinv[i + l * c] = v;
+    }
+  }
+}
+
+// out[i, c] = sum_{k <= c} Y[i, k] Rinv[k, c]; one thread per row, in place allowed.
+template <int LMAX>
+__global__ void k_trmm(const double* Y, int64_t I, int l, const double* __restrict__ Rinv,
+                       double* out, const DevState* st, int only_if_extra) {
+  __shared__ double Rs[LMAX * LMAX];
+  if (only_if_extra && !st->extra_round) return;
+  if (st->status) return;
+  for (int q = threadIdx.x; q < l * l; q += blockDim.x) Rs[(q % l) + LMAX * (q / l)] = Rinv[q];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= I) return;
+  double y[LMAX];
+#pragma unroll
+  for (int k = 0; k < LMAX; ++k) y[k] = (k < l) ? Y[i + I * k] : 0.0;
+#pragma unroll
+  for (int c = 0; c < LMAX; ++c) {
+    if (c < l) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k <= c; ++k) acc = fma(y[k], Rs[k + LMAX * c], acc);
+      out[i + I * c] = acc;
+    }
+  }
+}
+
+__global__ void k_sum_to(const double* __restrict__ x, int64_t n, double* dst) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += x[i];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) *dst = s;
+}
+
+__global__ void k_sumsq_part(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], x[i], acc);
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_to_f64(const T* __restrict__ src, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_reduce(const double* part, int64_t nsplit, int64_t n, double* out, double* tmp,
+                          int64_t tmp_elems, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned gx = (unsigned)((n + threads - 1) / threads);
+  if (nsplit > 2 * kRedChunks && tmp && tmp_elems >= kRedChunks * n) {
+    const int64_t stride = (nsplit + kRedChunks - 1) / kRedChunks;
+    k_reduce<<<dim3(gx, kRedChunks), threads, 0, s>>>(part, nsplit, n, 0, stride, tmp);
+    k_reduce<<<dim3(gx, 1), threads, 0, s>>>(tmp, kRedChunks, n, 0, kRedChunks, out);
+  } else {
+    k_reduce<<<dim3(gx, 1), threads, 0, s>>>(part, nsplit, n, 0, nsplit, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStream_t s) {
+  k_gram_pairs<<<l * (l + 1) / 2, 128, 0, s>>>(Y, I, l, Gp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
+                        int round, int als_mode, cudaStream_t s) {
+  k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmm(const double* Y, int64_t I, int l, const double* Rinv, double* out,
+                        const DevState* st, int only_if_extra, cudaStream_t s) {
+  const int threads = 64;
+  const unsigned grid = (unsigned)((I + threads - 1) / threads);
+  if (l <= 16) k_trmm<16><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
+  else if (l <= 32) k_trmm<32><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
+  else if (l <= 48) k_trmm<48><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
+  else k_trmm<64><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
+                          cudaStream_t s) {
+  // round 0 (shift allowed), round 1, round 2 (only after a shifted round); in place on Y
+  for (int round = 0; round < 3; ++round) {
+    cudaError_t e = launch_gram(Y, I, l, Gp, s);
+    if (e != cudaSuccess) return e;
+    e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s);
+    if (e != cudaSuccess) return e;
+    e = launch_trmm(Y, I, l, Rinv, Y, st, round == 2, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s) {
+  k_sum_to<<<1, 256, 0, s>>>(part, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
+                         cudaStream_t s) {
+  k_sumsq_part<<<nblocks, 256, 0, s>>>(x, n, part);
+  k_sum_to<<<1, 256, 0, s>>>(part, nblocks, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  if (src_dtype == RCP_DTYPE_F32)
+    k_to_f64<float><<<grid, 256, 0, s>>>((const float*)src, n, dst);
+  else
+    k_to_f64<double><<<grid, 256, 0, s>>>((const double*)src, n, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace rcp

@@ -1,0 +1,298 @@
+// FP64 sweeps over the working tensor T_n (plain method, CUDA cores).
+//
+// Row sweep   : P[i, c] = sum_j T_(n)[i, j] V[j, c]          (split over j)
+//   V = Omega_n  -> the sketch Y = T_(n) Omega_n             (Algorithm 1 step 6, Eq. sampleMatrix)
+//   V = W        -> Y = T_(n) W of a power iteration         (Algorithm 1 step 10)
+//   V = KR rows  -> the MTTKRP B_(n) (KR of the factors)     (Algorithm 2 steps 4, 6, 8)
+// Column sweep: W[j, c] = sum_i T_(n)[i, j] Q[i, c]          (no split)
+//   Q = Q of the sketch -> W = T_(n)^T Q                     (Algorithm 1 step 9), with the
+//                          Gram W^T W of its normalisation accumulated per CTA
+//   Q = Q_n             -> T_{n+1} = T_n x_n Q_n^T          (Algorithm 1 step 13, Definition 1)
+// W is written in the Kolda layout of T_{n+1}: W[a + L (c + l b)] for column j = a + L b.
+#include "rcp_internal.cuh"
+
+namespace rcp {
+namespace {
+
+constexpr int kRowTile = 32;      // columns j staged per step of the row sweep
+constexpr int kProjThreads = 256; // columns j per CTA step of the column sweep
+constexpr int kProjRows = 32;     // rows of Q staged per step of the column sweep
+
+enum { kSrcOmega = 0, kSrcW = 1, kSrcKr = 2 };
+
+template <typename T>
+__device__ __forceinline__ double ld_f64(const T* p) { return (double)__ldg(p); }
+
+template <int LMAX, typename TIn, int SRC, bool NORM>
+__global__ void __launch_bounds__(256)
+k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, uint64_t seed,
+            uint32_t sid, const double* __restrict__ W, KrDims kr, int64_t jchunk,
+            double* __restrict__ part, double* __restrict__ normpart) {
+  __shared__ double Vs[kRowTile][LMAX];
+  __shared__ int64_t offs[kRowTile];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * rows_per_cta + tid;
+  const bool row_ok = (tid < rows_per_cta) && (i < v.I);
+  const int64_t j0 = (int64_t)blockIdx.y * jchunk;
+  const int64_t j1 = min(v.J, j0 + jchunk);
+
+  double acc[LMAX];
+#pragma unroll
+  for (int c = 0; c < LMAX; ++c) acc[c] = 0.0;
+  double nrm = 0.0;
+
+  for (int k = tid; k < kRowTile * LMAX; k += blockDim.x) (&Vs[0][0])[k] = 0.0;
+  __syncthreads();
+
+  for (int64_t jt = j0; jt < j1; jt += kRowTile) {
+    const int nj = (int)min((int64_t)kRowTile, j1 - jt);
+    if (tid < nj) {
+      const int64_t j = jt + tid;
+      offs[tid] = (j % v.L) + v.L * v.I * (j / v.L);
+    }
+    if (SRC == kSrcOmega) {
+      // Omega_n[j, c] is element e = j * l + c of the stream; pairs g = e / 2.
+      const int64_t e0 = jt * l, e1 = (jt + nj) * (int64_t)l;
+      const int64_t g0 = e0 >> 1, g1 = (e1 - 1) >> 1;
+      for (int64_t g = g0 + tid; g <= g1; g += blockDim.x) {
+        const double2 z = normal_pair_f64(seed, sid, kPurposeSketch, (uint64_t)g);
+        int64_t e = 2 * g;
+        if (e >= e0) Vs[e / l - jt][e % l] = z.x;
+        ++e;
+        if (e < e1) Vs[e / l - jt][e % l] = z.y;
+      }
+    } else if (SRC == kSrcW) {
+      for (int k = tid; k < nj * l; k += blockDim.x) {
+        const int jj = k / l, c = k - jj * l;
+        const int64_t j = jt + jj;
+        Vs[jj][c] = W[(j % v.L) + v.L * (c + (int64_t)l * (j / v.L))];
+      }
+    } else {
+      // Khatri-Rao row of the factors of every mode but kr.n, mode 1 fastest.
+      for (int k = tid; k < nj * l; k += blockDim.x) {
+        const int jj = k / l, r = k - jj * l;
+        int64_t jr = jt + jj;
+        double prod = 1.0;
+        for (int m = 0; m < kr.N; ++m) {
+          if (m == kr.n) continue;
+          const int d = kr.dims[m];
+          const int im = (int)(jr % d);
+          jr /= d;
+          prod *= kr.A[m][im + (int64_t)d * r];
+        }
+        Vs[jj][r] = prod;
+      }
+    }
+    __syncthreads();
+    if (row_ok) {
+      for (int jj = 0; jj < nj; ++jj) {
+        const double x = ld_f64(T + offs[jj] + v.L * i);
+        if (NORM) nrm = fma(x, x, nrm);
+#pragma unroll
+        for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Vs[jj][c], acc[c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (row_ok) {
+#pragma unroll
+    for (int c = 0; c < LMAX; ++c)
+      if (c < l) part[((int64_t)blockIdx.y * l + c) * v.I + i] = acc[c];
+  }
+  if (NORM) {
+    __shared__ double red[256];
+    red[tid] = nrm;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s && tid + s < (int)blockDim.x) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    if (tid == 0) normpart[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+  }
+}
+
+template <int LMAX, typename TIn, bool GRAM>
+__global__ void __launch_bounds__(kProjThreads)
+k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
+            double* __restrict__ W, double* __restrict__ gpart) {
+  extern __shared__ double sm[];
+  double* Qs = sm;                                  // kProjRows x LMAX
+  double* Ws = sm + kProjRows * LMAX;               // kProjThreads x (LMAX + 1), GRAM only
+  __shared__ unsigned short pairs[kMaxL * (kMaxL + 1) / 2];
+  constexpr int kSlots = (LMAX * (LMAX + 1) / 2 + kProjThreads - 1) / kProjThreads;
+  const int tid = threadIdx.x;
+  const int npairs = l * (l + 1) / 2;
+  double gacc[GRAM ? kSlots : 1];
+#pragma unroll
+  for (int s = 0; s < (GRAM ? kSlots : 1); ++s) gacc[s] = 0.0;
+  if (GRAM && tid < l) {
+    int base = tid * l - tid * (tid - 1) / 2;
+    for (int c2 = tid; c2 < l; ++c2) pairs[base + c2 - tid] = (unsigned short)((tid << 8) | c2);
+  }
+
+  for (int64_t jb = blockIdx.x; jb * kProjThreads < v.J; jb += gridDim.x) {
+    const int64_t j = jb * kProjThreads + tid;
+    const bool ok = j < v.J;
+    const int64_t a = ok ? j % v.L : 0, b = ok ? j / v.L : 0;
+    const int64_t base = a + v.L * v.I * b;
+    double acc[LMAX];
+#pragma unroll
+    for (int c = 0; c < LMAX; ++c) acc[c] = 0.0;
+    for (int64_t i0 = 0; i0 < v.I; i0 += kProjRows) {
+      const int ni = (int)min((int64_t)kProjRows, v.I - i0);
+      __syncthreads();
+      for (int k = tid; k < kProjRows * LMAX; k += kProjThreads) {
+        const int ii = k / LMAX, c = k - ii * LMAX;
+        Qs[k] = (ii < ni && c < l) ? Q[(i0 + ii) + v.I * c] : 0.0;
+      }
+      __syncthreads();
+      if (ok) {
+        for (int ii = 0; ii < ni; ++ii) {
+          const double x = ld_f64(T + base + v.L * (i0 + ii));
+#pragma unroll
+          for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Qs[ii * LMAX + c], acc[c]);
+        }
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int c = 0; c < LMAX; ++c)
+        if (c < l) W[a + v.L * (c + (int64_t)l * b)] = acc[c];
+    }
+    if (GRAM) {
+#pragma unroll
+      for (int c = 0; c < LMAX; ++c) Ws[tid * (LMAX + 1) + c] = ok ? acc[c] : 0.0;
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        const int p = tid + s * kProjThreads;
+        if (p < npairs) {
+          const int c1 = pairs[p] >> 8, c2 = pairs[p] & 0xff;
+          double sum = 0.0;
+          for (int t = 0; t < kProjThreads; ++t)
+            sum = fma(Ws[t * (LMAX + 1) + c1], Ws[t * (LMAX + 1) + c2], sum);
+          gacc[s] += sum;
+        }
+      }
+    }
+  }
+  if (GRAM) {
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      const int p = tid + s * kProjThreads;
+      if (p < npairs) gpart[(int64_t)blockIdx.x * npairs + p] = gacc[s];
+    }
+  }
+}
+
+int lmax_bucket(int l) { return l <= 16 ? 16 : l <= 32 ? 32 : l <= 48 ? 48 : 64; }
+
+template <int LMAX, typename TIn>
+cudaError_t row_sweep_typed(const TIn* T, ModeView v, int l, uint64_t seed, uint32_t sid,
+                            const double* W, const KrDims* kr, int src, int nsplit, double* part,
+                            double* normpart, cudaStream_t s) {
+  const int64_t nib = (v.I + 255) / 256;
+  const int64_t rpc = (v.I + nib - 1) / nib;
+  const int threads = (int)((rpc + 31) / 32 * 32);
+  const int64_t jchunk = (v.J + nsplit - 1) / nsplit;
+  dim3 grid((unsigned)nib, (unsigned)nsplit);
+  KrDims k{};
+  if (kr) k = *kr;
+  if (src == kSrcOmega) {
+    if (normpart)
+      k_row_sweep<LMAX, TIn, kSrcOmega, true><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                     jchunk, part, normpart);
+    else
+      k_row_sweep<LMAX, TIn, kSrcOmega, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                      jchunk, part, normpart);
+  } else if (src == kSrcW) {
+    k_row_sweep<LMAX, TIn, kSrcW, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                jchunk, part, normpart);
+  } else {
+    k_row_sweep<LMAX, TIn, kSrcKr, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                 jchunk, part, normpart);
+  }
+  return cudaGetLastError();
+}
+
+template <typename TIn>
+cudaError_t row_sweep_any(const TIn* T, ModeView v, int l, uint64_t seed, uint32_t sid,
+                          const double* W, const KrDims* kr, int src, int nsplit, double* part,
+                          double* normpart, cudaStream_t s) {
+  switch (lmax_bucket(l)) {
+    case 16: return row_sweep_typed<16>(T, v, l, seed, sid, W, kr, src, nsplit, part, normpart, s);
+    case 32: return row_sweep_typed<32>(T, v, l, seed, sid, W, kr, src, nsplit, part, normpart, s);
+    case 48: return row_sweep_typed<48>(T, v, l, seed, sid, W, kr, src, nsplit, part, normpart, s);
+    default: return row_sweep_typed<64>(T, v, l, seed, sid, W, kr, src, nsplit, part, normpart, s);
+  }
+}
+
+template <int LMAX, typename TIn>
+cudaError_t col_sweep_typed(const TIn* T, ModeView v, int l, const double* Q, double* W,
+                            double* gpart, int nblocks, cudaStream_t s) {
+  const size_t smem_q = (size_t)kProjRows * LMAX * sizeof(double);
+  if (gpart) {
+    const size_t smem = smem_q + (size_t)kProjThreads * (LMAX + 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_col_sweep<LMAX, TIn, true><<<nblocks, kProjThreads, smem, s>>>(T, v, l, Q, W, gpart);
+  } else {
+    k_col_sweep<LMAX, TIn, false><<<nblocks, kProjThreads, smem_q, s>>>(T, v, l, Q, W, gpart);
+  }
+  return cudaGetLastError();
+}
+
+template <typename TIn>
+cudaError_t col_sweep_any(const TIn* T, ModeView v, int l, const double* Q, double* W,
+                          double* gpart, int nblocks, cudaStream_t s) {
+  switch (lmax_bucket(l)) {
+    case 16: return col_sweep_typed<16>(T, v, l, Q, W, gpart, nblocks, s);
+    case 32: return col_sweep_typed<32>(T, v, l, Q, W, gpart, nblocks, s);
+    case 48: return col_sweep_typed<48>(T, v, l, Q, W, gpart, nblocks, s);
+    default: return col_sweep_typed<64>(T, v, l, Q, W, gpart, nblocks, s);
+  }
+}
+
+}  // namespace
+
+int sketch_splits(const ModeView& v, int nsm) {
+  const int64_t nib = (v.I + 255) / 256;
+  int64_t want = (2LL * nsm + nib - 1) / nib;            // about two CTAs per SM
+  const int64_t maxs = (v.J + kRowTile - 1) / kRowTile;  // at least one tile per split
+  if (want > maxs) want = maxs;
+  if (want < 1) want = 1;
+  if (want > 65535) want = 65535;
+  return (int)want;
+}
+
+int project_grid(const ModeView& v, int nsm) {
+  const int64_t blocks = (v.J + kProjThreads - 1) / kProjThreads;
+  const int64_t cap = 4LL * nsm;
+  return (int)(blocks < cap ? (blocks < 1 ? 1 : blocks) : cap);
+}
+
+cudaError_t launch_sketch_f64(const void* T, int in_dtype, ModeView v, int l, uint64_t seed,
+                              uint32_t stream_id, const double* W, int nsplit, double* part,
+                              double* normpart, cudaStream_t s) {
+  const int src = W ? kSrcW : kSrcOmega;
+  if (in_dtype == RCP_DTYPE_F32)
+    return row_sweep_any((const float*)T, v, l, seed, stream_id, W, nullptr, src, nsplit, part,
+                         normpart, s);
+  return row_sweep_any((const double*)T, v, l, seed, stream_id, W, nullptr, src, nsplit, part,
+                       normpart, s);
+}
+
+cudaError_t launch_mttkrp_f64(const double* B, ModeView v, int R, const KrDims& kr, int nsplit,
+                              double* part, cudaStream_t s) {
+  return row_sweep_any(B, v, R, 0, 0, nullptr, &kr, kSrcKr, nsplit, part, nullptr, s);
+}
+
+cudaError_t launch_project_f64(const void* T, int in_dtype, ModeView v, int l, const double* Q,
+                               double* W, double* gpart, int nblocks, cudaStream_t s) {
+  if (in_dtype == RCP_DTYPE_F32)
+    return col_sweep_any((const float*)T, v, l, Q, W, gpart, nblocks, s);
+  return col_sweep_any((const double*)T, v, l, Q, W, gpart, nblocks, s);
+}
+
+}  // namespace rcp
