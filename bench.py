@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of randomized CP decomposition (rCP-ALS) on one synthetic workload.
+
+One step = one whole decomposition (Algorithm 1 compression of every mode,
+Algorithm 2 ALS on the compressed tensor, back-projection) of a tensor that is
+already resident in HBM.  Default workload: 400 x 400 x 400 FP32, R = 20 terms
+with factor congruence 0.5, SNR 10 dB, p = 10, q = 2, ALS up to 50 sweeps or a
+fit change below 1e-10.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+Launch with torchrun for several GPUs: every rank decomposes its own copy
+(weak scaling, no collective on the data path); timing is the max over ranks.
+"""
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rCP end-to-end s + sketch-pass HBM GB/s, 400³ R=20, vs FP64 GPU at equal fit"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+WORKLOADS = {
+    "c2": ("c2_400cubed_f32", "400x400x400 FP32, R=20, factor congruence 0.5, SNR 10 dB, p=10, q=2, "
+                              "ALS <=50 sweeps or fit change <1e-10, seed 0"),
+    "c1": ("c1_100cubed_f64", "100x100x100 FP64, R=5, N(0,1) factors, SNR 20 dB, p=10, q=2, "
+                              "ALS <=50 sweeps or fit change <1e-10, seed 0"),
+    "c3": ("c3_128cubed_x64_f32", "128x128x128x64 FP32, R=32, lambda_r=0.9^r, SNR 15 dB, p=16, q=1, "
+                                  "ALS <=50 sweeps or fit change <1e-10, seed 0"),
+    "c4": ("c4_flow_512x1024x800_f32", "512x1024x800 FP32 flow-like, R=10, SNR 20 dB, p=10, q=2, "
+                                       "ALS <=50 sweeps or fit change <1e-10, seed 0"),
+}
+
+# GB300 FP64 arithmetic peak used for ALU-bound FP64 kernels: 152 SMs x 2 FP64
+# FMA per clock per SM x 2 FLOP x 2.07 GHz ("Roofline").
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--precision", choices=["f64", "mixed"], default="f64")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, budget_s=30.0):
+    """The FP64 oracle as it stands, on the host cores, on one whole decomposition."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, 0)
+    dt = time.perf_counter() - t0
+    return {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one whole decomposition of the same workload (numpy FP64 oracle, "
+                      "BLAS threads = all host cores)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    name, desc = WORKLOADS[args.workload]
+    w = synth.config(name)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, 0)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "l2": "host run"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "one whole decomposition per step (numpy FP64 oracle)"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import synth
+    from paper_1703_09074_gb300 import Plan
+    from paper_1703_09074_gb300 import _lib
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=dev)
+        pg = td
+    name, desc = WORKLOADS[args.workload]
+    w = synth.config(name)
+    in_dt = torch.float64 if w.dtype == "f64" else torch.float32
+    X = torch.from_numpy(w.kolda).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = Plan(w.dims, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, seed=0,
+                in_dtype=in_dt, precision=args.precision, host_staging=True, stream=stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    for _ in range(args.warmup):
+        plan.decompose(X)
+        plan.result()
+
+    lib = plan.lib
+    _lib.check(lib.rcp_profile_enable(plan.h, 1), "rcp_profile_enable")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        plan.decompose(X)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    res = plan.result()
+
+    # per-kernel device times over the timed region
+    def kt(kind, mode):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _lib.check(lib.rcp_profile_read(plan.h, kind, mode, ctypes.byref(n), ctypes.byref(ms)),
+                   "rcp_profile_read")
+        return n.value, ms.value
+
+    launches_total, _ = kt(_lib.RCP_KT_ALL, 0)
+    stages = {}
+    for kind, nm in ((_lib.RCP_KT_SKETCH, "sketch"), (_lib.RCP_KT_APPLY, "apply"),
+                     (_lib.RCP_KT_PROJECT, "project"), (_lib.RCP_KT_TTM, "ttm"),
+                     (_lib.RCP_KT_ALS, "als")):
+        n, ms = kt(kind, 0)
+        stages[nm] = {"launches": n, "ms_per_step": ms / args.steps}
+    _lib.check(lib.rcp_profile_enable(plan.h, 0), "rcp_profile_enable")
+
+    # dominant sweep: mode-1 kernels over X
+    I, J = w.dims[0], 1
+    for d in w.dims[1:]:
+        J *= d
+    l1 = plan.widths[0]
+    xbytes = X.numel() * X.element_size()
+    sk_n, sk_ms = kt(_lib.RCP_KT_SKETCH, 1)
+    cands = {}
+    for kind, nm in ((_lib.RCP_KT_SKETCH, "sketch"), (_lib.RCP_KT_APPLY, "apply"),
+                     (_lib.RCP_KT_PROJECT, "project"), (_lib.RCP_KT_TTM, "ttm")):
+        n, ms = kt(kind, 1)
+        if n:
+            cands[nm] = (n, ms)
+    dom = max(cands, key=lambda k: cands[k][1])
+    n_dom, ms_dom = cands[dom]
+    per_launch_s = ms_dom / n_dom / 1e3
+    pk, src = peaks()
+    if args.precision == "f64":
+        flops = 2.0 * I * J * l1
+        achieved = flops / per_launch_s / 1e12
+        roof = {"bound": "alu", "kernel": f"mode-1 {dom} sweep (FP64 FMA)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived FP64 FMA rate (not in the measured-peaks file)",
+                "algorithmic": f"{flops:.4g} FLOP per launch (2 I J l)"}
+    else:
+        achieved = xbytes / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": f"mode-1 {dom} sweep", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": None, "peak_source": src,
+                "algorithmic": f"{xbytes} B per launch (one read of X)"}
+    sketch_gbs = xbytes / (sk_ms / sk_n / 1e3) / 1e9 if sk_n else None
+
+    # end to end through the host-buffer entry point (H2D of X and D2H of factors inside)
+    e2e = []
+    if args.e2e_steps > 0:
+        Xh = torch.from_numpy(w.kolda).pin_memory()
+        Ah = [torch.empty((w.rank, d), dtype=torch.float64, pin_memory=True) for d in w.dims]
+        lh = torch.empty(w.rank, dtype=torch.float64, pin_memory=True)
+        plan.decompose_host(Xh, Ah, lh)
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            plan.decompose_host(Xh, Ah, lh)
+            e2e.append(time.perf_counter() - t0)
+    e2e_v = statistics.mean(e2e) if e2e else float("nan")
+    d2h = sum(d * w.rank * 8 for d in w.dims) + w.rank * 8
+    if pg:
+        t = torch.tensor([e2e_v], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_v = float(t.item())
+
+    value = total_ms / 1e3 / (args.steps * ws)
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "f64" else "f32acc/tf32",
+            "data": "synthetic",
+            "config": {"workload": desc, "precision": args.precision,
+                       "l2": "X (256 MB) larger than L2, and a 512 MB L2 flush between steps",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "sketch_pass_gbs": sketch_gbs,
+            "fit": res["fit"], "rel_err": res["rel_err"], "als_iters": res["iters"],
+            "stages": stages,
+            "roofline": roof,
+            "e2e": {"value": e2e_v / ws, "unit": "s", "h2d_bytes_per_step": xbytes,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_total // args.steps,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

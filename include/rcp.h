@@ -209,6 +209,31 @@ rcp_status rcp_last_error(rcp_plan_t plan, int32_t* device_status);
 /* Static description of a status code. */
 const char* rcp_status_str(rcp_status s);
 
+/* Kernel classes timed by the profiling entry points. */
+typedef enum {
+  RCP_KT_SKETCH = 0,   /* Y = T_(n) Omega_n sweep (Algorithm 1 step 6)                */
+  RCP_KT_APPLY = 1,    /* Y = T_(n) W sweep of a power iteration (step 10)            */
+  RCP_KT_PROJECT = 2,  /* W = T_(n)^T Q sweep of a power iteration (step 9)           */
+  RCP_KT_TTM = 3,      /* T_{n+1} = T_n x_n Q_n^T (step 13)                           */
+  RCP_KT_ALS = 4,      /* every ALS kernel (Algorithm 2 steps 3-11)                   */
+  RCP_KT_ALL = 5,      /* read-only: all kernels the library launched                 */
+  RCP_KT_COUNT = 6
+} rcp_kernel_kind;
+
+/* Start (enable != 0) or stop recording CUDA events on the plan's stream
+ * around every sweep launch; enabling clears earlier records.  Launches are
+ * counted whether or not events are recorded.  Not a method step (the paper
+ * has no counterpart): it exists to measure the kernels. */
+rcp_status rcp_profile_enable(rcp_plan_t plan, int32_t enable);
+
+/* Synchronise and report, for kernel class `kind` in 1-based mode `mode`
+ * (0 = all modes), the number of launches and their summed device time in
+ * milliseconds since the last rcp_profile_enable(plan, 1).  For RCP_KT_ALL
+ * only `launches` is meaningful (total kernels launched by the library on
+ * this plan).  Either output may be NULL. */
+rcp_status rcp_profile_read(rcp_plan_t plan, int32_t kind, int32_t mode, int64_t* launches,
+                            double* total_ms);
+
 /* Test-matrix generator (Section 3.1: Gaussian entries for Omega_n), exposed
  * so that its counter-based stream can be checked against an independent
  * implementation.  Writes out_dev[k] for k < count: the element (first + k) of

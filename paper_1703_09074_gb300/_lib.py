@@ -18,6 +18,7 @@ RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
 RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
 RCP_FLAG_HOST_STAGING = 1
 RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED = 1, 2
+RCP_KT_SKETCH, RCP_KT_APPLY, RCP_KT_PROJECT, RCP_KT_TTM, RCP_KT_ALS, RCP_KT_ALL = range(6)
 
 
 class RcpConfig(ctypes.Structure):
@@ -64,6 +65,9 @@ SIGNATURES = {
     "rcp_get_compressed_factors": (ctypes.c_int, [P, ctypes.POINTER(P), P]),
     "rcp_last_error": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
     "rcp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "rcp_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
+    "rcp_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int64), DP]),
     "rcp_test_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_int64, ctypes.c_int64, P, P, P, P]),
 }

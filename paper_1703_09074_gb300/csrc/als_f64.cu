@@ -307,6 +307,7 @@ AlsArgs make_args(rcp_plan_s* p, int n0) {
 
 cudaError_t launch_als_init(rcp_plan_s* p, cudaStream_t s) {
   AlsArgs a = make_args(p, 0);
+  count_launches(1);
   k_als_init<<<1, 256, 0, s>>>(a, p->cfg.seed, p->user_init ? 1 : 0);
   return cudaGetLastError();
 }
@@ -342,6 +343,7 @@ cudaError_t launch_als_sweep(rcp_plan_s* p, int n0, cudaStream_t s) {
   const size_t smem = (size_t)(2 * ln * R + R * (R + 1) + R * R + R) * sizeof(double);
   e = cudaFuncSetAttribute(k_als_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   k_als_update<<<1, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -356,6 +358,7 @@ cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lamb
     pa.I[n] = p->dims[n];
     pa.A[n] = A_dev[n];
     const int64_t I = p->dims[n];
+    count_launches(1);
     k_backproject<<<(unsigned)((I + 63) / 64), 64, 0, s>>>(p->Q[n], I, p->l[n], p->At[n], p->R,
                                                            A_dev[n]);
     if (I * p->R > maxe) maxe = I * p->R;
@@ -363,6 +366,7 @@ cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lamb
   pa.nu = p->tmp;
   pa.lam_t = p->lam;
   pa.lam_out = lambda_dev;
+  count_launches(2);
   k_colnorms<<<p->N * p->R, 256, 0, s>>>(pa);
   k_normalise<<<dim3((unsigned)((maxe + 255) / 256), p->N), 256, 0, s>>>(pa);
   return cudaGetLastError();

@@ -21,7 +21,30 @@ cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, 
 
 using namespace rcp;
 
+int64_t& rcp::launch_counter() {
+  static thread_local int64_t count = 0;
+  return count;
+}
+
 namespace {
+
+// Records a pair of CUDA events on the plan's stream around the launches made
+// in its scope when profiling is on.
+struct Span {
+  rcp_plan_t p;
+  int idx = -1;
+  Span(rcp_plan_t p_, int kind, int mode) : p(p_) {
+    if (p->prof_on && p->prof_n < p->prof_cap) {
+      idx = p->prof_n++;
+      p->prof[idx].kind = kind;
+      p->prof[idx].mode = mode;
+      cudaEventRecord(p->prof[idx].a, p->stream);
+    }
+  }
+  ~Span() {
+    if (idx >= 0) cudaEventRecord(p->prof[idx].b, p->stream);
+  }
+};
 
 #define RCP_TRY(call)                                  \
   do {                                                 \
@@ -66,6 +89,13 @@ void free_plan(rcp_plan_t p) {
   cudaFree(p->dstate);
   cudaFree(p->X_stage);
   cudaFree(p->lam_stage);
+  if (p->prof) {
+    for (int k = 0; k < p->prof_cap; ++k) {
+      cudaEventDestroy(p->prof[k].a);
+      cudaEventDestroy(p->prof[k].b);
+    }
+    delete[] p->prof;
+  }
   delete p;
 }
 
@@ -271,8 +301,11 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
   }
   // Y = T_(n) Omega_n (Algorithm 1 step 6); mode 1 also accumulates |X|^2
   double* normpart = (mode == 1) ? p->normpart : nullptr;
-  RCP_TRY(launch_sketch_f64(T, dt, v, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, p->part,
-                            normpart, s));
+  {
+    Span sp(p, RCP_KT_SKETCH, mode);
+    RCP_TRY(launch_sketch_f64(T, dt, v, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, p->part,
+                              normpart, s));
+  }
   RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
   if (mode == 1) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
@@ -284,11 +317,17 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
   const int npairs = l * (l + 1) / 2;
   for (int it = 0; it < p->cfg.power_iters; ++it) {
     // W = T_(n)^T Q and its Gram (step 9)
-    RCP_TRY(launch_project_f64(T, dt, v, l, p->Y, W, p->gpart, ng, s));
+    {
+      Span sp(p, RCP_KT_PROJECT, mode);
+      RCP_TRY(launch_project_f64(T, dt, v, l, p->Y, W, p->gpart, ng, s));
+    }
     RCP_TRY(launch_reduce(p->gpart, ng, npairs, p->G, p->tmp, p->tmp_elems, s));
     RCP_TRY(launch_chol(p->G, l, p->RWinv, p->dstate, (double)v.J, -1, 0, s));
     // Y = T_(n) W R_W^{-1} (step 10), then Q = qr(Y) (step 8 of the next iteration / step 12)
-    RCP_TRY(launch_sketch_f64(T, dt, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
+    {
+      Span sp(p, RCP_KT_APPLY, mode);
+      RCP_TRY(launch_sketch_f64(T, dt, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
+    }
     RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
     RCP_TRY(launch_trmm(p->Y, v.I, l, p->RWinv, p->Y, p->dstate, 0, s));
     RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
@@ -308,8 +347,11 @@ rcp_status rcp_compress(rcp_plan_t p, const void* X, int32_t mode) {
   const int n0 = mode - 1;
   int dt = 0;
   const void* T = mode_input(p, X, mode, &dt);
-  RCP_TRY(launch_project_f64(T, dt, p->view[n0], p->l[n0], p->Q[n0], mode_output(p, mode), nullptr,
-                             project_grid(p->view[n0], p->nsm), p->stream));
+  {
+    Span sp(p, RCP_KT_TTM, mode);
+    RCP_TRY(launch_project_f64(T, dt, p->view[n0], p->l[n0], p->Q[n0], mode_output(p, mode),
+                               nullptr, project_grid(p->view[n0], p->nsm), p->stream));
+  }
   p->compressed = mode;
   if (mode == p->N) p->Bcore64 = mode_output(p, mode);
   return RCP_OK;
@@ -340,11 +382,14 @@ rcp_status rcp_als(rcp_plan_t p, double* lambda_host, double* fit_host, int32_t*
   if (p->compressed != p->N) return RCP_EORDER;
   if (check_device(p) != RCP_OK) return RCP_ECUDA;
   cudaStream_t s = p->stream;
-  RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
-  RCP_TRY(launch_als_init(p, s));
-  p->user_init = false;
-  for (int it = 0; it < p->cfg.max_iters; ++it)
-    for (int n0 = 0; n0 < p->N; ++n0) RCP_TRY(launch_als_sweep(p, n0, s));
+  {
+    Span sp(p, RCP_KT_ALS, 0);
+    RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
+    RCP_TRY(launch_als_init(p, s));
+    p->user_init = false;
+    for (int it = 0; it < p->cfg.max_iters; ++it)
+      for (int n0 = 0; n0 < p->N; ++n0) RCP_TRY(launch_als_sweep(p, n0, s));
+  }
   p->als_done = true;
   if (lambda_host || fit_host || iters_host) {
     if (lambda_host)
@@ -447,6 +492,53 @@ rcp_status rcp_get_compressed_factors(rcp_plan_t p, double* const* At_dev, doubl
   if (lambda_dev)
     RCP_TRY(cudaMemcpyAsync(lambda_dev, p->lam, sizeof(double) * p->R, cudaMemcpyDeviceToDevice,
                             p->stream));
+  return RCP_OK;
+}
+
+rcp_status rcp_profile_enable(rcp_plan_t p, int32_t enable) {
+  if (!valid_plan(p)) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  if (enable && !p->prof) {
+    const int cap = 8192;
+    p->prof = new (std::nothrow) rcp_plan_s::ProfRec[cap];
+    if (!p->prof) return RCP_ENOMEM;
+    for (int k = 0; k < cap; ++k) {
+      if (cudaEventCreate(&p->prof[k].a) != cudaSuccess ||
+          cudaEventCreate(&p->prof[k].b) != cudaSuccess)
+        return RCP_ECUDA;
+      p->prof_cap = k + 1;
+    }
+  }
+  if (enable) {
+    p->prof_n = 0;
+    p->launch_base = launch_counter();
+  }
+  p->prof_on = enable != 0;
+  return RCP_OK;
+}
+
+rcp_status rcp_profile_read(rcp_plan_t p, int32_t kind, int32_t mode, int64_t* launches,
+                            double* total_ms) {
+  if (!valid_plan(p) || kind < 0 || kind >= RCP_KT_COUNT) return RCP_EINVAL;
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return RCP_ECUDA;
+  if (kind == RCP_KT_ALL) {
+    if (launches) *launches = launch_counter() - p->launch_base;
+    if (total_ms) *total_ms = 0.0;
+    return RCP_OK;
+  }
+  int64_t cnt = 0;
+  double ms = 0.0;
+  for (int k = 0; k < p->prof_n; ++k) {
+    const auto& r = p->prof[k];
+    if (r.kind != kind || (mode != 0 && r.mode != mode)) continue;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return RCP_ECUDA;
+    ms += t;
+    ++cnt;
+  }
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = ms;
   return RCP_OK;
 }
 

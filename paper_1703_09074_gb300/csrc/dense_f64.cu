@@ -205,21 +205,25 @@ cudaError_t launch_reduce(const double* part, int64_t nsplit, int64_t n, double*
   const unsigned gx = (unsigned)((n + threads - 1) / threads);
   if (nsplit > 2 * kRedChunks && tmp && tmp_elems >= kRedChunks * n) {
     const int64_t stride = (nsplit + kRedChunks - 1) / kRedChunks;
+    count_launches(2);
     k_reduce<<<dim3(gx, kRedChunks), threads, 0, s>>>(part, nsplit, n, 0, stride, tmp);
     k_reduce<<<dim3(gx, 1), threads, 0, s>>>(tmp, kRedChunks, n, 0, kRedChunks, out);
   } else {
+    count_launches(1);
     k_reduce<<<dim3(gx, 1), threads, 0, s>>>(part, nsplit, n, 0, nsplit, out);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStream_t s) {
+  count_launches(1);
   k_gram_pairs<<<l * (l + 1) / 2, 128, 0, s>>>(Y, I, l, Gp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
                         int round, int als_mode, cudaStream_t s) {
+  count_launches(1);
   k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode);
   return cudaGetLastError();
 }
@@ -228,6 +232,7 @@ cudaError_t launch_trmm(const double* Y, int64_t I, int l, const double* Rinv, d
                         const DevState* st, int only_if_extra, cudaStream_t s) {
   const int threads = 64;
   const unsigned grid = (unsigned)((I + threads - 1) / threads);
+  count_launches(1);
   if (l <= 16) k_trmm<16><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
   else if (l <= 32) k_trmm<32><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
   else if (l <= 48) k_trmm<48><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
@@ -250,12 +255,14 @@ cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv,
 }
 
 cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s) {
+  count_launches(1);
   k_sum_to<<<1, 256, 0, s>>>(part, n, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
                          cudaStream_t s) {
+  count_launches(2);
   k_sumsq_part<<<nblocks, 256, 0, s>>>(x, n, part);
   k_sum_to<<<1, 256, 0, s>>>(part, nblocks, dst);
   return cudaGetLastError();
@@ -263,6 +270,7 @@ cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, 
 
 cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  count_launches(1);
   if (src_dtype == RCP_DTYPE_F32)
     k_to_f64<float><<<grid, 256, 0, s>>>((const float*)src, n, dst);
   else

@@ -39,6 +39,7 @@ extern "C" rcp_status rcp_test_normals(uint64_t seed, uint32_t stream, uint32_t 
   const int threads = 256;
   const int64_t blocks = (count + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return RCP_EINVAL;
+  rcp::count_launches(1);
   rcp::k_normals<<<(unsigned)blocks, threads, 0, (cudaStream_t)cuda_stream>>>(
       seed, stream, purpose, first, count, out_dev, words_dev, f32_out_dev);
   return cudaGetLastError() == cudaSuccess ? RCP_OK : RCP_ECUDA;

@@ -102,6 +102,16 @@ struct rcp_plan_s {
   void* X_stage;
   double* A_stage[rcp::kMaxN];
   double* lam_stage;
+
+  // profiling: CUDA events around sweep launches, and the launch count
+  struct ProfRec {
+    int kind, mode;
+    cudaEvent_t a, b;
+  };
+  ProfRec* prof;
+  int prof_cap, prof_n;
+  bool prof_on;
+  int64_t launch_base;
 };
 
 namespace rcp {
@@ -154,6 +164,10 @@ __device__ __forceinline__ float4 normal_quad_f32(uint64_t seed, uint32_t stream
   sincospif(2.0f * (float)(x.w >> 8) * s24, &sb, &cb);
   return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
 }
+
+// Kernels launched by this library on the calling host thread (profiling only).
+int64_t& launch_counter();
+inline void count_launches(int k) { launch_counter() += k; }
 
 constexpr uint32_t kPurposeSketch = 0;
 constexpr uint32_t kPurposeAlsInit = 1;

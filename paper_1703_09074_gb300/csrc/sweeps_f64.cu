@@ -198,6 +198,7 @@ cudaError_t row_sweep_typed(const TIn* T, ModeView v, int l, uint64_t seed, uint
   dim3 grid((unsigned)nib, (unsigned)nsplit);
   KrDims k{};
   if (kr) k = *kr;
+  count_launches(1);
   if (src == kSrcOmega) {
     if (normpart)
       k_row_sweep<LMAX, TIn, kSrcOmega, true><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
@@ -231,6 +232,7 @@ template <int LMAX, typename TIn>
 cudaError_t col_sweep_typed(const TIn* T, ModeView v, int l, const double* Q, double* W,
                             double* gpart, int nblocks, cudaStream_t s) {
   const size_t smem_q = (size_t)kProjRows * LMAX * sizeof(double);
+  count_launches(1);
   if (gpart) {
     const size_t smem = smem_q + (size_t)kProjThreads * (LMAX + 1) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, true>,
