@@ -248,6 +248,41 @@ rcp_status rcp_test_normals(uint64_t seed, uint32_t stream, uint32_t purpose, in
                             int64_t count, double* out_dev, uint32_t* words_dev,
                             float* f32_out_dev, void* cuda_stream);
 
+/* Allocation-free mode-1 range finder.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * that runs where cudaMalloc is forbidden or unsafe (inside another
+ * framework's memory budget that is fixed at start-up, inside a region whose
+ * allocations the host application tracks and refuses, or on a teardown path),
+ * and therefore cannot create an rcp_plan, which allocates its workspace.
+ *
+ * It computes what rcp_sketch(plan, X, 1, Q_out) computes for a plan with
+ * power_iters = 0 and the FP64 path: Y = X_(1) Omega_1 with the Gaussian test
+ * matrix of seed `seed`, then Q_1 = the thin QR factor of Y with a positive
+ * diagonal of R (CholeskyQR2, shifted fallback).  X_dev: device tensor in the
+ * Kolda layout (in_dtype RCP_DTYPE_F32 or RCP_DTYPE_F64), dims[0..ndim-1] =
+ * I_1..I_N (host array).  Q_dev: device output, I_1 x l column-major FP64 with
+ * l = min(rank + oversample, I_1, I_2 ... I_N).  status_dev: optional device
+ * int32 that receives the device status (RCP_ENAN for non-finite input,
+ * RCP_ESINGULAR for a sketch even the shift cannot factor).  stream:
+ * cudaStream_t.  Asynchronous; calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * Scratch: one file-scope device array of 4 MiB (2^19 doubles) per GPU that
+ * loads the library, held until process exit, holding the split partials,
+ * the sketch and the QR scratch.  Limit: I_1 * l <= 259052 (at least one
+ * split must fit); larger sizes return RCP_EINVAL before any work.  The first
+ * call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * outside any stream capture.  Every call on a device shares the same array
+ * and leaves its contents behind (the status word is cleared at the start of
+ * each call; partials and sketch are fully overwritten), so calls that
+ * overlap on the GPU -- on different streams or host threads -- race and
+ * must be serialised by the caller. */
+rcp_status rcp_sketch_mode1_static(const void* X_dev, int32_t in_dtype, int32_t ndim,
+                                   const int64_t* dims, int32_t rank, int32_t oversample,
+                                   uint64_t seed, double* Q_dev, int32_t* status_dev,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,9 @@ SIGNATURES = {
     "rcp_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
     "rcp_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int64), DP]),
+    "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_uint64, P, P, P]),
     "rcp_test_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_int64, ctypes.c_int64, P, P, P, P]),
 }
