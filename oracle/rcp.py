@@ -49,7 +49,18 @@ def sketch_width(R, p, dims_current, n):
     return min(R + p, I_n, J_n)
 
 
-def range_finder(T, n, l, q, seed):
+def gaussian_test_matrix(seed, n, J, l, omega="f64"):
+    """Omega_n (J x l, element (j, c) = stream element j l + c).
+
+    omega="f64" draws the FP64 stream; omega="f32" evaluates, in FP64, the
+    values of the reduced-precision stream that the tensor-core sweeps use.
+    """
+    if omega == "f32":
+        return philox.normals_f32_stream(seed, n, philox.PURPOSE_SKETCH, J * l).reshape(J, l)
+    return philox.gaussian_matrix(seed, n, philox.PURPOSE_SKETCH, J, l)
+
+
+def range_finder(T, n, l, q, seed, omega="f64"):
     """Basis Q_n for mode n of the current tensor T (Algorithm 1 steps 4-12).
 
     Y = T_(n) Omega; q times: Q = qr+(Y), Z = qr+(T_(n)^T Q), Y = T_(n) Z;
@@ -57,7 +68,7 @@ def range_finder(T, n, l, q, seed):
     """
     Tn = unfold(T, n)
     J = Tn.shape[1]
-    Omega = philox.gaussian_matrix(seed, n, philox.PURPOSE_SKETCH, J, l)
+    Omega = gaussian_test_matrix(seed, n, J, l, omega)
     Y = Tn @ Omega
     for _ in range(q):
         Q, _r = qr_pos(Y)
@@ -67,13 +78,13 @@ def range_finder(T, n, l, q, seed):
     return Qn
 
 
-def compress(X, R, p, q, seed):
+def compress(X, R, p, q, seed, omega="f64"):
     """Algorithm 1: returns the compressed tensor B and the bases [Q_1, ..., Q_N]."""
     T = np.asarray(X, dtype=np.float64)
     Qs = []
     for n in range(1, T.ndim + 1):
         l = sketch_width(R, p, T.shape, n)
-        Qn = range_finder(T, n, l, q, seed)
+        Qn = range_finder(T, n, l, q, seed, omega)
         Qs.append(Qn)
         T = ttm(T, Qn.T, n)
     return T, Qs
@@ -152,10 +163,10 @@ def back_project(Qs, lam, factors):
     return lam, out
 
 
-def rcp_als(X, R, p, q, tol, max_iters, seed, init=None):
+def rcp_als(X, R, p, q, tol, max_iters, seed, init=None, omega="f64"):
     """The whole method: compress, ALS on B, recover.  Returns a dict of every intermediate."""
     X = np.asarray(X, dtype=np.float64)
-    B, Qs = compress(X, R, p, q, seed)
+    B, Qs = compress(X, R, p, q, seed, omega)
     lam_t, At, rho, iters, hist = cp_als(B, R, tol, max_iters, seed, init=init)
     lam, A = back_project(Qs, lam_t, At)
     nX2 = fro2(X)

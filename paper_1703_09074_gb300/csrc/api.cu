@@ -86,6 +86,8 @@ void free_plan(rcp_plan_t p) {
   cudaFree(p->M);
   cudaFree(p->lam);
   cudaFree(p->Bcore_own);
+  cudaFree(p->part32);
+  cudaFree(p->QT32);
   cudaFree(p->dstate);
   cudaFree(p->X_stage);
   cudaFree(p->lam_stage);
@@ -145,7 +147,8 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   if (cfg->oversample < 0 || cfg->power_iters < 0 || cfg->max_iters < 1) return RCP_EINVAL;
   if (!(cfg->tol >= 0.0)) return RCP_EINVAL;
   if (cfg->in_dtype != RCP_DTYPE_F64 && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
-  if (cfg->precision != RCP_PREC_F64) return RCP_EINVAL;
+  if (cfg->precision != RCP_PREC_F64 && cfg->precision != RCP_PREC_MIXED) return RCP_EINVAL;
+  if (cfg->precision == RCP_PREC_MIXED && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
   for (int n = 0; n < N; ++n)
     if (cfg->dims[n] < 1 || cfg->dims[n] > (1LL << 40)) return RCP_EINVAL;
   {
@@ -170,7 +173,7 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   p->N = N;
   p->R = cfg->rank;
   p->prec = cfg->precision;
-  p->work_elem = 8;
+  p->work_elem = cfg->precision == RCP_PREC_MIXED ? 4 : 8;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     return RCP_ECUDA;
@@ -246,6 +249,20 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   A(dalloc(&p->M, (int64_t)kMaxL * p->R));
   A(dalloc(&p->lam, p->R));
   A(dalloc(&p->dstate, 1));
+  if (p->prec == RCP_PREC_MIXED) {
+    p->tc1 = tc_mode1_supported(p->dims[0], p->l[0]);
+    int64_t p32 = 1;
+    if (p->tc1) {
+      int ns = 0;
+      int64_t jc = 0;
+      tc_rows_split(p->dims[0], p->view[0].J, p->nsm, &ns, &jc);
+      p32 = (int64_t)ns * p->dims[0] * p->l[0];
+    }
+    p->part32_elems = p32;
+    A(dalloc(&p->part32, p32));
+    A(dalloc(&p->QT32, (int64_t)2 * 64 * tc_ipad(Imax)));
+    A(dalloc(&p->Bcore_own, p->core_elems));
+  }
   if (cfg->flags & RCP_FLAG_HOST_STAGING) {
     int64_t nx = 1;
     for (int n = 0; n < N; ++n) nx *= p->dims[n];
@@ -276,15 +293,12 @@ int32_t rcp_width(rcp_plan_t plan, int32_t mode) {
   return plan->l[mode - 1];
 }
 
-rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) {
-  if (!valid_plan(p) || mode < 1 || mode > p->N) return RCP_EINVAL;
-  if (mode == 1 && !X) return RCP_EINVAL;
-  if (mode == 1) {
-    p->sketched = p->compressed = 0;  // a new decomposition starts at mode 1
-  } else if (p->compressed != mode - 1) {
-    return RCP_EORDER;
-  }
-  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+}  // extern "C"
+
+namespace {
+
+// Algorithm 1 steps (5)-(12) for mode n on the FP64 path.
+rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
   cudaStream_t s = p->stream;
   const int n0 = mode - 1;
   const ModeView v = p->view[n0];
@@ -294,12 +308,7 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
   double* W = mode_output(p, mode);
   const int nsplit = sketch_splits(v, p->nsm);
   const int64_t ny = v.I * l;
-
-  if (mode == 1) {
-    RCP_TRY(cudaMemsetAsync(p->dstate, 0, sizeof(DevState), s));
-    p->als_done = false;
-  }
-  // Y = T_(n) Omega_n (Algorithm 1 step 6); mode 1 also accumulates |X|^2
+  // Y = T_(n) Omega_n (step 6); mode 1 also accumulates |X|^2
   double* normpart = (mode == 1) ? p->normpart : nullptr;
   {
     Span sp(p, RCP_KT_SKETCH, mode);
@@ -312,7 +321,7 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
   RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
-  // q normalised power iterations (Algorithm 1 steps 7-11)
+  // q normalised power iterations (steps 7-11)
   const int ng = project_grid(v, p->nsm);
   const int npairs = l * (l + 1) / 2;
   for (int it = 0; it < p->cfg.power_iters; ++it) {
@@ -332,6 +341,102 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
     RCP_TRY(launch_trmm(p->Y, v.I, l, p->RWinv, p->Y, p->dstate, 0, s));
     RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
   }
+  return RCP_OK;
+}
+
+// Mixed-precision form: mode 1 on the tensor cores (TF32 operands, FP32
+// accumulation), later modes on FP32 CUDA cores; every QR in FP64.  The
+// power-iteration W is not normalised: Y = T_(n) W differs from T_(n) Z by an
+// upper-triangular right factor, which the QR of Y removes.
+rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
+  cudaStream_t s = p->stream;
+  const int n0 = mode - 1;
+  const ModeView v = p->view[n0];
+  const int l = p->l[n0];
+  const float* T = (const float*)(mode == 1 ? X : p->bufT[(mode - 2) % 2]);
+  float* W = (float*)mode_output(p, mode);
+  const int64_t ny = v.I * l;
+  if (mode == 1 && p->tc1) {
+    int nsplit = 0;
+    int64_t jchunk = 0;
+    tc_rows_split(v.I, v.J, p->nsm, &nsplit, &jchunk);
+    const int cgrid = tc_cols_grid(v.J, p->nsm);
+    {
+      Span sp(p, RCP_KT_SKETCH, mode);
+      RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, jchunk,
+                             p->part32, p->normpart, p->dstate, s));
+    }
+    RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
+    const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA
+    RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+    for (int it = 0; it < p->cfg.power_iters; ++it) {
+      RCP_TRY(launch_q_to_qt32(p->Y, v.I, l, p->QT32, s));
+      {
+        Span sp(p, RCP_KT_PROJECT, mode);
+        RCP_TRY(launch_tc_cols(T, v.I, v.J, l, p->QT32, W, false, p->dstate, cgrid, s));
+      }
+      {
+        Span sp(p, RCP_KT_APPLY, mode);
+        RCP_TRY(launch_tc_rows(T, v.I, v.J, l, 0, 0, W, nsplit, jchunk, p->part32, nullptr,
+                               p->dstate, s));
+      }
+      RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
+      RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+    }
+    return RCP_OK;
+  }
+  const int nsplit = sketch_splits(v, p->nsm);
+  double* normpart = (mode == 1) ? p->normpart : nullptr;
+  {
+    Span sp(p, RCP_KT_SKETCH, mode);
+    RCP_TRY(launch_sketch_f32(T, v, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, p->part,
+                              normpart, s));
+  }
+  RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
+  if (mode == 1) {
+    const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
+    RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
+  }
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  const int ng = project_grid(v, p->nsm);
+  for (int it = 0; it < p->cfg.power_iters; ++it) {
+    {
+      Span sp(p, RCP_KT_PROJECT, mode);
+      RCP_TRY(launch_project_f32(T, v, l, p->Y, W, ng, s));
+    }
+    {
+      Span sp(p, RCP_KT_APPLY, mode);
+      RCP_TRY(launch_sketch_f32(T, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
+    }
+    RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  }
+  return RCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) {
+  if (!valid_plan(p) || mode < 1 || mode > p->N) return RCP_EINVAL;
+  if (mode == 1 && !X) return RCP_EINVAL;
+  if (mode == 1) {
+    p->sketched = p->compressed = 0;  // a new decomposition starts at mode 1
+  } else if (p->compressed != mode - 1) {
+    return RCP_EORDER;
+  }
+  if (check_device(p) != RCP_OK) return RCP_ECUDA;
+  cudaStream_t s = p->stream;
+  const int n0 = mode - 1;
+  const int64_t ny = p->view[n0].I * p->l[n0];
+  if (mode == 1) {
+    RCP_TRY(cudaMemsetAsync(p->dstate, 0, sizeof(DevState), s));
+    p->als_done = false;
+  }
+  const rcp_status st = p->prec == RCP_PREC_MIXED ? sketch_mixed(p, X, mode) : sketch_f64(p, X, mode);
+  if (st != RCP_OK) return st;
   RCP_TRY(cudaMemcpyAsync(p->Q[n0], p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
   if (Q_out)
     RCP_TRY(cudaMemcpyAsync(Q_out, p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
@@ -345,15 +450,35 @@ rcp_status rcp_compress(rcp_plan_t p, const void* X, int32_t mode) {
   if (p->sketched != mode || p->compressed != mode - 1) return RCP_EORDER;
   if (check_device(p) != RCP_OK) return RCP_ECUDA;
   const int n0 = mode - 1;
-  int dt = 0;
-  const void* T = mode_input(p, X, mode, &dt);
-  {
+  const ModeView& v = p->view[n0];
+  if (p->prec == RCP_PREC_MIXED) {
+    const float* T = (const float*)(mode == 1 ? X : p->bufT[(mode - 2) % 2]);
+    float* out = (float*)mode_output(p, mode);
     Span sp(p, RCP_KT_TTM, mode);
-    RCP_TRY(launch_project_f64(T, dt, p->view[n0], p->l[n0], p->Q[n0], mode_output(p, mode),
-                               nullptr, project_grid(p->view[n0], p->nsm), p->stream));
+    if (mode == 1 && p->tc1) {
+      RCP_TRY(launch_q_to_qt32(p->Q[0], v.I, p->l[0], p->QT32, p->stream));
+      RCP_TRY(launch_tc_cols(T, v.I, v.J, p->l[0], p->QT32, out, true, p->dstate,
+                             tc_cols_grid(v.J, p->nsm), p->stream));
+    } else {
+      RCP_TRY(launch_project_f32(T, v, p->l[n0], p->Q[n0], out, project_grid(v, p->nsm), p->stream));
+    }
+  } else {
+    int dt = 0;
+    const void* T = mode_input(p, X, mode, &dt);
+    Span sp(p, RCP_KT_TTM, mode);
+    RCP_TRY(launch_project_f64(T, dt, v, p->l[n0], p->Q[n0], mode_output(p, mode), nullptr,
+                               project_grid(v, p->nsm), p->stream));
   }
   p->compressed = mode;
-  if (mode == p->N) p->Bcore64 = mode_output(p, mode);
+  if (mode == p->N) {
+    if (p->prec == RCP_PREC_MIXED) {
+      RCP_TRY(launch_to_f64(mode_output(p, mode), RCP_DTYPE_F32, p->core_elems, p->Bcore_own,
+                            p->stream));
+      p->Bcore64 = p->Bcore_own;
+    } else {
+      p->Bcore64 = mode_output(p, mode);
+    }
+  }
   return RCP_OK;
 }
 

@@ -98,6 +98,12 @@ struct rcp_plan_s {
   int compressed;  // last mode compressed (0 = none)
   bool als_done;
 
+  // mixed-precision form
+  bool tc1;                  // mode 1 runs on the tensor cores
+  float* part32;             // FP32 split partials of the tensor-core row sweep
+  int64_t part32_elems;
+  float* QT32;               // Q^T in FP32, padded to NP x Ipad
+
   // host staging (rcp_decompose_host)
   void* X_stage;
   double* A_stage[rcp::kMaxN];
@@ -183,10 +189,30 @@ cudaError_t launch_sketch_f64(const void* T, int in_dtype, ModeView v, int l, ui
                               double* normpart, cudaStream_t s);
 cudaError_t launch_project_f64(const void* T, int in_dtype, ModeView v, int l, const double* Q,
                                double* W, double* gpart, int nblocks, cudaStream_t s);
+cudaError_t launch_sketch_f32(const float* T, ModeView v, int l, uint64_t seed, uint32_t stream_id,
+                              const float* W, int nsplit, double* part, double* normpart,
+                              cudaStream_t s);
+cudaError_t launch_project_f32(const float* T, ModeView v, int l, const double* Q, float* W,
+                               int nblocks, cudaStream_t s);
 cudaError_t launch_mttkrp_f64(const double* B, ModeView v, int R, const KrDims& kr, int nsplit,
                               double* part, cudaStream_t s);
 int project_grid(const ModeView& v, int nsm);
 int sketch_splits(const ModeView& v, int nsm);
+
+// Tensor-core mode-1 sweeps of the mixed-precision form (tc_sweeps.cu).
+bool tc_mode1_supported(int64_t I, int l);
+int tc_np(int l);
+int64_t tc_ipad(int64_t I);
+void tc_rows_split(int64_t I, int64_t J, int nsm, int* nsplit, int64_t* jchunk);
+int tc_cols_grid(int64_t J, int nsm);
+cudaError_t launch_tc_rows(const float* X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
+                           const float* WT, int nsplit, int64_t jchunk, float* part,
+                           double* normpart, DevState* st, cudaStream_t s);
+cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const float* QT, float* out,
+                           bool ttm, DevState* st, int grid, cudaStream_t s);
+cudaError_t launch_q_to_qt32(const double* Q, int64_t I, int l, float* QT, cudaStream_t s);
+cudaError_t launch_reduce_f32(const float* part, int64_t nsplit, int64_t n, double* out,
+                              cudaStream_t s);
 
 // Small dense FP64 linear algebra (dense_f64.cu).
 cudaError_t launch_reduce(const double* part, int64_t nsplit, int64_t n, double* out, double* tmp,

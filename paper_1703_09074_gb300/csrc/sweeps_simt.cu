@@ -1,4 +1,5 @@
-// FP64 sweeps over the working tensor T_n (plain method, CUDA cores).
+// Sweeps over the working tensor T_n on the CUDA cores: FP64 (the plain
+// method) and FP32 (later modes of the mixed-precision form).
 //
 // Row sweep   : P[i, c] = sum_j T_(n)[i, j] V[j, c]          (split over j)
 //   V = Omega_n  -> the sketch Y = T_(n) Omega_n             (Algorithm 1 step 6, Eq. sampleMatrix)
@@ -20,15 +21,12 @@ constexpr int kProjRows = 32;     // rows of Q staged per step of the column swe
 
 enum { kSrcOmega = 0, kSrcW = 1, kSrcKr = 2 };
 
-template <typename T>
-__device__ __forceinline__ double ld_f64(const T* p) { return (double)__ldg(p); }
-
-template <int LMAX, typename TIn, int SRC, bool NORM>
+template <int LMAX, typename TIn, typename TA, int SRC, bool NORM>
 __global__ void __launch_bounds__(256)
 k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, uint64_t seed,
-            uint32_t sid, const double* __restrict__ W, KrDims kr, int64_t jchunk,
+            uint32_t sid, const TA* __restrict__ W, KrDims kr, int64_t jchunk,
             double* __restrict__ part, double* __restrict__ normpart) {
-  __shared__ double Vs[kRowTile][LMAX];
+  __shared__ TA Vs[kRowTile][LMAX];
   __shared__ int64_t offs[kRowTile];
   const int tid = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * rows_per_cta + tid;
@@ -36,12 +34,12 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
   const int64_t j0 = (int64_t)blockIdx.y * jchunk;
   const int64_t j1 = min(v.J, j0 + jchunk);
 
-  double acc[LMAX];
+  TA acc[LMAX];
 #pragma unroll
-  for (int c = 0; c < LMAX; ++c) acc[c] = 0.0;
+  for (int c = 0; c < LMAX; ++c) acc[c] = (TA)0;
   double nrm = 0.0;
 
-  for (int k = tid; k < kRowTile * LMAX; k += blockDim.x) (&Vs[0][0])[k] = 0.0;
+  for (int k = tid; k < kRowTile * LMAX; k += blockDim.x) (&Vs[0][0])[k] = (TA)0;
   __syncthreads();
 
   for (int64_t jt = j0; jt < j1; jt += kRowTile) {
@@ -50,16 +48,29 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
       const int64_t j = jt + tid;
       offs[tid] = (j % v.L) + v.L * v.I * (j / v.L);
     }
-    if (SRC == kSrcOmega) {
-      // Omega_n[j, c] is element e = j * l + c of the stream; pairs g = e / 2.
+    if (SRC == kSrcOmega && sizeof(TA) == 8) {
+      // Omega_n[j, c] is element e = j * l + c of the FP64 stream; pairs g = e / 2.
       const int64_t e0 = jt * l, e1 = (jt + nj) * (int64_t)l;
       const int64_t g0 = e0 >> 1, g1 = (e1 - 1) >> 1;
       for (int64_t g = g0 + tid; g <= g1; g += blockDim.x) {
         const double2 z = normal_pair_f64(seed, sid, kPurposeSketch, (uint64_t)g);
         int64_t e = 2 * g;
-        if (e >= e0) Vs[e / l - jt][e % l] = z.x;
+        if (e >= e0) Vs[e / l - jt][e % l] = (TA)z.x;
         ++e;
-        if (e < e1) Vs[e / l - jt][e % l] = z.y;
+        if (e < e1) Vs[e / l - jt][e % l] = (TA)z.y;
+      }
+    } else if (SRC == kSrcOmega) {
+      // reduced-precision stream: quads g = e / 4
+      const int64_t e0 = jt * l, e1 = (jt + nj) * (int64_t)l;
+      const int64_t g0 = e0 >> 2, g1 = (e1 - 1) >> 2;
+      for (int64_t g = g0 + tid; g <= g1; g += blockDim.x) {
+        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)g);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t e = 4 * g + q;
+          if (e >= e0 && e < e1) Vs[e / l - jt][e % l] = (TA)zz[q];
+        }
       }
     } else if (SRC == kSrcW) {
       for (int k = tid; k < nj * l; k += blockDim.x) {
@@ -80,14 +91,14 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
           jr /= d;
           prod *= kr.A[m][im + (int64_t)d * r];
         }
-        Vs[jj][r] = prod;
+        Vs[jj][r] = (TA)prod;
       }
     }
     __syncthreads();
     if (row_ok) {
       for (int jj = 0; jj < nj; ++jj) {
-        const double x = ld_f64(T + offs[jj] + v.L * i);
-        if (NORM) nrm = fma(x, x, nrm);
+        const TA x = (TA)__ldg(T + offs[jj] + v.L * i);
+        if (NORM) nrm = fma((double)x, (double)x, nrm);
 #pragma unroll
         for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Vs[jj][c], acc[c]);
       }
@@ -97,7 +108,7 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
   if (row_ok) {
 #pragma unroll
     for (int c = 0; c < LMAX; ++c)
-      if (c < l) part[((int64_t)blockIdx.y * l + c) * v.I + i] = acc[c];
+      if (c < l) part[((int64_t)blockIdx.y * l + c) * v.I + i] = (double)acc[c];
   }
   if (NORM) {
     __shared__ double red[256];
@@ -111,12 +122,12 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
   }
 }
 
-template <int LMAX, typename TIn, bool GRAM>
+template <int LMAX, typename TIn, typename TA, bool GRAM>
 __global__ void __launch_bounds__(kProjThreads)
 k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
-            double* __restrict__ W, double* __restrict__ gpart) {
+            TA* __restrict__ W, double* __restrict__ gpart) {
   extern __shared__ double sm[];
-  double* Qs = sm;                                  // kProjRows x LMAX
+  TA* Qs = (TA*)sm;                                 // kProjRows x LMAX
   double* Ws = sm + kProjRows * LMAX;               // kProjThreads x (LMAX + 1), GRAM only
   __shared__ unsigned short pairs[kMaxL * (kMaxL + 1) / 2];
   constexpr int kSlots = (LMAX * (LMAX + 1) / 2 + kProjThreads - 1) / kProjThreads;
@@ -135,20 +146,20 @@ k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restri
     const bool ok = j < v.J;
     const int64_t a = ok ? j % v.L : 0, b = ok ? j / v.L : 0;
     const int64_t base = a + v.L * v.I * b;
-    double acc[LMAX];
+    TA acc[LMAX];
 #pragma unroll
-    for (int c = 0; c < LMAX; ++c) acc[c] = 0.0;
+    for (int c = 0; c < LMAX; ++c) acc[c] = (TA)0;
     for (int64_t i0 = 0; i0 < v.I; i0 += kProjRows) {
       const int ni = (int)min((int64_t)kProjRows, v.I - i0);
       __syncthreads();
       for (int k = tid; k < kProjRows * LMAX; k += kProjThreads) {
         const int ii = k / LMAX, c = k - ii * LMAX;
-        Qs[k] = (ii < ni && c < l) ? Q[(i0 + ii) + v.I * c] : 0.0;
+        Qs[k] = (ii < ni && c < l) ? (TA)Q[(i0 + ii) + v.I * c] : (TA)0;
       }
       __syncthreads();
       if (ok) {
         for (int ii = 0; ii < ni; ++ii) {
-          const double x = ld_f64(T + base + v.L * (i0 + ii));
+          const TA x = (TA)__ldg(T + base + v.L * (i0 + ii));
 #pragma unroll
           for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Qs[ii * LMAX + c], acc[c]);
         }
@@ -161,7 +172,7 @@ k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restri
     }
     if (GRAM) {
 #pragma unroll
-      for (int c = 0; c < LMAX; ++c) Ws[tid * (LMAX + 1) + c] = ok ? acc[c] : 0.0;
+      for (int c = 0; c < LMAX; ++c) Ws[tid * (LMAX + 1) + c] = ok ? (double)acc[c] : 0.0;
       __syncthreads();
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
@@ -187,9 +198,9 @@ k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restri
 
 int lmax_bucket(int l) { return l <= 16 ? 16 : l <= 32 ? 32 : l <= 48 ? 48 : 64; }
 
-template <int LMAX, typename TIn>
+template <int LMAX, typename TIn, typename TA>
 cudaError_t row_sweep_typed(const TIn* T, ModeView v, int l, uint64_t seed, uint32_t sid,
-                            const double* W, const KrDims* kr, int src, int nsplit, double* part,
+                            const TA* W, const KrDims* kr, int src, int nsplit, double* part,
                             double* normpart, cudaStream_t s) {
   const int64_t nib = (v.I + 255) / 256;
   const int64_t rpc = (v.I + nib - 1) / nib;
@@ -201,24 +212,24 @@ cudaError_t row_sweep_typed(const TIn* T, ModeView v, int l, uint64_t seed, uint
   count_launches(1);
   if (src == kSrcOmega) {
     if (normpart)
-      k_row_sweep<LMAX, TIn, kSrcOmega, true><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
-                                                                     jchunk, part, normpart);
+      k_row_sweep<LMAX, TIn, TA, kSrcOmega, true><<<grid, threads, 0, s>>>(
+          T, v, rpc, l, seed, sid, W, k, jchunk, part, normpart);
     else
-      k_row_sweep<LMAX, TIn, kSrcOmega, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
-                                                                      jchunk, part, normpart);
+      k_row_sweep<LMAX, TIn, TA, kSrcOmega, false><<<grid, threads, 0, s>>>(
+          T, v, rpc, l, seed, sid, W, k, jchunk, part, normpart);
   } else if (src == kSrcW) {
-    k_row_sweep<LMAX, TIn, kSrcW, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
-                                                                jchunk, part, normpart);
+    k_row_sweep<LMAX, TIn, TA, kSrcW, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                    jchunk, part, normpart);
   } else {
-    k_row_sweep<LMAX, TIn, kSrcKr, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
-                                                                 jchunk, part, normpart);
+    k_row_sweep<LMAX, TIn, TA, kSrcKr, false><<<grid, threads, 0, s>>>(T, v, rpc, l, seed, sid, W, k,
+                                                                     jchunk, part, normpart);
   }
   return cudaGetLastError();
 }
 
-template <typename TIn>
+template <typename TIn, typename TA>
 cudaError_t row_sweep_any(const TIn* T, ModeView v, int l, uint64_t seed, uint32_t sid,
-                          const double* W, const KrDims* kr, int src, int nsplit, double* part,
+                          const TA* W, const KrDims* kr, int src, int nsplit, double* part,
                           double* normpart, cudaStream_t s) {
   switch (lmax_bucket(l)) {
     case 16: return row_sweep_typed<16>(T, v, l, seed, sid, W, kr, src, nsplit, part, normpart, s);
@@ -228,25 +239,25 @@ cudaError_t row_sweep_any(const TIn* T, ModeView v, int l, uint64_t seed, uint32
   }
 }
 
-template <int LMAX, typename TIn>
-cudaError_t col_sweep_typed(const TIn* T, ModeView v, int l, const double* Q, double* W,
+template <int LMAX, typename TIn, typename TA>
+cudaError_t col_sweep_typed(const TIn* T, ModeView v, int l, const double* Q, TA* W,
                             double* gpart, int nblocks, cudaStream_t s) {
   const size_t smem_q = (size_t)kProjRows * LMAX * sizeof(double);
   count_launches(1);
   if (gpart) {
     const size_t smem = smem_q + (size_t)kProjThreads * (LMAX + 1) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, true>,
+    cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, TA, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_col_sweep<LMAX, TIn, true><<<nblocks, kProjThreads, smem, s>>>(T, v, l, Q, W, gpart);
+    k_col_sweep<LMAX, TIn, TA, true><<<nblocks, kProjThreads, smem, s>>>(T, v, l, Q, W, gpart);
   } else {
-    k_col_sweep<LMAX, TIn, false><<<nblocks, kProjThreads, smem_q, s>>>(T, v, l, Q, W, gpart);
+    k_col_sweep<LMAX, TIn, TA, false><<<nblocks, kProjThreads, smem_q, s>>>(T, v, l, Q, W, gpart);
   }
   return cudaGetLastError();
 }
 
-template <typename TIn>
-cudaError_t col_sweep_any(const TIn* T, ModeView v, int l, const double* Q, double* W,
+template <typename TIn, typename TA>
+cudaError_t col_sweep_any(const TIn* T, ModeView v, int l, const double* Q, TA* W,
                           double* gpart, int nblocks, cudaStream_t s) {
   switch (lmax_bucket(l)) {
     case 16: return col_sweep_typed<16>(T, v, l, Q, W, gpart, nblocks, s);
@@ -285,9 +296,17 @@ cudaError_t launch_sketch_f64(const void* T, int in_dtype, ModeView v, int l, ui
                        normpart, s);
 }
 
+cudaError_t launch_sketch_f32(const float* T, ModeView v, int l, uint64_t seed, uint32_t stream_id,
+                              const float* W, int nsplit, double* part, double* normpart,
+                              cudaStream_t s) {
+  const int src = W ? kSrcW : kSrcOmega;
+  return row_sweep_any(T, v, l, seed, stream_id, W, nullptr, src, nsplit, part, normpart, s);
+}
+
 cudaError_t launch_mttkrp_f64(const double* B, ModeView v, int R, const KrDims& kr, int nsplit,
                               double* part, cudaStream_t s) {
-  return row_sweep_any(B, v, R, 0, 0, nullptr, &kr, kSrcKr, nsplit, part, nullptr, s);
+  return row_sweep_any(B, v, R, 0, 0, (const double*)nullptr, &kr, kSrcKr, nsplit, part, nullptr,
+                       s);
 }
 
 cudaError_t launch_project_f64(const void* T, int in_dtype, ModeView v, int l, const double* Q,
@@ -295,6 +314,11 @@ cudaError_t launch_project_f64(const void* T, int in_dtype, ModeView v, int l, c
   if (in_dtype == RCP_DTYPE_F32)
     return col_sweep_any((const float*)T, v, l, Q, W, gpart, nblocks, s);
   return col_sweep_any((const double*)T, v, l, Q, W, gpart, nblocks, s);
+}
+
+cudaError_t launch_project_f32(const float* T, ModeView v, int l, const double* Q, float* W,
+                               int nblocks, cudaStream_t s) {
+  return col_sweep_any(T, v, l, Q, W, (double*)nullptr, nblocks, s);
 }
 
 }  // namespace rcp

@@ -1,0 +1,478 @@
+// Tensor-core sweeps over X for mode 1 of the mixed-precision form
+// (tcgen05 kind::tf32, FP32 accumulation in tensor memory).  Mode 1 reads the
+// whole input X, 2q + 2 times, so these sweeps set the end-to-end time.
+//
+// Precision: every FP32 operand is split into hi = its TF32 truncation and
+// lo = the exact remainder, and each product is formed as
+// hi*hi + hi*lo + lo*hi (three MMAs), which keeps about 21 bits.  Plain TF32
+// (10 fraction bits) loses the weak signal directions of unfoldings whose
+// spectrum spans two decades (factor congruence 0.5 at R = 20).
+//
+// X_(1) is I x J with columns contiguous (column j = the mode-1 fibre at j).
+//
+// Row sweep (k_tc_rows): P = X_(1) V with V = Omega_1 (Algorithm 1 step 6,
+//   Eq. sampleMatrix; Gaussian entries from the reduced-precision counter
+//   stream) or V = W of a power iteration (step 10).  Tensor-core problem:
+//   M = I (rows i), N = l, K = J.  The A operand needs K (= j) contiguous, the
+//   transpose of X's layout, so each thread loads one row i for 32 columns j
+//   (coalesced across the warp) and writes it as one 128-byte swizzled row.
+//   Each CTA owns 128 rows and a contiguous range of j (split over J).  Two
+//   shared-memory stages and two register buffers: the loads of chunks k + 1
+//   and k + 2 are in flight while the MMAs of chunk k run.
+// Column sweep (k_tc_cols): W = X_(1)^T Q (Algorithm 1 step 9) or the mode
+//   product T_2 = X x_1 Q_1^T (step 13).  M = J (128 columns j per block),
+//   N = l, K = I: K is X's contiguous direction, so 16-byte loads go straight
+//   into the swizzled tile.  Persistent CTAs walk j-blocks.
+#include "rcp_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace rcp {
+namespace {
+
+constexpr int kATile = 16384;  // 128 rows x 128 bytes
+constexpr long long kWaitBudget = 1LL << 31;  // clock cycles (about 1 s)
+
+// FP32 = hi + lo with hi = the value truncated to TF32 (10 fraction bits) and
+// lo = the exact remainder; hi * hi + hi * lo + lo * hi keeps about 21 bits.
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// Stage layout shared by both kernels: [A hi | A lo | B hi | B lo], each tile
+// K-major, 128-byte swizzled, 1024-byte aligned.
+template <int NP>
+struct Stage {
+  static constexpr int kA = kATile;
+  static constexpr int kB = NP * 128;
+  static constexpr int kBytes = 2 * kA + 2 * kB;
+  static constexpr int kSmem = 2 * kBytes + 1024;
+};
+
+__device__ __forceinline__ void issue_3xtf32(uint32_t d, uint32_t ahi, uint32_t alo, uint32_t bhi,
+                                             uint32_t blo, uint32_t idesc, bool first) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t o = 32u * k;
+    tc::mma_tf32(d, tc::desc_kmajor_sw128(ahi + o), tc::desc_kmajor_sw128(bhi + o), idesc,
+                 (first && k == 0) ? 0u : 1u);
+    tc::mma_tf32(d, tc::desc_kmajor_sw128(ahi + o), tc::desc_kmajor_sw128(blo + o), idesc, 1u);
+    tc::mma_tf32(d, tc::desc_kmajor_sw128(alo + o), tc::desc_kmajor_sw128(bhi + o), idesc, 1u);
+  }
+}
+
+// Row sweep, one M = 128 block of rows per CTA (128 threads, thread = row).
+template <int NP, int SRC, bool NORM>
+__global__ void __launch_bounds__(128)
+k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
+          const float* __restrict__ WT, int64_t jchunk, float* __restrict__ part,
+          double* __restrict__ normpart, DevState* st) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tbase_sh;
+  __shared__ int abort_sh;
+  __shared__ double red[4];
+  using S = Stage<NP>;
+  constexpr uint32_t NCOLS = NP;
+  constexpr uint32_t IDESC = tc::idesc_tf32(128, NP);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * 128;
+  const int64_t jb = (int64_t)blockIdx.y * jchunk;
+  const int64_t je = min(J, jb + jchunk);
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    abort_sh = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase_sh, NCOLS);
+  for (int k = tid; k < 2 * 2 * NP * 32; k += 128) {  // B rows c >= l stay zero
+    const int s = k / (2 * NP * 32), e = k % (2 * NP * 32);
+    *(float*)(sm + s * S::kBytes + 2 * S::kA + 4 * e) = 0.0f;
+  }
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
+  const uint32_t tbase = tbase_sh;
+
+  const int64_t row = i0 + tid;
+  const bool row_ok = row < I;
+  const int nk = (int)((je - jb + 31) / 32);
+  float xa[32], xb[32];
+  float nrm = 0.0f;
+  uint32_t par0 = 0, par1 = 0;
+
+  auto load = [&](float (&xr)[32], int kc) {
+    const int64_t j0 = jb + 32LL * kc;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int64_t j = j0 + jj;
+      xr[jj] = (row_ok && j < je) ? __ldg(X + row + I * j) : 0.0f;
+    }
+  };
+  auto put_b = [&](uint8_t* Bh, uint8_t* Bl, int c, int jj, float v) {
+    const float h = tf32_hi(v);
+    const uint32_t off = tc::sw128_offset((uint32_t)c, (uint32_t)jj);
+    *(float*)(Bh + off) = h;
+    *(float*)(Bl + off) = v - h;
+  };
+  // one 32-column chunk: stage it, prefetch chunk kc + 2 into the same registers, issue MMAs
+  auto step = [&](float (&xr)[32], int kc) -> bool {
+    const int s = kc & 1;
+    uint8_t* Ah = sm + s * S::kBytes;
+    uint8_t* Al = Ah + S::kA;
+    uint8_t* Bh = Al + S::kA;
+    uint8_t* Bl = Bh + S::kB;
+    if (kc >= 2) {
+      const uint32_t par = s ? par1 : par0;
+      if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) atomicExch(&abort_sh, 1);
+      if (s) par1 ^= 1; else par0 ^= 1;
+    }
+    const uint32_t rr = (uint32_t)tid;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float4 h, lo;
+      h.x = tf32_hi(xr[4 * c]);     lo.x = xr[4 * c] - h.x;
+      h.y = tf32_hi(xr[4 * c + 1]); lo.y = xr[4 * c + 1] - h.y;
+      h.z = tf32_hi(xr[4 * c + 2]); lo.z = xr[4 * c + 2] - h.z;
+      h.w = tf32_hi(xr[4 * c + 3]); lo.w = xr[4 * c + 3] - h.w;
+      if (NORM)
+        nrm += xr[4 * c] * xr[4 * c] + xr[4 * c + 1] * xr[4 * c + 1] +
+               xr[4 * c + 2] * xr[4 * c + 2] + xr[4 * c + 3] * xr[4 * c + 3];
+      const uint32_t off = rr * 128 + ((((uint32_t)c ^ (rr & 7u)) & 7u) << 4);
+      *(float4*)(Ah + off) = h;
+      *(float4*)(Al + off) = lo;
+    }
+    if (kc + 2 < nk) load(xr, kc + 2);
+    const int64_t j0 = jb + 32LL * kc;
+    if (SRC == 0) {
+      // Omega_1[j, c] = element e = j l + c of the reduced-precision stream
+      const int64_t e0 = j0 * l, e1 = (j0 + 32) * (int64_t)l;
+      const int64_t g0 = e0 >> 2, g1 = (e1 - 1) >> 2;
+      for (int64_t g = g0 + tid; g <= g1; g += 128) {
+        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)g);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t e = 4 * g + q;
+          if (e < e0 || e >= e1) continue;
+          const int64_t j = e / l;
+          put_b(Bh, Bl, (int)(e - j * l), (int)(j - j0), (j < je) ? zz[q] : 0.0f);
+        }
+      }
+    } else {
+      for (int k = tid; k < l * 32; k += 128) {
+        const int c = k >> 5, jj = k & 31;
+        const int64_t j = j0 + jj;
+        put_b(Bh, Bl, c, jj, (j < je) ? __ldg(WT + (int64_t)c * J + j) : 0.0f);
+      }
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (abort_sh) return false;
+    if (tid == 0) {
+      tc::tc_fence_after_sync();
+      issue_3xtf32(tbase, tc::smem_u32(Ah), tc::smem_u32(Al), tc::smem_u32(Bh), tc::smem_u32(Bl),
+                   IDESC, kc == 0);
+      tc::mma_commit(&mbar[s]);
+    }
+    return true;
+  };
+
+  if (nk > 0) load(xa, 0);
+  if (nk > 1) load(xb, 1);
+  bool ok = true;
+  for (int kc = 0; kc < nk && ok; kc += 2) {
+    ok = step(xa, kc);
+    if (ok && kc + 1 < nk) ok = step(xb, kc + 1);
+  }
+  for (int kc = (nk >= 2 ? nk - 2 : 0); kc < nk && ok; ++kc) {
+    const int s = kc & 1;
+    const uint32_t par = s ? par1 : par0;
+    if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) ok = false;
+    if (s) par1 ^= 1; else par0 ^= 1;
+  }
+  tc::tc_fence_after_sync();
+  if (!ok && tid == 0) set_status(st, RCP_ETIMEOUT);
+
+  {
+    const int64_t r = i0 + warp * 32 + lane;
+#pragma unroll
+    for (int cg = 0; cg < NP / 32; ++cg) {
+      float v[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const int col = cg * 32 + k;
+        if (col < l && r < I)
+          part[((int64_t)blockIdx.y * l + col) * I + r] = (ok && nk > 0) ? v[k] : 0.0f;
+      }
+    }
+  }
+  if (NORM) {
+    double d = (double)nrm;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if (lane == 0) red[warp] = d;
+  }
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  if (NORM && tid == 0) normpart[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] =
+      red[0] + red[1] + red[2] + red[3];
+  if (warp == 0) tc::tmem_dealloc(tbase, NCOLS);
+}
+
+// out = X_(1)^T Q for every j: TTM ? row-major J x l (the Kolda layout of T_2)
+//                                     : l x J (the power-iteration W, transposed).
+// Two tensor-memory accumulators: the epilogue of j-block b runs while the
+// MMAs of block b + 1 are queued.
+template <int NP, bool TTM>
+__global__ void __launch_bounds__(128)
+k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad,
+          const float* __restrict__ QTh, const float* __restrict__ QTl, float* __restrict__ out,
+          DevState* st) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t mbar[3];  // two stages + accumulator ready
+  __shared__ uint32_t tbase_sh;
+  __shared__ int abort_sh;
+  using S = Stage<NP>;
+  constexpr uint32_t NCOLS = 2 * NP;
+  constexpr uint32_t IDESC = tc::idesc_tf32(128, NP);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) tc::mbar_init(&mbar[k], 1);
+    abort_sh = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase_sh, NCOLS);
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
+  const uint32_t tbase = tbase_sh;
+
+  const int nkc = (int)(Ipad / 32);
+  const int64_t njb = (J + 127) / 128;
+  const int64_t my_blocks = (njb > blockIdx.x) ? (njb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t total = my_blocks * nkc;
+  const int c16 = tid & 7, r0 = tid >> 3;
+  float4 xa[8], xb[8];
+  uint32_t par0 = 0, par1 = 0, pacc = 0;
+
+  auto load = [&](float4 (&xv)[8], int64_t g) {
+    const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
+    const int kc = (int)(g % nkc);
+    const int64_t i = 32LL * kc + 4 * c16;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const int64_t j = jblk * 128 + r0 + 16 * p;
+      xv[p] = (j < J && i < I) ? __ldg((const float4*)(X + j * I + i)) : make_float4(0, 0, 0, 0);
+    }
+  };
+  auto epilogue = [&](int64_t blk_local) -> bool {
+    bool good = tc::mbar_wait(&mbar[2], pacc, kWaitBudget);
+    pacc ^= 1;
+    tc::tc_fence_after_sync();
+    const int64_t jblk = blockIdx.x + blk_local * gridDim.x;
+    const int64_t j = jblk * 128 + warp * 32 + lane;
+    const uint32_t acc = tbase + (uint32_t)((blk_local & 1) * NP);
+#pragma unroll
+    for (int cg = 0; cg < NP / 32; ++cg) {
+      float v[32];
+      tc::tmem_ld32(acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), v);
+      if (j < J && good) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int c = cg * 32 + k;
+          if (c < l) {
+            if (TTM) out[j * l + c] = v[k];
+            else out[(int64_t)c * J + j] = v[k];
+          }
+        }
+      }
+    }
+    tc::tc_fence_before_sync();
+    return good;
+  };
+  auto step = [&](float4 (&xv)[8], int64_t g) -> bool {
+    const int s = (int)(g & 1);
+    const int kc = (int)(g % nkc);
+    const int64_t blk = g / nkc;
+    uint8_t* Ah = sm + s * S::kBytes;
+    uint8_t* Al = Ah + S::kA;
+    uint8_t* Bh = Al + S::kA;
+    uint8_t* Bl = Bh + S::kB;
+    if (g >= 2) {
+      const uint32_t par = s ? par1 : par0;
+      if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) atomicExch(&abort_sh, 1);
+      if (s) par1 ^= 1; else par0 ^= 1;
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const uint32_t r = (uint32_t)(r0 + 16 * p);
+      const uint32_t off = r * 128 + ((((uint32_t)c16 ^ (r & 7u)) & 7u) << 4);
+      float4 h, lo;
+      h.x = tf32_hi(xv[p].x); lo.x = xv[p].x - h.x;
+      h.y = tf32_hi(xv[p].y); lo.y = xv[p].y - h.y;
+      h.z = tf32_hi(xv[p].z); lo.z = xv[p].z - h.z;
+      h.w = tf32_hi(xv[p].w); lo.w = xv[p].w - h.w;
+      *(float4*)(Ah + off) = h;
+      *(float4*)(Al + off) = lo;
+    }
+    if (g + 2 < total) load(xv, g + 2);
+    for (int k = tid; k < NP * 8; k += 128) {
+      const int c = k >> 3, cc = k & 7;
+      const uint32_t off = c * 128 + ((((uint32_t)cc ^ ((uint32_t)c & 7u)) & 7u) << 4);
+      const int64_t src = (int64_t)c * Ipad + 32LL * kc + 4 * cc;
+      *(float4*)(Bh + off) = __ldg((const float4*)(QTh + src));
+      *(float4*)(Bl + off) = __ldg((const float4*)(QTl + src));
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (abort_sh) return false;
+    if (tid == 0) {
+      tc::tc_fence_after_sync();
+      issue_3xtf32(tbase + (uint32_t)((blk & 1) * NP), tc::smem_u32(Ah), tc::smem_u32(Al),
+                   tc::smem_u32(Bh), tc::smem_u32(Bl), IDESC, kc == 0);
+      tc::mma_commit(&mbar[s]);
+    }
+    bool good = true;
+    if (kc == 0 && blk > 0) good = epilogue(blk - 1);
+    if (tid == 0 && kc == nkc - 1) tc::mma_commit(&mbar[2]);
+    return good;
+  };
+
+  if (total > 0) load(xa, 0);
+  if (total > 1) load(xb, 1);
+  bool ok = true;
+  for (int64_t g = 0; g < total && ok; g += 2) {
+    ok = step(xa, g);
+    if (ok && g + 1 < total) ok = step(xb, g + 1);
+  }
+  if (ok && total > 0) ok = epilogue(my_blocks - 1);
+  for (int64_t g = (total >= 2 ? total - 2 : 0); g < total && ok; ++g) {
+    const int s = (int)(g & 1);
+    const uint32_t par = s ? par1 : par0;
+    if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) ok = false;
+    if (s) par1 ^= 1; else par0 ^= 1;
+  }
+  if (!ok && tid == 0) set_status(st, RCP_ETIMEOUT);
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, NCOLS);
+}
+
+// QT = Q^T in FP32 split into TF32 hi + lo, padded with zeros to NP x Ipad.
+__global__ void k_q_to_qt32(const double* __restrict__ Q, int64_t I, int l, int NP, int64_t Ipad,
+                            float* __restrict__ QTh, float* __restrict__ QTl) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)NP * Ipad) return;
+  const int c = (int)(e / Ipad);
+  const int64_t i = e % Ipad;
+  const float v = (c < l && i < I) ? (float)Q[i + I * c] : 0.0f;
+  const float h = tf32_hi(v);
+  QTh[e] = h;
+  QTl[e] = v - h;
+}
+
+__global__ void k_reduce_f32(const float* __restrict__ part, int64_t nsplit, int64_t n,
+                             double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double acc = 0.0;
+  for (int64_t s = 0; s < nsplit; ++s) acc += (double)part[s * n + e];
+  out[e] = acc;
+}
+
+template <int NP, int SRC, bool NORM>
+cudaError_t rows_launch(const float* X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
+                        const float* WT, int nsplit, int64_t jchunk, float* part,
+                        double* normpart, DevState* st, cudaStream_t s) {
+  auto kern = k_tc_rows<NP, SRC, NORM>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<NP>::kSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((I + 127) / 128), (unsigned)nsplit);
+  count_launches(1);
+  kern<<<grid, 128, Stage<NP>::kSmem, s>>>(X, I, J, l, seed, sid, WT, jchunk, part, normpart, st);
+  return cudaGetLastError();
+}
+
+template <int NP, bool TTM>
+cudaError_t cols_launch(const float* X, int64_t I, int64_t J, int l, int64_t Ipad,
+                        const float* QT, float* out, DevState* st, int grid, cudaStream_t s) {
+  auto kern = k_tc_cols<NP, TTM>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<NP>::kSmem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<grid, 128, Stage<NP>::kSmem, s>>>(X, I, J, l, Ipad, QT, QT + (int64_t)NP * Ipad, out, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_mode1_supported(int64_t I, int l) { return l <= 64 && I % 4 == 0 && I <= 4096; }
+
+int tc_np(int l) { return l <= 32 ? 32 : 64; }
+
+int64_t tc_ipad(int64_t I) { return (I + 31) / 32 * 32; }
+
+// Split of J for the row sweep: about two CTAs per SM, chunks of 32 columns.
+void tc_rows_split(int64_t I, int64_t J, int nsm, int* nsplit, int64_t* jchunk) {
+  const int64_t mgroups = (I + 127) / 128;
+  int64_t want = (2LL * nsm + mgroups - 1) / mgroups;
+  int64_t chunk = (J + want - 1) / want;
+  chunk = (chunk + 31) / 32 * 32;
+  if (chunk < 64) chunk = 64;
+  *jchunk = chunk;
+  *nsplit = (int)((J + chunk - 1) / chunk);
+}
+
+int tc_cols_grid(int64_t J, int nsm) {
+  const int64_t njb = (J + 127) / 128;
+  const int64_t cap = 2LL * nsm;
+  return (int)(njb < cap ? njb : cap);
+}
+cudaError_t launch_tc_rows(const float* X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
+                           const float* WT, int nsplit, int64_t jchunk, float* part,
+                           double* normpart, DevState* st, cudaStream_t s) {
+  const bool norm = normpart != nullptr;
+  if (tc_np(l) == 32) {
+    if (WT) return rows_launch<32, 1, false>(X, I, J, l, 0, 0, WT, nsplit, jchunk, part, nullptr, st, s);
+    if (norm) return rows_launch<32, 0, true>(X, I, J, l, seed, sid, nullptr, nsplit, jchunk, part, normpart, st, s);
+    return rows_launch<32, 0, false>(X, I, J, l, seed, sid, nullptr, nsplit, jchunk, part, nullptr, st, s);
+  }
+  if (WT) return rows_launch<64, 1, false>(X, I, J, l, 0, 0, WT, nsplit, jchunk, part, nullptr, st, s);
+  if (norm) return rows_launch<64, 0, true>(X, I, J, l, seed, sid, nullptr, nsplit, jchunk, part, normpart, st, s);
+  return rows_launch<64, 0, false>(X, I, J, l, seed, sid, nullptr, nsplit, jchunk, part, nullptr, st, s);
+}
+
+cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const float* QT, float* out,
+                           bool ttm, DevState* st, int grid, cudaStream_t s) {
+  const int64_t Ipad = tc_ipad(I);
+  if (tc_np(l) == 32) {
+    if (ttm) return cols_launch<32, true>(X, I, J, l, Ipad, QT, out, st, grid, s);
+    return cols_launch<32, false>(X, I, J, l, Ipad, QT, out, st, grid, s);
+  }
+  if (ttm) return cols_launch<64, true>(X, I, J, l, Ipad, QT, out, st, grid, s);
+  return cols_launch<64, false>(X, I, J, l, Ipad, QT, out, st, grid, s);
+}
+
+cudaError_t launch_q_to_qt32(const double* Q, int64_t I, int l, float* QT, cudaStream_t s) {
+  const int NP = tc_np(l);
+  const int64_t Ipad = tc_ipad(I);
+  const int64_t n = (int64_t)NP * Ipad;
+  count_launches(1);
+  k_q_to_qt32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q, I, l, NP, Ipad, QT, QT + n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_f32(const float* part, int64_t nsplit, int64_t n, double* out,
+                              cudaStream_t s) {
+  count_launches(1);
+  k_reduce_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nsplit, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rcp
