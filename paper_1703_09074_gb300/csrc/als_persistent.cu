@@ -1,0 +1,677 @@
+// CP-ALS on the compressed tensor B (Algorithm 2 steps 3-11) as one persistent
+// cooperative kernel: every sweep of every mode runs without a host round trip.
+//
+// Per mode n (1-based in the paper, n0 = n - 1 here):
+//   phase A (all CTAs): MTTKRP partials  M_g = B_(n)[:, cols of g] KR[cols of g, :]
+//             where KR is the Khatri-Rao product of the other factors (built per
+//             column tile from the factor copies in shared memory);
+//   barrier;
+//   phase B (row owners): M[i, :] = sum_g M_g[i, :] in fixed order, then the
+//             row of Definition 2's solve x = M[i, :] V^{-1} with V the Hadamard
+//             product of the other Grams: an FP32 Cholesky factor of V and up to
+//             six steps of FP64 iterative refinement (residual m - x V in FP64)
+//             until the correction falls below FP64 roundoff; if the FP32
+//             factorisation meets a pivot below 64 u_32 trace(V), an FP64
+//             Cholesky (with a diagonal shift as last resort) is used instead;
+//   barrier;
+//   phase C (every CTA, identically): column norms of the new factor,
+//             normalisation (lambda = the norms at n = N), its Gram, and after
+//             mode N the fit of Section 3.3 and the stop rule.
+// Every CTA holds the same factors and Grams, so no third barrier is needed.
+// Serial FP64 chains are kept short on purpose: one FP64 warp instruction
+// occupies a GB300 sub-partition for about 76 cycles (FP64 runs at 1/73 of
+// FP32), so substitutions and factorisations run in FP32 and only the
+// refinement residuals, the reductions and the Grams of the FP64 path are FP64.
+// Grid barriers spin with a clock budget and record RCP_ETIMEOUT instead of
+// hanging.  TM is the MTTKRP type (double for the FP64 path, float for the
+// mixed form, whose factor Grams are also accumulated in FP32).
+#include <math.h>
+
+#include "rcp_internal.cuh"
+
+namespace rcp {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kTileJ = 32;
+constexpr int kBP = kTileJ + 1;                   // padded pitch of the B tile
+constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
+
+struct PersArgs {
+  int N, R, G;
+  int GA;                // CTAs that compute MTTKRP partials (GA <= G)
+  int dims[kMaxN];       // l_1..l_N
+  const void* B;         // TM, Kolda layout
+  double* At[kMaxN];     // out: normalised factors (column-major l_n x R); in: user init
+  double* lam;           // out: lambda
+  double* part;          // G x (l_max x R) MTTKRP partials
+  double* rows;          // l_max x R new factor rows (unnormalised)
+  double* ipp;           // l_max partial inner products
+  double* nbp;           // G partial |B|^2
+  unsigned* bar;         // grid barrier: count, generation
+  int* abort_flag;
+  DevState* st;
+  uint64_t seed;
+  double tol;
+  int max_iters;
+  int user_init;
+};
+
+__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag) {
+  __syncthreads();
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    int ok = 1;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > kBarrierBudget) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(abort_flag, 1);
+    ok_sh = ok && (*(volatile int*)abort_flag == 0);
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// One warp factors V = U^T U in place (upper triangle, row pitch R + 1),
+// left-looking: row k of U is V[k, :] minus the dot products with the rows
+// above, so every inner loop only reads shared memory (no read-after-write
+// chains); false on a pivot <= floor.
+template <typename T>
+__device__ bool warp_chol(T* U, int R, T floor_) {
+  const int lane = threadIdx.x & 31;
+  const int P = R + 1;
+  for (int k = 0; k < R; ++k) {
+    T part = (T)0;
+    for (int i = lane; i < k; i += 32) part += U[i * P + k] * U[i * P + k];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const T d = U[k * P + k] - part;
+    if (!(d > floor_)) return false;  // warp-uniform: every lane holds the same d
+    const T inv = (T)1 / sqrt(d);
+    for (int j = k + 1 + lane; j < R; j += 32) {
+      T s0 = U[k * P + j], s1 = (T)0;
+      int i = 0;
+      for (; i + 1 < k; i += 2) {
+        s0 -= U[i * P + k] * U[i * P + j];
+        s1 -= U[(i + 1) * P + k] * U[(i + 1) * P + j];
+      }
+      if (i < k) s0 -= U[i * P + k] * U[i * P + j];
+      U[k * P + j] = (s0 + s1) * inv;
+    }
+    if (lane == 0) U[k * P + k] = d * inv;
+    __syncwarp();
+  }
+  return true;
+}
+
+// Solve U^T U x = b in place for one right-hand side held two entries per
+// lane (entry c in lane c % 32, slot c / 32): column-oriented substitutions,
+// one broadcast and one fused multiply-add per step.
+template <typename T>
+__device__ void warp_solve(const T* U, const T* invd, int R, double (&b)[2]) {
+  const int lane = threadIdx.x & 31;
+  const int P = R + 1;
+  T y[2] = {(T)b[0], (T)b[1]};
+  for (int k = 0; k < R; ++k) {  // U^T y = b
+    const int owner = k & 31, hk = k >> 5;
+    const T yk = __shfl_sync(0xffffffffu, (hk ? y[1] : y[0]) * invd[k], owner);
+    if (lane == owner) {
+      if (hk) y[1] = yk; else y[0] = yk;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j > k && j < R) y[h] -= U[k * P + j] * yk;
+    }
+  }
+  for (int k = R - 1; k >= 0; --k) {  // U x = y
+    const int owner = k & 31, hk = k >> 5;
+    const T xk = __shfl_sync(0xffffffffu, (hk ? y[1] : y[0]) * invd[k], owner);
+    if (lane == owner) {
+      if (hk) y[1] = xk; else y[0] = xk;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i < k) y[h] -= U[i * P + k] * xk;
+    }
+  }
+  b[0] = (double)y[0];
+  b[1] = (double)y[1];
+}
+
+// One warp inverts the SPD matrix V (FP64 in shared memory, row pitch R + 1,
+// R <= 32) in FP32 registers by Gauss-Jordan elimination without pivoting
+// (lane j holds column j; the pivot column travels by shuffles), and writes
+// Z ~ V^{-1} (row pitch 32) to shared memory.  False on a pivot <= floor.
+__device__ bool warp_inverse32(const double* V, int R, float* Z, float floor_) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = (i < R && lane < R) ? (float)V[i * (R + 1) + lane] : 0.0f;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < R) {
+      // the pivot column first, all shuffles back to back, then the updates
+      float f[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) f[i] = __shfl_sync(0xffffffffu, a[i], k);
+      const float p = f[k];
+      ok = ok && (p > floor_);
+      const float pinv = 1.0f / p;
+      const float rowk = (lane == k) ? pinv : a[k] * pinv;
+      const bool pivot_lane = lane == k;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i != k) a[i] = fmaf(-f[i], rowk, pivot_lane ? 0.0f : a[i]);
+      a[k] = rowk;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < R && lane < R) Z[i * 32 + lane] = a[i];
+  return ok;
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N, R = a.R, G = a.G, GA = a.GA, g = blockIdx.x;
+  int lmax = 1, ftot = 0;
+  int foff[kMaxN];
+  for (int m = 0; m < N; ++m) {
+    lmax = max(lmax, a.dims[m]);
+    foff[m] = ftot;
+    ftot += a.dims[m] * R;
+  }
+
+  // shared-memory carve-up
+  double* Gr = (double*)smem;                   // N x R x R Grams
+  double* V = Gr + N * R * R;                   // R x (R + 1): V, or its FP64 factor
+  double* invd64 = V + R * (R + 1);             // R
+  double* Xs = invd64 + R;                      // lmax x R new factor (FP64)
+  double* nu = Xs + lmax * R;                   // R
+  double* red = nu + R;                         // 64 scalars
+  double* wsum = red + 64;                      // kWarps x 64 row / norm partials
+  float* U32 = (float*)(wsum + kWarps * 64);    // R x (R + 1) FP32 factor, or 32 x 32 Z ~ V^{-1}
+  float* invd32 = U32 + max(R * (R + 1), 1024); // R
+  TM* Fac = (TM*)(((uintptr_t)(invd32 + R) + 15) & ~(uintptr_t)15);  // factor copies
+  TM* Bs = Fac + ftot;                          // lmax x kBP
+  TM* Ks = Bs + lmax * kBP;                     // kTileJ x R
+  DevState* st = a.st;
+
+  // ---- initial factors (modes 2..N) and their Grams, identical in every CTA
+  for (int m = 1; m < N; ++m) {
+    const int lm = a.dims[m];
+    for (int e = tid; e < lm * R; e += kThreads) {
+      const int i = e / R, r = e - i * R;
+      double v;
+      if (a.user_init) {
+        v = a.At[m][i + lm * r];
+      } else {
+        const double2 z = normal_pair_f64(a.seed, (uint32_t)(m + 1), kPurposeAlsInit, (uint64_t)(e >> 1));
+        v = (e & 1) ? z.y : z.x;
+      }
+      Fac[foff[m] + i + lm * r] = (TM)v;
+      Xs[i + lm * r] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < R * R; e += kThreads) {
+      const int r = e % R, c = e / R;
+      double acc = 0.0;
+      for (int i = 0; i < lm; ++i) acc = fma(Xs[i + lm * r], Xs[i + lm * c], acc);
+      Gr[m * R * R + e] = acc;
+    }
+    __syncthreads();
+  }
+
+  double rho_prev = 0.0, nb2 = 0.0;
+  int done = 0;
+  bool ok = true;
+  for (int it = 1; it <= a.max_iters && ok && !done; ++it) {
+    for (int n0 = 0; n0 < N && ok; ++n0) {
+      const int ln = a.dims[n0];
+      int L = 1, Rt = 1;
+      for (int m = 0; m < n0; ++m) L *= a.dims[m];
+      for (int m = n0 + 1; m < N; ++m) Rt *= a.dims[m];
+      const int J = L * Rt;
+      const int nout = ln * R;
+      // ---- phase A: MTTKRP partial over this CTA's column tiles
+      double acc[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+      double nbpart = 0.0;
+      // column tiles of tj <= kTileJ columns, narrow enough to keep the GA CTAs busy
+      const int tj = max(1, min(kTileJ, (J + GA - 1) / GA));
+      for (int t0 = g * tj; g < GA && t0 < J; t0 += GA * tj) {
+        const int nj = min(tj, J - t0);
+        // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], coalesced along the contiguous index
+        for (int e = tid; e < ln * kTileJ; e += kThreads) {
+          int i, jj;
+          if (L == 1) { i = e % ln; jj = e / ln; }
+          else { jj = e % kTileJ; i = e / kTileJ; }
+          TM v = (TM)0;
+          if (jj < nj) {
+            const int j = t0 + jj;
+            const int b = j / L;
+            v = ((const TM*)a.B)[(int64_t)(j - b * L) + (int64_t)L * (i + (int64_t)ln * b)];
+          }
+          Bs[i * kBP + jj] = v;
+        }
+        // Khatri-Rao rows of the other factors, mode 1 fastest
+        for (int e = tid; e < kTileJ * R; e += kThreads) {
+          const int jj = e / R, r = e - jj * R;
+          TM prod = (TM)0;
+          if (jj < nj) {
+            int jr = t0 + jj;
+            prod = (TM)1;
+            for (int m = 0; m < N; ++m) {
+              if (m == n0) continue;
+              const int d = a.dims[m];
+              const int q = jr / d;
+              prod *= Fac[foff[m] + (jr - q * d) + d * r];
+              jr = q;
+            }
+          }
+          Ks[jj * R + r] = prod;
+        }
+        __syncthreads();
+        if (it == 1 && n0 == 0) {
+          for (int e = tid; e < ln * kTileJ; e += kThreads) {
+            const double v = (double)Bs[(e / kTileJ) * kBP + e % kTileJ];
+            nbpart = fma(v, v, nbpart);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int o = tid + k * kThreads;
+          if (o < nout) {
+            const int i = o % ln, r = o / ln;
+            TM s = (TM)0;
+            for (int jj = 0; jj < nj; ++jj) s += Bs[i * kBP + jj] * Ks[jj * R + r];
+            acc[k] += (double)s;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int o = tid + k * kThreads;
+        if (o < nout && g < GA) a.part[(int64_t)g * nout + o] = acc[k];
+      }
+      if (it == 1 && n0 == 0 && g < GA) {
+        for (int o = 16; o > 0; o >>= 1) nbpart += __shfl_down_sync(0xffffffffu, nbpart, o);
+        if (lane == 0) red[8 + warp] = nbpart;
+        __syncthreads();
+        if (tid == 0) {
+          double s = 0.0;
+          for (int w = 0; w < kWarps; ++w) s += red[8 + w];
+          a.nbp[g] = s;
+        }
+      }
+      if (!grid_sync(a.bar, (unsigned)G, a.abort_flag)) { ok = false; break; }
+
+      // ---- phase B: rows owned by this CTA (rows i = g, g + G, ...)
+      if (g < ln) {
+        // V = Hadamard product of the other Grams (FP64) and its FP32 copy
+        for (int e = tid; e < R * R; e += kThreads) {
+          const int r = e % R, c = e / R;
+          double v = 1.0;
+          for (int m = 0; m < N; ++m)
+            if (m != n0) v *= Gr[m * R * R + e];
+          V[r * (R + 1) + c] = v;
+          U32[r * (R + 1) + c] = (float)v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          float tr = 0.0f;
+          for (int c = 0; c < R; ++c) tr += U32[c * (R + 1) + c];
+          const float floor32 = 64.0f * 5.9604645e-08f * tr;
+          // path 2: FP32 inverse Z ~ V^{-1} in registers (R <= 32); path 1: FP32
+          // Cholesky factor (R > 32); path 0: FP64 Cholesky of V itself
+          int path = 0;
+          if (R <= 32) {
+            if (warp_inverse32(V, R, U32, floor32)) path = 2;
+          } else {
+            bool f32ok = warp_chol(U32, R, floor32);
+            if (f32ok)
+              for (int k = lane; k < R; k += 32) invd32[k] = 1.0f / U32[k * (R + 1) + k];
+            if (__all_sync(0xffffffffu, f32ok)) path = 1;
+          }
+          path = __shfl_sync(0xffffffffu, path, 0);
+          if (path == 0) {
+            // FP64 Cholesky of V itself; a diagonal shift R u trace(V) as last resort
+            double trd = 0.0;
+            for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
+            const double shift = (double)R * 1.1102230246251565e-16 * trd;
+            bool ok64 = warp_chol(V, R, shift);
+            if (!ok64) {
+              for (int e = lane; e < R * R; e += 32) {
+                const int r = e % R, c = e / R;
+                double v = 1.0;
+                for (int m = 0; m < N; ++m)
+                  if (m != n0) v *= Gr[m * R * R + e];
+                V[r * (R + 1) + c] = v + (r == c ? shift : 0.0);
+              }
+              __syncwarp();
+              ok64 = warp_chol(V, R, 0.0);
+              if (lane == 0) atomicOr(&st->info, RCP_INFO_ALS_REGULARISED);
+            }
+            if (!ok64 && lane == 0) set_status(st, RCP_ESINGULAR);
+            for (int k = lane; k < R; k += 32) invd64[k] = 1.0 / V[k * (R + 1) + k];
+          }
+          if (lane == 0) red[0] = (double)path;
+        }
+        __syncthreads();
+        const int path = (int)red[0];
+        const bool use32 = path != 0;
+        // all warps reduce one row's partials; warp 0 solves with the FP32 factor;
+        // the FP64 residuals m - x V of the refinement are split over all warps
+        double* xs = wsum + (kWarps - 1) * 64;  // x broadcast (the last warp's slot is read first)
+        for (int i = g; i < ln; i += G) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            if (r < R) {
+              const double* src = a.part + i + (int64_t)ln * r;
+              int gg = warp;
+              for (; gg + 3 * kWarps < GA; gg += 4 * kWarps) {
+                s0 += src[(int64_t)gg * nout];
+                s1 += src[(int64_t)(gg + kWarps) * nout];
+                s2 += src[(int64_t)(gg + 2 * kWarps) * nout];
+                s3 += src[(int64_t)(gg + 3 * kWarps) * nout];
+              }
+              for (; gg < GA; gg += kWarps) s0 += src[(int64_t)gg * nout];
+            }
+            wsum[warp * 64 + r] = (s0 + s1) + (s2 + s3);
+          }
+          __syncthreads();
+          double m[2] = {0.0, 0.0}, x[2] = {0.0, 0.0};
+          // d = v Z for the inverse path: lane c sums v_k Z[k][c] (v broadcast from shared memory)
+          auto matvec_z = [&](double (&v)[2]) {
+            xs[lane] = v[0];
+            __syncwarp();
+            float d = 0.0f;
+            for (int k = 0; k < R; ++k) d = fmaf((float)xs[k], U32[k * 32 + lane], d);
+            __syncwarp();
+            v[0] = (lane < R) ? (double)d : 0.0;
+            v[1] = 0.0;
+          };
+          if (warp == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = lane + 32 * h;
+              double s = 0.0;
+              if (r < R)
+                for (int w = 0; w < kWarps; ++w) s += wsum[w * 64 + r];
+              m[h] = s;
+              x[h] = s;
+            }
+            if (path == 2) matvec_z(x);
+            else if (path == 1) warp_solve(U32, invd32, R, x);
+            else warp_solve(V, invd64, R, x);
+          }
+          if (use32) {
+            for (int step = 0; step < 6; ++step) {
+              __syncthreads();
+              if (warp == 0) {
+                xs[lane] = x[0];
+                xs[lane + 32] = x[1];
+              }
+              __syncthreads();
+              // warp w: partial residual over k = w, w + 8, ... (lanes own columns c)
+              double pr[2] = {0.0, 0.0};
+              for (int k = warp; k < R; k += kWarps) {
+                const double xk = xs[k];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int c = lane + 32 * h;
+                  if (c < R) pr[h] = fma(V[k * (R + 1) + c], xk, pr[h]);
+                }
+              }
+              __syncthreads();
+              wsum[warp * 64 + lane] = pr[0];
+              wsum[warp * 64 + lane + 32] = pr[1];
+              __syncthreads();
+              int stop = 0;
+              if (warp == 0) {
+                double rr[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  double sum = 0.0;
+                  for (int w = 0; w < kWarps; ++w) sum += wsum[w * 64 + lane + 32 * h];
+                  rr[h] = (lane + 32 * h < R) ? m[h] - sum : 0.0;
+                }
+                if (path == 2) matvec_z(rr);
+                else warp_solve(U32, invd32, R, rr);
+                x[0] += rr[0];
+                x[1] += rr[1];
+                // stop once max |correction| <= 2^-52 max |x| (warp-uniform)
+                double dm = fmax(fabs(rr[0]), fabs(rr[1])), xm = fmax(fabs(x[0]), fabs(x[1]));
+                for (int o = 16; o > 0; o >>= 1) {
+                  dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                  xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+                }
+                stop = dm <= 2.220446049250313e-16 * xm;
+                if (lane == 0) red[6] = stop ? 1.0 : 0.0;
+              }
+              __syncthreads();
+              if (red[6] != 0.0) break;
+            }
+          }
+          if (warp == 0) {
+            double ip = 0.0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = lane + 32 * h;
+              if (r < R) {
+                a.rows[i + ln * r] = x[h];
+                ip += m[h] * x[h];
+              }
+            }
+            for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
+            if (lane == 0) a.ipp[i] = ip;
+          }
+          __syncthreads();
+        }
+      }
+      if (!grid_sync(a.bar, (unsigned)G, a.abort_flag)) { ok = false; break; }
+      // every CTA reads the status once, after the barrier, so all leave together
+      if (tid == 0) red[3] = (double)*(volatile int*)&st->status;
+      __syncthreads();
+      if (red[3] != 0.0) { ok = false; break; }
+
+      // ---- phase C (every CTA): norms, normalisation, Gram
+      for (int e = tid; e < nout; e += kThreads) Xs[e] = a.rows[e];
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {  // column norms: warp w sums rows w, w + 8, ...
+        const int r = lane + 32 * h;
+        double s = 0.0;
+        if (r < R)
+          for (int i = warp; i < ln; i += kWarps) s = fma(Xs[i + ln * r], Xs[i + ln * r], s);
+        wsum[warp * 64 + r] = s;
+      }
+      __syncthreads();
+      for (int r = tid; r < R; r += kThreads) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += wsum[w * 64 + r];
+        nu[r] = sqrt(s);
+        wsum[kWarps * 64 - 64 + r] = nu[r] > 0.0 ? 1.0 / nu[r] : 0.0;  // last warp's row is free now
+      }
+      __syncthreads();
+      for (int e = tid; e < nout; e += kThreads) {
+        const int r = e / ln;
+        const double v = Xs[e] * wsum[kWarps * 64 - 64 + r];
+        Xs[e] = v;
+        Fac[foff[n0] + e] = (TM)v;
+        if (g == 0) a.At[n0][e] = v;
+      }
+      __syncthreads();
+      if (sizeof(TM) == 4) {
+        // mixed form: Gram of the normalised factor from the FP32 copies
+        for (int e = tid; e < R * R; e += kThreads) {
+          const int r = e % R, c = e / R;
+          float s = 0.0f;
+          const TM* fr = Fac + foff[n0] + ln * r;
+          const TM* fc = Fac + foff[n0] + ln * c;
+          for (int i = 0; i < ln; ++i) s = fmaf((float)fr[i], (float)fc[i], s);
+          Gr[n0 * R * R + e] = (double)s;
+        }
+      } else {
+        // symmetric: entries r <= c only
+        for (int e = tid; e < R * (R + 1) / 2; e += kThreads) {
+          int c = 0, rem = e;
+          while (rem > c) { rem -= c + 1; ++c; }
+          const int r = rem;
+          double s = 0.0;
+          for (int i = 0; i < ln; ++i) s = fma(Xs[i + ln * r], Xs[i + ln * c], s);
+          Gr[n0 * R * R + r + R * c] = s;
+          Gr[n0 * R * R + c + R * r] = s;
+        }
+      }
+      __syncthreads();
+      if (n0 == N - 1) {
+        // |Bhat|^2 = lambda^T (Hadamard product of all Grams) lambda, <Bhat, B> = sum_i ipp[i]
+        double bh = 0.0;
+        for (int e = tid; e < R * R; e += kThreads) {
+          const int r = e % R, c = e / R;
+          double v = nu[r] * nu[c];
+          for (int m = 0; m < N; ++m) v *= Gr[m * R * R + e];
+          bh += v;
+        }
+        double sb = 0.0, si = 0.0;
+        if (warp == 0) {
+          if (it == 1)
+            for (int gg = lane; gg < GA; gg += 32) sb += a.nbp[gg];
+          for (int i = lane; i < ln; i += 32) si += a.ipp[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          bh += __shfl_xor_sync(0xffffffffu, bh, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) red[16 + warp] = bh;
+        if (tid == 0) {
+          red[4] = sb;
+          red[5] = si;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          if (it == 1) nb2 = red[4];
+          double bhat = 0.0;
+          for (int w = 0; w < kWarps; ++w) bhat += red[16 + w];
+          const double ip = red[5];
+          const double rho = 1.0 - (nb2 + bhat - 2.0 * ip) / nb2;
+          const bool conv = fabs(rho - rho_prev) < a.tol;
+          red[2] = (conv || it >= a.max_iters) ? (conv ? 1.0 : 2.0) : 0.0;
+          rho_prev = rho;
+          if (g == 0) {
+            st->fit = rho;
+            st->ip = ip;
+            st->fit_prev = rho;
+            st->als_iters = it;
+            st->norm_b2 = nb2;
+            if (!isfinite(rho)) set_status(st, RCP_ENAN);
+          }
+        }
+        if (g == 0)
+          for (int r = tid; r < R; r += kThreads) a.lam[r] = nu[r];
+        __syncthreads();
+        done = red[2] != 0.0 ? (int)red[2] : 0;
+        if (done && g == 0 && tid == 0) st->als_done = done;
+        __syncthreads();
+      }
+    }
+  }
+  if (!ok && g == 0 && tid == 0 && !*(volatile int*)&st->status) set_status(st, RCP_ETIMEOUT);
+}
+
+template <typename TM>
+size_t smem_bytes(const rcp_plan_s* p) {
+  int lmax = 1, ftot = 0;
+  for (int m = 0; m < p->N; ++m) {
+    lmax = lmax > p->l[m] ? lmax : p->l[m];
+    ftot += p->l[m] * p->R;
+  }
+  const size_t R = p->R, N = p->N;
+  const size_t d = N * R * R + R * (R + 1) + R + (size_t)lmax * R + R + 64 + kWarps * 64;
+  const size_t f = (R * (R + 1) > 1024 ? R * (R + 1) : 1024) + R;
+  return d * sizeof(double) + f * sizeof(float) + 16 +
+         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * R) * sizeof(TM);
+}
+
+template <typename TM>
+cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
+  const size_t smem = smem_bytes<TM>(p);
+  cudaError_t e = cudaFuncSetAttribute(k_als_persistent<TM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_als_persistent<TM>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  PersArgs a{};
+  a.N = p->N;
+  a.R = p->R;
+  a.G = p->nsm;  // one CTA per SM
+  a.GA = a.G;  // every CTA computes MTTKRP partials (fewer CTAs leave L2 latency exposed)
+  for (int m = 0; m < p->N; ++m) {
+    a.dims[m] = p->l[m];
+    a.At[m] = p->At[m];
+  }
+  a.B = B;
+  a.lam = p->lam;
+  a.part = p->part;
+  a.rows = p->M;
+  a.ipp = p->tmp;
+  a.nbp = p->normpart;
+  a.bar = p->bar;
+  a.abort_flag = p->abort_flag;
+  a.st = p->dstate;
+  a.seed = p->cfg.seed;
+  a.tol = p->cfg.tol;
+  a.max_iters = p->cfg.max_iters;
+  a.user_init = p->user_init ? 1 : 0;
+  void* args[] = {&a};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel((const void*)k_als_persistent<TM>, dim3(a.G), dim3(kThreads),
+                                     args, smem, s);
+}
+
+}  // namespace
+
+// True when the persistent kernel fits this plan (shared memory, rank, 32-bit core indexing).
+bool als_persistent_fits(const rcp_plan_s* p, bool f32) {
+  if (p->R > 64) return false;
+  int lmax = 1;
+  for (int m = 0; m < p->N; ++m) lmax = lmax > p->l[m] ? lmax : p->l[m];
+  if ((int64_t)lmax * p->R > 16 * kThreads) return false;
+  if (p->core_elems >= (1LL << 31)) return false;
+  const size_t smem = f32 ? smem_bytes<float>(p) : smem_bytes<double>(p);
+  return smem <= 200 * 1024;
+}
+
+cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s) {
+  return f32 ? launch_typed<float>(p, B, s) : launch_typed<double>(p, B, s);
+}
+
+}  // namespace rcp

@@ -89,6 +89,8 @@ void free_plan(rcp_plan_t p) {
   cudaFree(p->part32);
   cudaFree(p->QT32);
   cudaFree(p->dstate);
+  cudaFree(p->bar);
+  cudaFree(p->abort_flag);
   cudaFree(p->X_stage);
   cudaFree(p->lam_stage);
   if (p->prof) {
@@ -220,6 +222,11 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     v.J = v.L * v.Rt;
     part_max = std::max(part_max, (int64_t)sketch_splits(v, p->nsm) * p->l[n] * p->R);
   }
+  {
+    int lmx = 1;
+    for (int n = 0; n < N; ++n) lmx = lmx > p->l[n] ? lmx : p->l[n];
+    part_max = std::max(part_max, (int64_t)p->nsm * lmx * p->R);  // persistent ALS partials
+  }
   p->bufT_elems = bufmax;
   p->part_elems = part_max;
   p->tmp_elems = std::max<int64_t>(16 * std::max(red_max, (int64_t)kMaxL * (kMaxL + 1) / 2),
@@ -249,6 +256,8 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   A(dalloc(&p->M, (int64_t)kMaxL * p->R));
   A(dalloc(&p->lam, p->R));
   A(dalloc(&p->dstate, 1));
+  A(dalloc(&p->bar, 4));
+  A(dalloc(&p->abort_flag, 4));
   if (p->prec == RCP_PREC_MIXED) {
     p->tc1 = tc_mode1_supported(p->dims[0], p->l[0]);
     int64_t p32 = 1;
@@ -509,11 +518,20 @@ rcp_status rcp_als(rcp_plan_t p, double* lambda_host, double* fit_host, int32_t*
   cudaStream_t s = p->stream;
   {
     Span sp(p, RCP_KT_ALS, 0);
-    RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
-    RCP_TRY(launch_als_init(p, s));
+    const bool f32 = p->prec == RCP_PREC_MIXED;
+    if (als_persistent_fits(p, f32)) {
+      // one cooperative kernel runs every sweep (FP32 MTTKRP in the mixed form)
+      RCP_TRY(cudaMemsetAsync(p->bar, 0, 4 * sizeof(unsigned), s));
+      RCP_TRY(cudaMemsetAsync(p->abort_flag, 0, 4 * sizeof(int), s));
+      const void* B = f32 ? (const void*)mode_output(p, p->N) : (const void*)p->Bcore64;
+      RCP_TRY(launch_als_persistent(p, B, f32, s));
+    } else {
+      RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
+      RCP_TRY(launch_als_init(p, s));
+      for (int it = 0; it < p->cfg.max_iters; ++it)
+        for (int n0 = 0; n0 < p->N; ++n0) RCP_TRY(launch_als_sweep(p, n0, s));
+    }
     p->user_init = false;
-    for (int it = 0; it < p->cfg.max_iters; ++it)
-      for (int n0 = 0; n0 < p->N; ++n0) RCP_TRY(launch_als_sweep(p, n0, s));
   }
   p->als_done = true;
   if (lambda_host || fit_host || iters_host) {

@@ -98,6 +98,10 @@ struct rcp_plan_s {
   int compressed;  // last mode compressed (0 = none)
   bool als_done;
 
+  // persistent ALS: grid barrier words and abort flag
+  unsigned* bar;
+  int* abort_flag;
+
   // mixed-precision form
   bool tc1;                  // mode 1 runs on the tensor cores
   float* part32;             // FP32 split partials of the tensor-core row sweep
@@ -230,6 +234,8 @@ cudaError_t launch_als_init(rcp_plan_s* p, cudaStream_t s);
 cudaError_t launch_als_sweep(rcp_plan_s* p, int mode0, cudaStream_t s);
 cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lambda_dev,
                                cudaStream_t s);
+bool als_persistent_fits(const rcp_plan_s* p, bool f32);
+cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s);
 cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* dst, cudaStream_t s);
 
