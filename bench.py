@@ -226,6 +226,13 @@ def run_ours(args):
                      (_lib.RCP_KT_ALS, "als")):
         n, ms = kt(kind, 0)
         stages[nm] = {"launches": n, "ms_per_step": ms / args.steps}
+    mode1 = {}
+    for kind, nm in ((_lib.RCP_KT_SKETCH, "sketch"), (_lib.RCP_KT_APPLY, "apply"),
+                     (_lib.RCP_KT_PROJECT, "project"), (_lib.RCP_KT_TTM, "ttm")):
+        n, ms = kt(kind, 1)
+        if n:
+            mode1[nm] = {"launches": n, "us_per_launch": 1e3 * ms / n,
+                         "gbs": (X.numel() * X.element_size()) / (ms / n / 1e3) / 1e9}
     _lib.check(lib.rcp_profile_enable(plan.h, 0), "rcp_profile_enable")
 
     # dominant sweep: mode-1 kernels over X
@@ -293,6 +300,7 @@ def run_ours(args):
             "sketch_pass_gbs": sketch_gbs,
             "fit": res["fit"], "rel_err": res["rel_err"], "als_iters": res["iters"],
             "stages": stages,
+            "mode1_sweeps": mode1,
             "roofline": roof,
             "e2e": {"value": e2e_v / ws, "unit": "s", "h2d_bytes_per_step": xbytes,
                     "d2h_bytes_per_step": d2h},

@@ -72,6 +72,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   __shared__ uint32_t tbase_sh;
   __shared__ int abort_sh;
   __shared__ double red[4];
+  __shared__ uint16_t boff[32 * 64];  // element t = jj * l + c of a chunk -> its byte offset in B
   using S = Stage<NP>;
   constexpr uint32_t NCOLS = NP;
   constexpr uint32_t IDESC = tc::idesc_tf32(128, NP);
@@ -91,6 +92,10 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     const int s = k / (2 * NP * 32), e = k % (2 * NP * 32);
     *(float*)(sm + s * S::kBytes + 2 * S::kA + 4 * e) = 0.0f;
   }
+  for (int t = tid; t < 32 * l; t += 128) {
+    const int jj = t / l, c = t - jj * l;
+    boff[t] = (uint16_t)tc::sw128_offset((uint32_t)c, (uint32_t)jj);
+  }
   tc::tc_fence_before_sync();
   __syncthreads();
   tc::tc_fence_after_sync();
@@ -100,8 +105,19 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   const bool row_ok = row < I;
   const int nk = (int)((je - jb + 31) / 32);
   float xa[32], xb[32];
+  float wa[NP / 4], wb[NP / 4];  // SRC 1: this thread's W^T values of a chunk (t = tid + 128 k)
   float nrm = 0.0f;
   uint32_t par0 = 0, par1 = 0;
+  auto load_w = [&](float (&wr)[NP / 4], int kc) {
+    const int64_t j0 = jb + 32LL * kc;
+#pragma unroll
+    for (int k = 0; k < NP / 4; ++k) {
+      const int t = tid + 128 * k;  // t = c * 32 + jj, covering NP x 32
+      const int c = t >> 5, jj = t & 31;
+      const int64_t j = j0 + jj;
+      wr[k] = (c < l && j < je) ? __ldg(WT + (int64_t)c * J + j) : 0.0f;
+    }
+  };
 
   auto load = [&](float (&xr)[32], int kc) {
     const int64_t j0 = jb + 32LL * kc;
@@ -111,14 +127,13 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       xr[jj] = (row_ok && j < je) ? __ldg(X + row + I * j) : 0.0f;
     }
   };
-  auto put_b = [&](uint8_t* Bh, uint8_t* Bl, int c, int jj, float v) {
+  auto put_b = [&](uint8_t* Bh, uint8_t* Bl, uint32_t off, float v) {
     const float h = tf32_hi(v);
-    const uint32_t off = tc::sw128_offset((uint32_t)c, (uint32_t)jj);
     *(float*)(Bh + off) = h;
     *(float*)(Bl + off) = v - h;
   };
   // one 32-column chunk: stage it, prefetch chunk kc + 2 into the same registers, issue MMAs
-  auto step = [&](float (&xr)[32], int kc) -> bool {
+  auto step = [&](float (&xr)[32], float (&wr)[NP / 4], int kc) -> bool {
     const int s = kc & 1;
     uint8_t* Ah = sm + s * S::kBytes;
     uint8_t* Al = Ah + S::kA;
@@ -144,28 +159,34 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       *(float4*)(Ah + off) = h;
       *(float4*)(Al + off) = lo;
     }
-    if (kc + 2 < nk) load(xr, kc + 2);
     const int64_t j0 = jb + 32LL * kc;
     if (SRC == 0) {
-      // Omega_1[j, c] = element e = j l + c of the reduced-precision stream
-      const int64_t e0 = j0 * l, e1 = (j0 + 32) * (int64_t)l;
-      const int64_t g0 = e0 >> 2, g1 = (e1 - 1) >> 2;
-      for (int64_t g = g0 + tid; g <= g1; g += 128) {
-        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)g);
+      if (kc + 2 < nk) load(xr, kc + 2);
+      // Omega_1[j, c] = element e = j l + c of the reduced-precision stream; local
+      // index t = e - j0 l in [0, 32 l), counters g = e / 4 from g0 = (j0 l) / 4
+      const int64_t e0 = j0 * l;
+      const int lead = (int)(e0 & 3);                      // elements of quad g0 before e0
+      const int tend = (int)min((int64_t)32, je - j0) * l;  // valid elements of this chunk
+      const int nq = (32 * l + lead + 3) >> 2;
+      for (int q = tid; q < nq; q += 128) {
+        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)((e0 >> 2) + q));
         const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t e = 4 * g + q;
-          if (e < e0 || e >= e1) continue;
-          const int64_t j = e / l;
-          put_b(Bh, Bl, (int)(e - j * l), (int)(j - j0), (j < je) ? zz[q] : 0.0f);
+        for (int u = 0; u < 4; ++u) {
+          const int t = 4 * q + u - lead;
+          if (t >= 0 && t < 32 * l) put_b(Bh, Bl, boff[t], t < tend ? zz[u] : 0.0f);
         }
       }
     } else {
-      for (int k = tid; k < l * 32; k += 128) {
-        const int c = k >> 5, jj = k & 31;
-        const int64_t j = j0 + jj;
-        put_b(Bh, Bl, c, jj, (j < je) ? __ldg(WT + (int64_t)c * J + j) : 0.0f);
+#pragma unroll
+      for (int k = 0; k < NP / 4; ++k) {
+        const int t = tid + 128 * k;
+        const int c = t >> 5, jj = t & 31;
+        if (c < l) put_b(Bh, Bl, tc::sw128_offset((uint32_t)c, (uint32_t)jj), wr[k]);
+      }
+      if (kc + 2 < nk) {
+        load(xr, kc + 2);
+        load_w(wr, kc + 2);
       }
     }
     tc::fence_proxy_async_smem();
@@ -182,10 +203,14 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
 
   if (nk > 0) load(xa, 0);
   if (nk > 1) load(xb, 1);
+  if (SRC == 1) {
+    if (nk > 0) load_w(wa, 0);
+    if (nk > 1) load_w(wb, 1);
+  }
   bool ok = true;
   for (int kc = 0; kc < nk && ok; kc += 2) {
-    ok = step(xa, kc);
-    if (ok && kc + 1 < nk) ok = step(xb, kc + 1);
+    ok = step(xa, wa, kc);
+    if (ok && kc + 1 < nk) ok = step(xb, wb, kc + 1);
   }
   for (int kc = (nk >= 2 ? nk - 2 : 0); kc < nk && ok; ++kc) {
     const int s = kc & 1;
@@ -256,8 +281,21 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
   const int64_t my_blocks = (njb > blockIdx.x) ? (njb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t total = my_blocks * nkc;
   const int c16 = tid & 7, r0 = tid >> 3;
+  constexpr int QV = NP / 16;  // float4 of Q^T hi (and lo) per thread and chunk
   float4 xa[8], xb[8];
+  float4 qa[2 * QV], qb[2 * QV];
   uint32_t par0 = 0, par1 = 0, pacc = 0;
+  auto load_q = [&](float4 (&qv)[2 * QV], int64_t g) {
+    const int kc = (int)(g % nkc);
+#pragma unroll
+    for (int k = 0; k < QV; ++k) {
+      const int t = tid + 128 * k;  // t = c * 8 + cc
+      const int c = t >> 3, cc = t & 7;
+      const int64_t src = (int64_t)c * Ipad + 32LL * kc + 4 * cc;
+      qv[k] = __ldg((const float4*)(QTh + src));
+      qv[QV + k] = __ldg((const float4*)(QTl + src));
+    }
+  };
 
   auto load = [&](float4 (&xv)[8], int64_t g) {
     const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
@@ -294,7 +332,7 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     tc::tc_fence_before_sync();
     return good;
   };
-  auto step = [&](float4 (&xv)[8], int64_t g) -> bool {
+  auto step = [&](float4 (&xv)[8], float4 (&qv)[2 * QV], int64_t g) -> bool {
     const int s = (int)(g & 1);
     const int kc = (int)(g % nkc);
     const int64_t blk = g / nkc;
@@ -319,13 +357,17 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
       *(float4*)(Ah + off) = h;
       *(float4*)(Al + off) = lo;
     }
-    if (g + 2 < total) load(xv, g + 2);
-    for (int k = tid; k < NP * 8; k += 128) {
-      const int c = k >> 3, cc = k & 7;
+#pragma unroll
+    for (int k = 0; k < QV; ++k) {
+      const int t = tid + 128 * k;
+      const int c = t >> 3, cc = t & 7;
       const uint32_t off = c * 128 + ((((uint32_t)cc ^ ((uint32_t)c & 7u)) & 7u) << 4);
-      const int64_t src = (int64_t)c * Ipad + 32LL * kc + 4 * cc;
-      *(float4*)(Bh + off) = __ldg((const float4*)(QTh + src));
-      *(float4*)(Bl + off) = __ldg((const float4*)(QTl + src));
+      *(float4*)(Bh + off) = qv[k];
+      *(float4*)(Bl + off) = qv[QV + k];
+    }
+    if (g + 2 < total) {
+      load(xv, g + 2);
+      load_q(qv, g + 2);
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -342,12 +384,18 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     return good;
   };
 
-  if (total > 0) load(xa, 0);
-  if (total > 1) load(xb, 1);
+  if (total > 0) {
+    load(xa, 0);
+    load_q(qa, 0);
+  }
+  if (total > 1) {
+    load(xb, 1);
+    load_q(qb, 1);
+  }
   bool ok = true;
   for (int64_t g = 0; g < total && ok; g += 2) {
-    ok = step(xa, g);
-    if (ok && g + 1 < total) ok = step(xb, g + 1);
+    ok = step(xa, qa, g);
+    if (ok && g + 1 < total) ok = step(xb, qb, g + 1);
   }
   if (ok && total > 0) ok = epilogue(my_blocks - 1);
   for (int64_t g = (total >= 2 ? total - 2 : 0); g < total && ok; ++g) {
