@@ -248,6 +248,47 @@ rcp_status rcp_test_normals(uint64_t seed, uint32_t stream, uint32_t purpose, in
                             int64_t count, double* out_dev, uint32_t* words_dev,
                             float* f32_out_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many tensors of uneven shapes decomposed together.  Every
+ * step of Algorithm 1 (per mode), Algorithm 2 and the recovery of Eq. (qbs)
+ * runs as one launch over all tensors (persistent kernels pulling
+ * (tensor, tile) work items largest tensor first; one CTA per tensor for the
+ * FP64 CholeskyQR2 of each sketch and for the ALS of each compressed tensor),
+ * and the whole sequence is captured into one CUDA graph on the first run and
+ * replayed afterwards.
+ * ---------------------------------------------------------------------- */
+typedef struct rcp_batched_s* rcp_batched_t;
+
+/* Plan `count` decompositions.  cfgs[b] describes tensor b; all must have the
+ * same ndim and power_iters, in_dtype RCP_DTYPE_F32, precision
+ * RCP_PREC_MIXED, rank <= 32 and widths l_n <= 32.  Allocates one workspace
+ * arena for the batch; stream as in rcp_plan.  RCP_EINVAL / RCP_ENOMEM. */
+rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
+                            rcp_batched_t* out);
+
+/* Decompose every tensor: X_dev[b] is a device pointer to tensor b (Kolda
+ * layout, FP32), valid until the run completes.  The first call captures the
+ * launch sequence into a CUDA graph; later calls replay it (the pointers may
+ * change between calls; each call waits for the previous run to finish before
+ * updating them).  Asynchronous otherwise. */
+rcp_status rcp_batched_run(rcp_batched_t plan, const void* const* X_dev);
+
+/* Choose the launch shapes of the batched sweeps (persistent CTAs per SM for
+ * the row and column sweeps, candidates 1, 2, 4, 8) by timing a complete
+ * batch run per candidate pair on X_dev; keeps the fastest for later runs
+ * and writes it to choice[0..1] when choice is not NULL.  Synchronises. */
+rcp_status rcp_batched_autotune(rcp_batched_t plan, const void* const* X_dev, int32_t* choice);
+
+/* Results of tensor `index` after a run: factors A_n (A_dev[n-1], device,
+ * I_n x R column-major FP64, entries may be NULL), lambda (device, R doubles,
+ * may be NULL) and the result record.  Synchronises the stream; returns the
+ * tensor's device status. */
+rcp_status rcp_batched_result(rcp_batched_t plan, int32_t index, double* const* A_dev,
+                              double* lambda_dev, rcp_result* res);
+
+/* Free the batch plan (synchronises first).  NULL is ignored. */
+rcp_status rcp_batched_destroy(rcp_batched_t plan);
+
 /* Allocation-free mode-1 range finder.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
  * that runs where cudaMalloc is forbidden or unsafe (inside another

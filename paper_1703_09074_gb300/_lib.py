@@ -68,6 +68,13 @@ SIGNATURES = {
     "rcp_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
     "rcp_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int64), DP]),
+    "rcp_plan_batched": (ctypes.c_int, [ctypes.POINTER(RcpConfig), ctypes.c_int32, P,
+                                        ctypes.POINTER(P)]),
+    "rcp_batched_run": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+    "rcp_batched_autotune": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int32)]),
+    "rcp_batched_result": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P), P,
+                                          ctypes.POINTER(RcpResult)]),
+    "rcp_batched_destroy": (ctypes.c_int, [P]),
     "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_uint64, P, P, P]),

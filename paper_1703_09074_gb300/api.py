@@ -204,3 +204,86 @@ def test_normals(seed, stream, purpose, first, count, device="cuda"):
                                ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(f.data_ptr()),
                                ctypes.c_void_p(s.cuda_stream)), "rcp_test_normals")
     return z, w, f
+
+
+class BatchedPlan:
+    """Many decompositions of uneven shapes run together (one CUDA graph per batch).
+
+    ``problems``: list of dicts with keys dims, rank, oversample, power_iters,
+    tol, max_iters, seed (FP32 inputs, mixed precision).
+    """
+
+    def __init__(self, problems, stream=None):
+        self.lib = _lib.load()
+        self.count = len(problems)
+        arr = (RcpConfig * self.count)()
+        self.dims = []
+        self.ranks = []
+        for b, pr in enumerate(problems):
+            c = arr[b]
+            dims = tuple(int(d) for d in pr["dims"])
+            c.ndim = len(dims)
+            for k, d in enumerate(dims):
+                c.dims[k] = d
+            c.in_dtype = _lib.RCP_DTYPE_F32
+            c.rank = int(pr["rank"])
+            c.oversample = int(pr.get("oversample", 8))
+            c.power_iters = int(pr.get("power_iters", 1))
+            c.tol = float(pr.get("tol", 1e-10))
+            c.max_iters = int(pr.get("max_iters", 50))
+            c.seed = int(pr.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+            c.precision = _lib.RCP_PREC_MIXED
+            c.flags = 0
+            self.dims.append(dims)
+            self.ranks.append(c.rank)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        h = ctypes.c_void_p()
+        check(self.lib.rcp_plan_batched(arr, self.count, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)), "rcp_plan_batched")
+        self.h = h
+
+    def _ptrs(self, Xs):
+        if len(Xs) != self.count:
+            raise ValueError("one tensor per problem")
+        for X, d in zip(Xs, self.dims):
+            if not (X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+                    and tuple(reversed(X.shape)) == d):
+                raise ValueError(f"expected a contiguous FP32 CUDA tensor of shape {tuple(reversed(d))}")
+        return _ptr_array(Xs)
+
+    def run(self, Xs):
+        self._keep = Xs
+        check(self.lib.rcp_batched_run(self.h, self._ptrs(Xs)), "rcp_batched_run")
+
+    def autotune(self, Xs):
+        ch = (ctypes.c_int32 * 2)()
+        check(self.lib.rcp_batched_autotune(self.h, self._ptrs(Xs), ch), "rcp_batched_autotune")
+        return ch[0], ch[1]
+
+    def result(self, b):
+        A = [torch.empty((self.ranks[b], I), dtype=torch.float64, device=self.device)
+             for I in self.dims[b]]
+        lam = torch.empty(self.ranks[b], dtype=torch.float64, device=self.device)
+        res = RcpResult()
+        code = self.lib.rcp_batched_result(self.h, b, _ptr_array(A), ctypes.c_void_p(lam.data_ptr()),
+                                           ctypes.byref(res))
+        check(code, "rcp_batched_result")
+        return [a.t() for a in A], lam, _result_dict(res, len(self.dims[b]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rcp_batched_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

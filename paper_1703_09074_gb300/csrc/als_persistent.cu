@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include "rcp_internal.cuh"
+#include "small_la.cuh"
 
 namespace rcp {
 namespace {
@@ -38,25 +39,6 @@ constexpr int kTileJ = 32;
 constexpr int kBP = kTileJ + 1;                   // padded pitch of the B tile
 constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
 
-struct PersArgs {
-  int N, R, G;
-  int GA;                // CTAs that compute MTTKRP partials (GA <= G)
-  int dims[kMaxN];       // l_1..l_N
-  const void* B;         // TM, Kolda layout
-  double* At[kMaxN];     // out: normalised factors (column-major l_n x R); in: user init
-  double* lam;           // out: lambda
-  double* part;          // G x (l_max x R) MTTKRP partials
-  double* rows;          // l_max x R new factor rows (unnormalised)
-  double* ipp;           // l_max partial inner products
-  double* nbp;           // G partial |B|^2
-  unsigned* bar;         // grid barrier: count, generation
-  int* abort_flag;
-  DevState* st;
-  uint64_t seed;
-  double tol;
-  int max_iters;
-  int user_init;
-};
 
 __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag) {
   __syncthreads();
@@ -88,112 +70,20 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag) {
   return ok_sh != 0;
 }
 
-// One warp factors V = U^T U in place (upper triangle, row pitch R + 1),
-// left-looking: row k of U is V[k, :] minus the dot products with the rows
-// above, so every inner loop only reads shared memory (no read-after-write
-// chains); false on a pivot <= floor.
-template <typename T>
-__device__ bool warp_chol(T* U, int R, T floor_) {
-  const int lane = threadIdx.x & 31;
-  const int P = R + 1;
-  for (int k = 0; k < R; ++k) {
-    T part = (T)0;
-    for (int i = lane; i < k; i += 32) part += U[i * P + k] * U[i * P + k];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const T d = U[k * P + k] - part;
-    if (!(d > floor_)) return false;  // warp-uniform: every lane holds the same d
-    const T inv = (T)1 / sqrt(d);
-    for (int j = k + 1 + lane; j < R; j += 32) {
-      T s0 = U[k * P + j], s1 = (T)0;
-      int i = 0;
-      for (; i + 1 < k; i += 2) {
-        s0 -= U[i * P + k] * U[i * P + j];
-        s1 -= U[(i + 1) * P + k] * U[(i + 1) * P + j];
-      }
-      if (i < k) s0 -= U[i * P + k] * U[i * P + j];
-      U[k * P + j] = (s0 + s1) * inv;
-    }
-    if (lane == 0) U[k * P + k] = d * inv;
-    __syncwarp();
+// Block-wide barrier for the G CTAs of one problem (a plain __syncthreads when G == 1).
+__device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
+  if (G == 1) {
+    __syncthreads();
+    return true;
   }
-  return true;
-}
-
-// Solve U^T U x = b in place for one right-hand side held two entries per
-// lane (entry c in lane c % 32, slot c / 32): column-oriented substitutions,
-// one broadcast and one fused multiply-add per step.
-template <typename T>
-__device__ void warp_solve(const T* U, const T* invd, int R, double (&b)[2]) {
-  const int lane = threadIdx.x & 31;
-  const int P = R + 1;
-  T y[2] = {(T)b[0], (T)b[1]};
-  for (int k = 0; k < R; ++k) {  // U^T y = b
-    const int owner = k & 31, hk = k >> 5;
-    const T yk = __shfl_sync(0xffffffffu, (hk ? y[1] : y[0]) * invd[k], owner);
-    if (lane == owner) {
-      if (hk) y[1] = yk; else y[0] = yk;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = lane + 32 * h;
-      if (j > k && j < R) y[h] -= U[k * P + j] * yk;
-    }
-  }
-  for (int k = R - 1; k >= 0; --k) {  // U x = y
-    const int owner = k & 31, hk = k >> 5;
-    const T xk = __shfl_sync(0xffffffffu, (hk ? y[1] : y[0]) * invd[k], owner);
-    if (lane == owner) {
-      if (hk) y[1] = xk; else y[0] = xk;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = lane + 32 * h;
-      if (i < k) y[h] -= U[i * P + k] * xk;
-    }
-  }
-  b[0] = (double)y[0];
-  b[1] = (double)y[1];
-}
-
-// One warp inverts the SPD matrix V (FP64 in shared memory, row pitch R + 1,
-// R <= 32) in FP32 registers by Gauss-Jordan elimination without pivoting
-// (lane j holds column j; the pivot column travels by shuffles), and writes
-// Z ~ V^{-1} (row pitch 32) to shared memory.  False on a pivot <= floor.
-__device__ bool warp_inverse32(const double* V, int R, float* Z, float floor_) {
-  const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) a[i] = (i < R && lane < R) ? (float)V[i * (R + 1) + lane] : 0.0f;
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < R) {
-      // the pivot column first, all shuffles back to back, then the updates
-      float f[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) f[i] = __shfl_sync(0xffffffffu, a[i], k);
-      const float p = f[k];
-      ok = ok && (p > floor_);
-      const float pinv = 1.0f / p;
-      const float rowk = (lane == k) ? pinv : a[k] * pinv;
-      const bool pivot_lane = lane == k;
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i != k) a[i] = fmaf(-f[i], rowk, pivot_lane ? 0.0f : a[i]);
-      a[k] = rowk;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i)
-    if (i < R && lane < R) Z[i * 32 + lane] = a[i];
-  return ok;
+  return grid_sync(a.bar, (unsigned)G, a.abort_flag);
 }
 
 template <typename TM>
-__global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
+__device__ void als_body(const PersArgs& a, int g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int N = a.N, R = a.R, G = a.G, GA = a.GA, g = blockIdx.x;
+  const int N = a.N, R = a.R, G = a.G, GA = a.GA;
   int lmax = 1, ftot = 0;
   int foff[kMaxN];
   for (int m = 0; m < N; ++m) {
@@ -326,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
           a.nbp[g] = s;
         }
       }
-      if (!grid_sync(a.bar, (unsigned)G, a.abort_flag)) { ok = false; break; }
+      if (!phase_sync(a, G)) { ok = false; break; }
 
       // ---- phase B: rows owned by this CTA (rows i = g, g + G, ...)
       if (g < ln) {
@@ -382,6 +272,71 @@ __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
         __syncthreads();
         const int path = (int)red[0];
         const bool use32 = path != 0;
+        if (G == 1) {
+          // one CTA per problem: warp w solves rows w, w + 8, ... on its own
+          double* wsc = wsum + warp * 64;  // this warp's broadcast scratch
+          auto wmatvec = [&](double (&v)[2]) {
+            wsc[lane] = v[0];
+            __syncwarp();
+            float d = 0.0f;
+            for (int k = 0; k < R; ++k) d = fmaf((float)wsc[k], U32[k * 32 + lane], d);
+            __syncwarp();
+            v[0] = (lane < R) ? (double)d : 0.0;
+            v[1] = 0.0;
+          };
+          for (int i = warp; i < ln; i += kWarps) {
+            double m[2], x[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = lane + 32 * h;
+              double sm_ = 0.0;
+              if (r < R)
+                for (int gg = 0; gg < GA; ++gg) sm_ += a.part[(int64_t)gg * nout + i + ln * r];
+              m[h] = sm_;
+              x[h] = sm_;
+            }
+            if (path == 2) wmatvec(x);
+            else if (path == 1) warp_solve(U32, invd32, R, x);
+            else warp_solve(V, invd64, R, x);
+            for (int step = 0; use32 && step < 6; ++step) {
+              double rr[2] = {m[0], m[1]};
+              for (int k = 0; k < R; ++k) {
+                const double xk = __shfl_sync(0xffffffffu, (k >> 5) ? x[1] : x[0], k & 31);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int c = lane + 32 * h;
+                  if (c < R) rr[h] = fma(-V[k * (R + 1) + c], xk, rr[h]);
+                }
+              }
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h >= R) rr[h] = 0.0;
+              if (path == 2) wmatvec(rr);
+              else warp_solve(U32, invd32, R, rr);
+              x[0] += rr[0];
+              x[1] += rr[1];
+              double dm = fmax(fabs(rr[0]), fabs(rr[1])), xm = fmax(fabs(x[0]), fabs(x[1]));
+              for (int o = 16; o > 0; o >>= 1) {
+                dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+              }
+              if (dm <= 2.220446049250313e-16 * xm) break;
+            }
+            double ip = 0.0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = lane + 32 * h;
+              if (r < R) {
+                a.rows[i + ln * r] = x[h];
+                ip += m[h] * x[h];
+              }
+            }
+            for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
+            if (lane == 0) a.ipp[i] = ip;
+          }
+          __syncthreads();
+        } else
+        {
         // all warps reduce one row's partials; warp 0 solves with the FP32 factor;
         // the FP64 residuals m - x V of the refinement are split over all warps
         double* xs = wsum + (kWarps - 1) * 64;  // x broadcast (the last warp's slot is read first)
@@ -492,8 +447,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
           }
           __syncthreads();
         }
+        }
       }
-      if (!grid_sync(a.bar, (unsigned)G, a.abort_flag)) { ok = false; break; }
+      if (!phase_sync(a, G)) { ok = false; break; }
       // every CTA reads the status once, after the barrier, so all leave together
       if (tid == 0) red[3] = (double)*(volatile int*)&st->status;
       __syncthreads();
@@ -606,6 +562,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
 }
 
 template <typename TM>
+__global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
+  als_body<TM>(a, blockIdx.x);
+}
+
+// Batched form: CTA b runs the whole ALS of problem b alone (G = 1).
+template <typename TM>
+__global__ void __launch_bounds__(kThreads, 1) k_als_batched(const PersArgs* __restrict__ args) {
+  const PersArgs a = args[blockIdx.x];
+  als_body<TM>(a, 0);
+}
+
+template <typename TM>
 size_t smem_bytes(const rcp_plan_s* p) {
   int lmax = 1, ftot = 0;
   for (int m = 0; m < p->N; ++m) {
@@ -668,6 +636,30 @@ bool als_persistent_fits(const rcp_plan_s* p, bool f32) {
   if (p->core_elems >= (1LL << 31)) return false;
   const size_t smem = f32 ? smem_bytes<float>(p) : smem_bytes<double>(p);
   return smem <= 200 * 1024;
+}
+
+size_t als_smem_bytes_f32(int N, int R, const int* l) {
+  int lmax = 1, ftot = 0;
+  for (int m = 0; m < N; ++m) {
+    lmax = lmax > l[m] ? lmax : l[m];
+    ftot += l[m] * R;
+  }
+  const size_t RR = R, NN = N;
+  const size_t d = NN * RR * RR + RR * (RR + 1) + RR + (size_t)lmax * RR + RR + 64 + kWarps * 64;
+  const size_t f = (RR * (RR + 1) > 1024 ? RR * (RR + 1) : 1024) + RR;
+  return d * sizeof(double) + f * sizeof(float) + 16 +
+         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * RR) * sizeof(float);
+}
+
+cudaError_t prepare_als_batched(size_t smem) {
+  return cudaFuncSetAttribute(k_als_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s) {
+  count_launches(1);
+  k_als_batched<float><<<count, kThreads, smem, s>>>(dev_args);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s) {

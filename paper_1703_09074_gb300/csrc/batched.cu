@@ -1,0 +1,801 @@
+// Batched form: hundreds of small tensors of uneven shapes decomposed together.
+//
+// Every step of the method (Algorithm 1 per mode, Algorithm 2, the recovery of
+// Eq. qbs) runs as ONE launch over all tensors of the batch:
+//   - sweeps: persistent CTAs pull (tensor, tile) work items from an atomic
+//     counter, largest tensor first (sweeps_simt.cu, FP32 CUDA cores: with
+//     l <= 24 these sweeps have <= 12 FLOP per byte and stay memory-bound);
+//   - sketch orthonormalisation: one CTA per tensor reduces the split
+//     partials and runs CholeskyQR2 (shifted CholeskyQR3 fallback) in FP64;
+//   - ALS: one CTA per tensor runs every sweep of its own problem
+//     (als_persistent.cu, FP32 MTTKRP, FP64-refined Gram solves);
+//   - recovery: one CTA per (tensor, mode), then lambda per tensor.
+// The whole sequence is captured once into a CUDA graph and replayed; the
+// input pointers reach the graph through a pinned host array copied by the
+// graph itself.  The launch shapes (CTAs per SM of the persistent sweeps and
+// columns per work item) are chosen by timing candidates on the batch.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "rcp_internal.cuh"
+#include "small_la.cuh"
+
+using namespace rcp;
+
+namespace rcp {
+
+struct BQr {
+  const double* part;   // nsplit x (I x l) split partials
+  int nsplit;
+  int64_t I;
+  int l;
+  double* Y;            // I x l sketch in, Q out (column-major)
+  double* Qout;         // optional copy target (Q_n)
+  const double* normpart;
+  int nnorm;            // > 0: sum normpart into st->norm_x2
+  DevState* st;
+};
+
+struct BProj {
+  int N, R;
+  int64_t I[kMaxN];
+  int l[kMaxN];
+  const double* Q[kMaxN];
+  const double* At[kMaxN];
+  double* A[kMaxN];
+  double* nu;           // N x R column norms
+  const double* lam_t;
+  double* lam;
+};
+
+namespace {
+
+constexpr int kQrThreads = 256;
+
+// CTA per tensor: reduce partials, then CholeskyQR2 (+ a third round after a
+// shifted first round), all in FP64.  Y is I x l column-major in global memory.
+__global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) {
+  __shared__ double Gs[kMaxL * (kMaxL + 1)];
+  __shared__ double Ri[kMaxL * kMaxL];
+  __shared__ double red[32];
+  __shared__ int flag[2];
+  const BQr p = P[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t I = p.I;
+  const int l = p.l, Pp = l + 1;
+  const int64_t n = I * l;
+  for (int64_t e = tid; e < n; e += kQrThreads) {
+    double s = 0.0;
+    for (int k = 0; k < p.nsplit; ++k) s += p.part[(int64_t)k * n + e];
+    p.Y[e] = s;
+  }
+  if (p.nnorm > 0) {
+    double s = 0.0;
+    for (int k = tid; k < p.nnorm; k += kQrThreads) s += p.normpart[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kQrThreads / 32; ++w) t += red[w];
+      p.st->norm_x2 = t;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) flag[0] = 0;
+  for (int round = 0; round < 3; ++round) {
+    __syncthreads();
+    if (round == 2 && !flag[0]) break;
+    // Gram G = Y^T Y (upper triangle, pitch l + 1)
+    for (int q = tid; q < l * (l + 1) / 2; q += kQrThreads) {
+      int c = 0, rem = q;
+      while (rem > c) {
+        rem -= c + 1;
+        ++c;
+      }
+      const int r = rem;
+      const double* y1 = p.Y + I * r;
+      const double* y2 = p.Y + I * c;
+      double s0 = 0.0, s1 = 0.0;
+      int64_t i = 0;
+      for (; i + 1 < I; i += 2) {
+        s0 = fma(y1[i], y2[i], s0);
+        s1 = fma(y1[i + 1], y2[i + 1], s1);
+      }
+      if (i < I) s0 = fma(y1[i], y2[i], s0);
+      Gs[r * Pp + c] = s0 + s1;
+    }
+    __syncthreads();
+    // Cholesky (warp 0): round 0 may fall back to the shifted Gram G + s I
+    // (shifted CholeskyQR3, then one more plain round); a failure after that
+    // is reported as singular
+    if (warp == 0) {
+      double tr = 0.0;
+      bool bad = false;
+      for (int c = 0; c < l; ++c) {
+        tr += Gs[c * Pp + c];
+        bad = bad || !isfinite(Gs[c * Pp + c]);
+      }
+      const double shift = 11.0 * ((double)I * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
+      int res = 0;  // 0 ok, 1 shifted retry needed, 2 fatal
+      if (bad) {
+        res = 2;
+        if (lane == 0) set_status(p.st, RCP_ENAN);
+      } else if (!warp_chol(Gs, l, round == 0 ? shift : 0.0)) {
+        res = round == 0 ? 1 : 2;
+        if (res == 2 && lane == 0) set_status(p.st, RCP_ESINGULAR);
+      }
+      if (lane == 0) flag[1] = res;
+    }
+    __syncthreads();
+    if (flag[1] == 2) return;
+    if (flag[1] == 1) {
+      for (int q = tid; q < l * (l + 1) / 2; q += kQrThreads) {
+        int c = 0, rem = q;
+        while (rem > c) {
+          rem -= c + 1;
+          ++c;
+        }
+        const int r = rem;
+        const double* y1 = p.Y + I * r;
+        const double* y2 = p.Y + I * c;
+        double s = 0.0;
+        for (int64_t i = 0; i < I; ++i) s = fma(y1[i], y2[i], s);
+        Gs[r * Pp + c] = s;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double tr = 0.0;
+        for (int c = 0; c < l; ++c) tr += Gs[c * Pp + c];
+        const double shift = 11.0 * ((double)I * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
+        __syncwarp();
+        for (int c = lane; c < l; c += 32) Gs[c * Pp + c] += shift;
+        __syncwarp();
+        const bool ok = warp_chol(Gs, l, 0.0);
+        if (lane == 0) {
+          flag[1] = ok ? 0 : 2;
+          flag[0] = 1;
+          atomicOr(&p.st->info, RCP_INFO_SHIFTED_QR);
+          if (!ok) set_status(p.st, RCP_ESINGULAR);
+        }
+      }
+      __syncthreads();
+      if (flag[1] == 2) return;
+    }
+    // R^{-1} by back substitution, lanes of warp 0 own columns
+    if (warp == 0) {
+      for (int c = lane; c < l; c += 32) {
+        for (int i = l - 1; i >= 0; --i) {
+          double v = 0.0;
+          if (i <= c) {
+            v = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) v -= Gs[i * Pp + k] * Ri[k * kMaxL + c];
+            v /= Gs[i * Pp + i];
+          }
+          Ri[i * kMaxL + c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // Y <- Y R^{-1}, one thread per row, in place
+    for (int64_t i = tid; i < I; i += kQrThreads) {
+      double y[kMaxL];
+      for (int k = 0; k < l; ++k) y[k] = p.Y[i + I * k];
+      for (int c = l - 1; c >= 0; --c) {
+        double s = 0.0;
+        for (int k = 0; k <= c; ++k) s = fma(y[k], Ri[k * kMaxL + c], s);
+        y[c] = s;  // y[k] for k < c still holds the input row
+      }
+      for (int c = 0; c < l; ++c) p.Y[i + I * c] = y[c];
+    }
+  }
+  __syncthreads();
+  if (p.Qout)
+    for (int64_t e = tid; e < n; e += kQrThreads) p.Qout[e] = p.Y[e];
+}
+
+// CTA (b, n): A_n = Q_n Atilde_n, its column norms, normalised in place.
+__global__ void __launch_bounds__(256) k_b_backproject(const BProj* __restrict__ P, int N) {
+  __shared__ double red[8][kMaxL];
+  const BProj& p = P[blockIdx.x / N];
+  const int n = blockIdx.x % N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t I = p.I[n];
+  const int l = p.l[n], R = p.R;
+  double nrm[kMaxL];
+  for (int r = 0; r < R; ++r) nrm[r] = 0.0;
+  for (int64_t i = tid; i < I; i += 256) {
+    for (int r = 0; r < R; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < l; ++c) s = fma(p.Q[n][i + I * c], p.At[n][c + l * r], s);
+      p.A[n][i + I * r] = s;
+      nrm[r] = fma(s, s, nrm[r]);
+    }
+  }
+  for (int r = 0; r < R; ++r) {
+    double v = nrm[r];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][r] = v;
+  }
+  __syncthreads();
+  __shared__ double inv[kMaxL];
+  if (tid < R) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][tid];
+    const double nu = sqrt(v);
+    p.nu[n * R + tid] = nu;
+    inv[tid] = nu > 0.0 ? 1.0 / nu : 0.0;
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < I * R; e += 256) p.A[n][e] *= inv[e / I];
+}
+
+__global__ void k_b_lambda(const BProj* __restrict__ P) {
+  const BProj& p = P[blockIdx.x];
+  for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+    double v = p.lam_t[r];
+    for (int n = 0; n < p.N; ++n) v *= p.nu[n * p.R + r];
+    p.lam[r] = v;
+  }
+}
+
+__global__ void k_b_state_reset(DevState* const* st, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count) {
+    DevState* s = st[b];
+    s->status = 0;
+    s->info = 0;
+    s->extra_round = 0;
+    s->als_done = 0;
+    s->als_iters = 0;
+    s->norm_x2 = 0.0;
+    s->norm_b2 = 0.0;
+    s->fit = 0.0;
+    s->fit_prev = 0.0;
+    s->ip = 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace rcp
+
+// ------------------------------------------------------------------ host side
+
+struct rcp_batched_s {
+  int count = 0;
+  int N = 3;
+  cudaStream_t stream = nullptr;
+  int nsm = 0;
+  std::vector<rcp_config> cfg;
+  struct Tn {
+    int N, R;
+    int64_t dims[kMaxN];
+    int l[kMaxN];
+    ModeView view[kMaxN];
+    int nsplit[kMaxN];
+    int64_t jchunk[kMaxN];
+    int ncolitems[kMaxN];
+    int64_t core;
+    float* buf[2];
+    double *Y, *part, *normpart, *lam, *lam_t, *nu, *rows, *ipp, *nbp, *alspart;
+    double *Q[kMaxN], *At[kMaxN], *A[kMaxN];
+    DevState* st;
+  };
+  std::vector<Tn> t;
+  char* arena = nullptr;
+  // device tables
+  BRowSweep* rowP = nullptr;   // [N][2][count]
+  BColSweep* colP = nullptr;   // [N][2][count]
+  BItem* rowItems = nullptr;   // concatenated per mode
+  BItem* colItems = nullptr;
+  std::vector<int> rowItemOff, rowItemCnt, colItemOff, colItemCnt;
+  BQr* qrP = nullptr;          // [N][3][count]: initial, power-iteration, final
+  PersArgs* alsP = nullptr;
+  BProj* projP = nullptr;
+  DevState** stPtrs = nullptr;
+  unsigned* counters = nullptr;
+  int ncounters = 0;
+  const float** xptrs_dev = nullptr;
+  const float** xptrs_host = nullptr;  // pinned
+  unsigned* dummy_bar = nullptr;
+  int* dummy_abort = nullptr;
+  size_t als_smem = 0;
+  int lmax = 1;
+  int row_grid_mult = 4, col_grid_mult = 4;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t gstream = nullptr;    // own stream: the graph is captured and replayed here
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace {
+
+#define RCPB_TRY(call)                                 \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return RCP_ECUDA;           \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void free_batched(rcp_batched_t p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->gstream) cudaStreamDestroy(p->gstream);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
+  cudaFree(p->arena);
+  cudaFree(p->rowP);
+  cudaFree(p->colP);
+  cudaFree(p->rowItems);
+  cudaFree(p->colItems);
+  cudaFree(p->qrP);
+  cudaFree(p->alsP);
+  cudaFree(p->projP);
+  cudaFree(p->stPtrs);
+  cudaFree(p->counters);
+  cudaFree(p->xptrs_dev);
+  cudaFree(p->dummy_bar);
+  cudaFree(p->dummy_abort);
+  if (p->xptrs_host) cudaFreeHost(p->xptrs_host);
+  delete p;
+}
+
+// Enqueue the whole batched decomposition on p->stream (also used under capture).
+rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
+  const int C = p->count;
+  RCPB_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned) * p->ncounters, s));
+  RCPB_TRY(cudaMemcpyAsync(p->xptrs_dev, p->xptrs_host, sizeof(float*) * C, cudaMemcpyHostToDevice, s));
+  count_launches(1);
+  k_b_state_reset<<<(C + 127) / 128, 128, 0, s>>>(p->stPtrs, C);
+  RCPB_TRY(cudaGetLastError());
+  const int rgrid = p->row_grid_mult * p->nsm, cgrid = p->col_grid_mult * p->nsm;
+  int ctr = 0;
+  const int q = p->cfg[0].power_iters;
+  for (int n = 0; n < p->N; ++n) {
+    BRowSweep* rO = p->rowP + ((size_t)n * 2 + 0) * C;
+    BRowSweep* rW = p->rowP + ((size_t)n * 2 + 1) * C;
+    BColSweep* cW = p->colP + ((size_t)n * 2 + 0) * C;
+    BColSweep* cT = p->colP + ((size_t)n * 2 + 1) * C;
+    const BItem* ri = p->rowItems + p->rowItemOff[n];
+    const BItem* ci = p->colItems + p->colItemOff[n];
+    RCPB_TRY(launch_b_row_sweep(rO, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, false,
+                                p->xptrs_dev, rgrid, s));
+    count_launches(1);
+    k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (q == 0 ? 2 : 0)) * C);
+    RCPB_TRY(cudaGetLastError());
+    for (int it = 0; it < q; ++it) {
+      RCPB_TRY(launch_b_col_sweep(cW, ci, p->colItemCnt[n], p->counters + ctr++, p->lmax,
+                                  p->xptrs_dev, cgrid, s));
+      RCPB_TRY(launch_b_row_sweep(rW, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, true,
+                                  p->xptrs_dev, rgrid, s));
+      count_launches(1);
+      k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (it == q - 1 ? 2 : 1)) * C);
+      RCPB_TRY(cudaGetLastError());
+    }
+    RCPB_TRY(launch_b_col_sweep(cT, ci, p->colItemCnt[n], p->counters + ctr++, p->lmax,
+                                p->xptrs_dev, cgrid, s));
+  }
+  RCPB_TRY(launch_als_batched(p->alsP, C, p->als_smem, s));
+  count_launches(2);
+  k_b_backproject<<<C * p->N, 256, 0, s>>>(p->projP, p->N);
+  RCPB_TRY(cudaGetLastError());
+  k_b_lambda<<<C, 64, 0, s>>>(p->projP);
+  RCPB_TRY(cudaGetLastError());
+  return RCP_OK;
+}
+
+rcp_status build_tables(rcp_batched_t p) {
+  const int C = p->count, N = p->N;
+  std::vector<BRowSweep> rowP((size_t)N * 2 * C);
+  std::vector<BColSweep> colP((size_t)N * 2 * C);
+  std::vector<BQr> qrP((size_t)N * 3 * C);
+  std::vector<BItem> rItems, cItems;
+  p->rowItemOff.assign(N, 0);
+  p->rowItemCnt.assign(N, 0);
+  p->colItemOff.assign(N, 0);
+  p->colItemCnt.assign(N, 0);
+  // largest tensors first
+  std::vector<int> order(C);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return p->t[a].view[0].I * p->t[a].view[0].J > p->t[b].view[0].I * p->t[b].view[0].J;
+  });
+  for (int n = 0; n < N; ++n) {
+    p->rowItemOff[n] = (int)rItems.size();
+    p->colItemOff[n] = (int)cItems.size();
+    for (int b : order) {
+      auto& t = p->t[b];
+      const ModeView v = t.view[n];
+      const int l = t.l[n];
+      const float* Tin = n == 0 ? nullptr : t.buf[(n - 1) % 2];
+      float* Wout = t.buf[n % 2];
+      const int gx = sweep_row_blocks(v.I);
+      for (int by = 0; by < t.nsplit[n]; ++by)
+        for (int bx = 0; bx < gx; ++bx) rItems.push_back(BItem{b, bx, by});
+      for (int bx = 0; bx < t.ncolitems[n]; ++bx) cItems.push_back(BItem{b, bx, 0});
+      BRowSweep r{};
+      r.T = Tin;
+      r.v = v;
+      r.rows_per_cta = sweep_rows_per_cta(v.I);
+      r.l = l;
+      r.seed = p->cfg[b].seed;
+      r.sid = (uint32_t)(n + 1);
+      r.W = nullptr;
+      r.jchunk = t.jchunk[n];
+      r.part = t.part;
+      r.normpart = n == 0 ? t.normpart : nullptr;
+      r.gx = gx;
+      rowP[((size_t)n * 2 + 0) * C + b] = r;
+      r.W = Wout;
+      r.normpart = nullptr;
+      rowP[((size_t)n * 2 + 1) * C + b] = r;
+      BColSweep c{};
+      c.T = Tin;
+      c.v = v;
+      c.l = l;
+      c.Q = t.Y;
+      c.W = Wout;
+      c.nb = t.ncolitems[n];
+      colP[((size_t)n * 2 + 0) * C + b] = c;
+      c.Q = t.Q[n];
+      colP[((size_t)n * 2 + 1) * C + b] = c;
+      for (int kind = 0; kind < 3; ++kind) {
+        BQr qr{};
+        qr.part = t.part;
+        qr.nsplit = t.nsplit[n];
+        qr.I = v.I;
+        qr.l = l;
+        qr.Y = t.Y;
+        qr.Qout = kind == 2 ? t.Q[n] : nullptr;
+        qr.normpart = t.normpart;
+        qr.nnorm = (n == 0 && kind != 1) ? t.nsplit[0] * gx : 0;
+        qr.st = t.st;
+        qrP[((size_t)n * 3 + kind) * C + b] = qr;
+      }
+    }
+    p->rowItemCnt[n] = (int)rItems.size() - p->rowItemOff[n];
+    p->colItemCnt[n] = (int)cItems.size() - p->colItemOff[n];
+  }
+  // ALS and recovery
+  std::vector<PersArgs> als(C);
+  std::vector<BProj> proj(C);
+  std::vector<DevState*> sts(C);
+  for (int b = 0; b < C; ++b) {
+    auto& t = p->t[b];
+    PersArgs a{};
+    a.N = N;
+    a.R = t.R;
+    a.G = 1;
+    a.GA = 1;
+    for (int m = 0; m < N; ++m) {
+      a.dims[m] = t.l[m];
+      a.At[m] = t.At[m];
+    }
+    a.B = t.buf[(N - 1) % 2];
+    a.lam = t.lam_t;
+    a.part = t.alspart;
+    a.rows = t.rows;
+    a.ipp = t.ipp;
+    a.nbp = t.nbp;
+    a.bar = p->dummy_bar;
+    a.abort_flag = p->dummy_abort;
+    a.st = t.st;
+    a.seed = p->cfg[b].seed;
+    a.tol = p->cfg[b].tol;
+    a.max_iters = p->cfg[b].max_iters;
+    a.user_init = 0;
+    als[b] = a;
+    BProj pr{};
+    pr.N = N;
+    pr.R = t.R;
+    for (int m = 0; m < N; ++m) {
+      pr.I[m] = t.dims[m];
+      pr.l[m] = t.l[m];
+      pr.Q[m] = t.Q[m];
+      pr.At[m] = t.At[m];
+      pr.A[m] = t.A[m];
+    }
+    pr.nu = t.nu;
+    pr.lam_t = t.lam_t;
+    pr.lam = t.lam;
+    proj[b] = pr;
+    sts[b] = t.st;
+  }
+  auto up = [&](auto** dst, const auto& v) -> bool {
+    using T = typename std::remove_reference<decltype(v[0])>::type;
+    if (cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1)) != cudaSuccess) return false;
+    return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up(&p->rowP, rowP) || !up(&p->colP, colP) || !up(&p->qrP, qrP) || !up(&p->rowItems, rItems) ||
+      !up(&p->colItems, cItems) || !up(&p->alsP, als) || !up(&p->projP, proj) || !up(&p->stPtrs, sts))
+    return RCP_ENOMEM;
+  return RCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream, rcp_batched_t* out) {
+  if (!cfgs || !out || count < 1 || count > (1 << 20)) return RCP_EINVAL;
+  const int N = cfgs[0].ndim;
+  for (int b = 0; b < count; ++b) {
+    const rcp_config& c = cfgs[b];
+    if (c.ndim != N || N < 2 || N > kMaxN) return RCP_EINVAL;
+    if (c.in_dtype != RCP_DTYPE_F32 || c.precision != RCP_PREC_MIXED) return RCP_EINVAL;
+    if (c.power_iters != cfgs[0].power_iters || c.power_iters < 0) return RCP_EINVAL;
+    if (c.rank < 1 || c.rank > 32 || c.oversample < 0 || c.max_iters < 1 || !(c.tol >= 0.0))
+      return RCP_EINVAL;
+    int64_t cur[kMaxN];
+    for (int n = 0; n < N; ++n) {
+      if (c.dims[n] < 1 || c.dims[n] > (1LL << 24)) return RCP_EINVAL;
+      cur[n] = c.dims[n];
+    }
+    for (int n = 0; n < N; ++n) {
+      int64_t J = 1;
+      for (int m = 0; m < N; ++m)
+        if (m != n) J *= cur[m];
+      const int64_t l = std::min<int64_t>((int64_t)c.rank + c.oversample, std::min(cur[n], J));
+      if (l < c.rank || l > 32) return RCP_EINVAL;
+      cur[n] = l;
+    }
+  }
+  rcp_batched_t p = new (std::nothrow) rcp_batched_s();
+  if (!p) return RCP_ENOMEM;
+  p->count = count;
+  p->N = N;
+  p->stream = (cudaStream_t)stream;
+  p->cfg.assign(cfgs, cfgs + count);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete p;
+    return RCP_ECUDA;
+  }
+  // per-tensor sizes
+  p->t.resize(count);
+  size_t bytes = 0;
+  std::vector<size_t> off(count);
+  for (int b = 0; b < count; ++b) {
+    auto& t = p->t[b];
+    const rcp_config& c = cfgs[b];
+    t.N = N;
+    t.R = c.rank;
+    int64_t cur[kMaxN];
+    for (int n = 0; n < N; ++n) cur[n] = t.dims[n] = c.dims[n];
+    int64_t bufmax = 1, partmax = 1, Imax = 1;
+    for (int n = 0; n < N; ++n) {
+      int64_t J = 1, L = 1, Rt = 1;
+      for (int m = 0; m < N; ++m)
+        if (m != n) J *= cur[m];
+      for (int m = 0; m < n; ++m) L *= cur[m];
+      for (int m = n + 1; m < N; ++m) Rt *= cur[m];
+      const int l = (int)std::min<int64_t>((int64_t)c.rank + c.oversample, std::min(cur[n], J));
+      t.l[n] = l;
+      t.view[n] = ModeView{L, cur[n], Rt, J};
+      // about 2048 columns per row-sweep item, at most 64 splits
+      int ns = (int)std::min<int64_t>(64, std::max<int64_t>(1, (J + 2047) / 2048));
+      t.nsplit[n] = ns;
+      t.jchunk[n] = (J + ns - 1) / ns;
+      t.ncolitems[n] = (int)std::max<int64_t>(1, (J + 1023) / 1024);  // 4 blocks of 256 columns
+      bufmax = std::max(bufmax, J * l);
+      partmax = std::max(partmax, (int64_t)ns * cur[n] * l);
+      Imax = std::max(Imax, cur[n]);
+      cur[n] = l;
+      p->lmax = std::max(p->lmax, l);
+    }
+    t.core = 1;
+    for (int n = 0; n < N; ++n) t.core *= t.l[n];
+    off[b] = bytes;
+    bytes += 2 * align256(bufmax * sizeof(float));
+    bytes += align256(Imax * 32 * sizeof(double));                      // Y
+    bytes += align256(partmax * sizeof(double));                        // part
+    bytes += align256((size_t)64 * sweep_row_blocks(t.dims[0]) * sizeof(double));  // normpart
+    for (int n = 0; n < N; ++n) {
+      bytes += align256(t.dims[n] * t.l[n] * sizeof(double));          // Q_n
+      bytes += align256((size_t)t.l[n] * t.R * sizeof(double));        // At_n
+      bytes += align256(t.dims[n] * t.R * sizeof(double));             // A_n
+    }
+    bytes += 3 * align256(t.R * sizeof(double) * kMaxN);                // lam, lam_t, nu
+    bytes += 3 * align256((size_t)32 * 32 * sizeof(double));            // rows, alspart, ipp
+    bytes += align256(sizeof(double)) + align256(sizeof(DevState));     // nbp, state
+  }
+  if (cudaMalloc((void**)&p->arena, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    free_batched(p);
+    return RCP_ENOMEM;
+  }
+  for (int b = 0; b < count; ++b) {
+    auto& t = p->t[b];
+    char* q = p->arena + off[b];
+    auto take = [&](size_t n) {
+      char* r = q;
+      q += align256(n);
+      return r;
+    };
+    int64_t bufmax = 1, partmax = 1, Imax = 1;
+    for (int n = 0; n < N; ++n) {
+      bufmax = std::max(bufmax, t.view[n].J * t.l[n]);
+      partmax = std::max(partmax, (int64_t)t.nsplit[n] * t.view[n].I * t.l[n]);
+      Imax = std::max(Imax, t.view[n].I);
+    }
+    t.buf[0] = (float*)take(bufmax * sizeof(float));
+    t.buf[1] = (float*)take(bufmax * sizeof(float));
+    t.Y = (double*)take(Imax * 32 * sizeof(double));
+    t.part = (double*)take(partmax * sizeof(double));
+    t.normpart = (double*)take((size_t)64 * sweep_row_blocks(t.dims[0]) * sizeof(double));
+    for (int n = 0; n < N; ++n) {
+      t.Q[n] = (double*)take(t.dims[n] * t.l[n] * sizeof(double));
+      t.At[n] = (double*)take((size_t)t.l[n] * t.R * sizeof(double));
+      t.A[n] = (double*)take(t.dims[n] * t.R * sizeof(double));
+    }
+    t.lam = (double*)take(t.R * sizeof(double) * kMaxN);
+    t.lam_t = (double*)take(t.R * sizeof(double) * kMaxN);
+    t.nu = (double*)take(t.R * sizeof(double) * kMaxN);
+    t.rows = (double*)take((size_t)32 * 32 * sizeof(double));
+    t.alspart = (double*)take((size_t)32 * 32 * sizeof(double));
+    t.ipp = (double*)take((size_t)32 * 32 * sizeof(double));
+    t.nbp = (double*)take(sizeof(double));
+    t.st = (DevState*)take(sizeof(DevState));
+  }
+  // counters: one per batched sweep launch
+  p->ncounters = N * (2 + 2 * std::max(0, cfgs[0].power_iters)) + 4;
+  int lsm[kMaxN];
+  size_t smax = 0;
+  for (int b = 0; b < count; ++b) {
+    for (int n = 0; n < N; ++n) lsm[n] = p->t[b].l[n];
+    smax = std::max(smax, als_smem_bytes_f32(N, p->t[b].R, lsm));
+  }
+  p->als_smem = smax;
+  if (cudaMalloc((void**)&p->counters, sizeof(unsigned) * p->ncounters) != cudaSuccess ||
+      cudaMalloc((void**)&p->xptrs_dev, sizeof(float*) * count) != cudaSuccess ||
+      cudaMallocHost((void**)&p->xptrs_host, sizeof(float*) * count) != cudaSuccess ||
+      cudaMalloc((void**)&p->dummy_bar, 16) != cudaSuccess ||
+      cudaMalloc((void**)&p->dummy_abort, 16) != cudaSuccess) {
+    cudaGetLastError();
+    free_batched(p);
+    return RCP_ENOMEM;
+  }
+  memset(p->xptrs_host, 0, sizeof(float*) * count);
+  if (cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      prepare_als_batched(p->als_smem) != cudaSuccess) {
+    cudaGetLastError();
+    free_batched(p);
+    return RCP_ECUDA;
+  }
+  rcp_status st = build_tables(p);
+  if (st != RCP_OK) {
+    free_batched(p);
+    return st;
+  }
+  *out = p;
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_destroy(rcp_batched_t plan) {
+  if (!plan) return RCP_OK;
+  cudaStreamSynchronize(plan->stream);
+  if (plan->gstream) cudaStreamSynchronize(plan->gstream);
+  free_batched(plan);
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_run(rcp_batched_t p, const void* const* X_dev) {
+  if (!p || !X_dev) return RCP_EINVAL;
+  for (int b = 0; b < p->count; ++b)
+    if (!X_dev[b]) return RCP_EINVAL;
+  // the graph copies this pinned array when it runs, so wait for the previous run
+  RCPB_TRY(cudaStreamSynchronize(p->gstream));
+  for (int b = 0; b < p->count; ++b) p->xptrs_host[b] = (const float*)X_dev[b];
+  if (!p->exec) {
+    RCPB_TRY(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    const rcp_status st = enqueue_batched(p, p->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->gstream, &g);
+    if (st != RCP_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != RCP_OK ? st : RCP_ECUDA;
+    }
+    p->graph = g;
+    if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return RCP_ECUDA;
+    }
+  }
+  // order the replay after earlier work on the caller's stream, and later work after it
+  RCPB_TRY(cudaEventRecord(p->ev_in, p->stream));
+  RCPB_TRY(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
+  count_launches(1);
+  RCPB_TRY(cudaGraphLaunch(p->exec, p->gstream));
+  RCPB_TRY(cudaEventRecord(p->ev_out, p->gstream));
+  RCPB_TRY(cudaStreamWaitEvent(p->stream, p->ev_out, 0));
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_autotune(rcp_batched_t p, const void* const* X_dev, int32_t* choice) {
+  if (!p || !X_dev) return RCP_EINVAL;
+  for (int b = 0; b < p->count; ++b) p->xptrs_host[b] = (const float*)X_dev[b];
+  const int cands[] = {1, 2, 4, 8};
+  cudaEvent_t a, b2;
+  RCPB_TRY(cudaEventCreate(&a));
+  RCPB_TRY(cudaEventCreate(&b2));
+  float best = 1e30f;
+  int br = 4, bc = 4;
+  for (int r : cands) {
+    for (int c : cands) {
+      p->row_grid_mult = r;
+      p->col_grid_mult = c;
+      RCPB_TRY(cudaStreamSynchronize(p->stream));
+      RCPB_TRY(cudaStreamSynchronize(p->gstream));
+      if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;  // warm
+      RCPB_TRY(cudaEventRecord(a, p->gstream));
+      if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;
+      RCPB_TRY(cudaEventRecord(b2, p->gstream));
+      RCPB_TRY(cudaEventSynchronize(b2));
+      float ms = 0.0f;
+      RCPB_TRY(cudaEventElapsedTime(&ms, a, b2));
+      if (ms < best) {
+        best = ms;
+        br = r;
+        bc = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b2);
+  p->row_grid_mult = br;
+  p->col_grid_mult = bc;
+  if (p->exec) {  // re-capture with the chosen shapes on the next run
+    cudaGraphExecDestroy(p->exec);
+    cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+  }
+  if (choice) {
+    choice[0] = br;
+    choice[1] = bc;
+  }
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_result(rcp_batched_t p, int32_t index, double* const* A_dev,
+                              double* lambda_dev, rcp_result* res) {
+  if (!p || index < 0 || index >= p->count) return RCP_EINVAL;
+  const auto& t = p->t[index];
+  cudaStream_t s = p->stream;
+  if (A_dev)
+    for (int n = 0; n < p->N; ++n)
+      if (A_dev[n])
+        RCPB_TRY(cudaMemcpyAsync(A_dev[n], t.A[n], sizeof(double) * t.dims[n] * t.R,
+                                 cudaMemcpyDeviceToDevice, s));
+  if (lambda_dev)
+    RCPB_TRY(cudaMemcpyAsync(lambda_dev, t.lam, sizeof(double) * t.R, cudaMemcpyDeviceToDevice, s));
+  DevState h;
+  RCPB_TRY(cudaMemcpyAsync(&h, t.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  RCPB_TRY(cudaStreamSynchronize(s));
+  if (res) {
+    memset(res, 0, sizeof(*res));
+    res->fit = h.fit;
+    res->iters = h.als_iters;
+    res->info = h.info;
+    res->norm_x2 = h.norm_x2;
+    res->norm_b2 = h.norm_b2;
+    const double r2 = h.norm_x2 - h.fit * h.norm_b2;
+    res->rel_err = h.norm_x2 > 0.0 ? sqrt(std::max(r2, 0.0) / h.norm_x2) : 0.0;
+    res->device_status = h.status;
+    for (int n = 0; n < p->N; ++n) res->widths[n] = t.l[n];
+  }
+  return (rcp_status)h.status;
+}
+
+}  // extern "C"

@@ -186,6 +186,57 @@ __device__ __forceinline__ void set_status(DevState* st, int code) {
   atomicCAS(&st->status, 0, code);
 }
 
+// Arguments of one CP-ALS problem for the persistent ALS kernel (als_persistent.cu).
+struct PersArgs {
+  int N, R, G;
+  int GA;                // CTAs that compute MTTKRP partials (GA <= G)
+  int dims[kMaxN];       // l_1..l_N
+  const void* B;         // TM, Kolda layout
+  double* At[kMaxN];     // out: normalised factors (column-major l_n x R); in: user init
+  double* lam;           // out: lambda
+  double* part;          // G x (l_max x R) MTTKRP partials
+  double* rows;          // l_max x R new factor rows (unnormalised)
+  double* ipp;           // l_max partial inner products
+  double* nbp;           // G partial |B|^2
+  unsigned* bar;         // grid barrier: count, generation
+  int* abort_flag;
+  DevState* st;
+  uint64_t seed;
+  double tol;
+  int max_iters;
+  int user_init;
+};
+
+// ---------------------------------------------------------------- batched form
+struct BItem {
+  int b;   // tensor index
+  int bx;  // block coordinates within that tensor's grid
+  int by;
+};
+
+struct BRowSweep {  // P = T_(n) V for one tensor (V = Omega_n or W)
+  const float* T;
+  ModeView v;
+  int64_t rows_per_cta;
+  int l;
+  uint64_t seed;
+  uint32_t sid;
+  const float* W;
+  int64_t jchunk;
+  double* part;
+  double* normpart;
+  int gx;
+};
+
+struct BColSweep {  // W = T_(n)^T Q for one tensor, W in the Kolda layout of T_{n+1}
+  const float* T;
+  ModeView v;
+  int l;
+  const double* Q;
+  float* W;
+  int nb;
+};
+
 // ---------------------------------------------------------------- launchers
 // Sweeps over the working tensor (sweeps_f64.cu).
 cudaError_t launch_sketch_f64(const void* T, int in_dtype, ModeView v, int l, uint64_t seed,
@@ -201,6 +252,13 @@ cudaError_t launch_project_f32(const float* T, ModeView v, int l, const double* 
 cudaError_t launch_mttkrp_f64(const double* B, ModeView v, int R, const KrDims& kr, int nsplit,
                               double* part, cudaStream_t s);
 int project_grid(const ModeView& v, int nsm);
+cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitems, unsigned* counter,
+                               int lmax, bool use_w, const float* const* xptrs, int grid,
+                               cudaStream_t s);
+cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitems, unsigned* counter,
+                               int lmax, const float* const* xptrs, int grid, cudaStream_t s);
+int sweep_rows_per_cta(int64_t I);
+int sweep_row_blocks(int64_t I);
 int sketch_splits(const ModeView& v, int nsm);
 
 // Tensor-core mode-1 sweeps of the mixed-precision form (tc_sweeps.cu).
@@ -235,6 +293,9 @@ cudaError_t launch_als_sweep(rcp_plan_s* p, int mode0, cudaStream_t s);
 cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lambda_dev,
                                cudaStream_t s);
 bool als_persistent_fits(const rcp_plan_s* p, bool f32);
+size_t als_smem_bytes_f32(int N, int R, const int* l);
+cudaError_t prepare_als_batched(size_t smem);
+cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s);
 cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s);
 cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* dst, cudaStream_t s);

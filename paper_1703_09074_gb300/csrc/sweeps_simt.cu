@@ -21,17 +21,24 @@ constexpr int kProjRows = 32;     // rows of Q staged per step of the column swe
 
 enum { kSrcOmega = 0, kSrcW = 1, kSrcKr = 2 };
 
+}  // namespace
+
+// Row sweep body for block (bx, by) of a (gx, gy) grid: rows bx * rows_per_cta +
+// [0, rows_per_cta), columns by * jchunk + [0, jchunk).
 template <int LMAX, typename TIn, typename TA, int SRC, bool NORM>
-__global__ void __launch_bounds__(256)
-k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, uint64_t seed,
-            uint32_t sid, const TA* __restrict__ W, KrDims kr, int64_t jchunk,
-            double* __restrict__ part, double* __restrict__ normpart) {
+__device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeView v,
+                                               int64_t rows_per_cta, int l, uint64_t seed,
+                                               uint32_t sid, const TA* __restrict__ W,
+                                               const KrDims& kr, int64_t jchunk,
+                                               double* __restrict__ part,
+                                               double* __restrict__ normpart, int bx, int by,
+                                               int gx) {
   __shared__ TA Vs[kRowTile][LMAX];
   __shared__ int64_t offs[kRowTile];
   const int tid = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * rows_per_cta + tid;
+  const int64_t i = (int64_t)bx * rows_per_cta + tid;
   const bool row_ok = (tid < rows_per_cta) && (i < v.I);
-  const int64_t j0 = (int64_t)blockIdx.y * jchunk;
+  const int64_t j0 = (int64_t)by * jchunk;
   const int64_t j1 = min(v.J, j0 + jchunk);
 
   TA acc[LMAX];
@@ -108,7 +115,7 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
   if (row_ok) {
 #pragma unroll
     for (int c = 0; c < LMAX; ++c)
-      if (c < l) part[((int64_t)blockIdx.y * l + c) * v.I + i] = (double)acc[c];
+      if (c < l) part[((int64_t)by * l + c) * v.I + i] = (double)acc[c];
   }
   if (NORM) {
     __shared__ double red[256];
@@ -118,14 +125,33 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
       if (tid < s && tid + s < (int)blockDim.x) red[tid] += red[tid + s];
       __syncthreads();
     }
-    if (tid == 0) normpart[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    if (tid == 0) normpart[(int64_t)by * gx + bx] = red[0];
   }
 }
 
+// Column sweep body for CTA bx of nb persistent CTAs.
 template <int LMAX, typename TIn, typename TA, bool GRAM>
-__global__ void __launch_bounds__(kProjThreads)
-k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
-            TA* __restrict__ W, double* __restrict__ gpart) {
+__device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
+                                               const double* __restrict__ Q, TA* __restrict__ W,
+                                               double* __restrict__ gpart, int bx, int nb);
+
+namespace {
+
+template <int LMAX, typename TIn, typename TA, int SRC, bool NORM>
+__global__ void __launch_bounds__(256)
+k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, uint64_t seed,
+            uint32_t sid, const TA* __restrict__ W, KrDims kr, int64_t jchunk,
+            double* __restrict__ part, double* __restrict__ normpart) {
+  row_sweep_body<LMAX, TIn, TA, SRC, NORM>(T, v, rows_per_cta, l, seed, sid, W, kr, jchunk, part,
+                                           normpart, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+}  // namespace
+
+template <int LMAX, typename TIn, typename TA, bool GRAM>
+__device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
+                                               const double* __restrict__ Q, TA* __restrict__ W,
+                                               double* __restrict__ gpart, int bx, int nb) {
   extern __shared__ double sm[];
   TA* Qs = (TA*)sm;                                 // kProjRows x LMAX
   double* Ws = sm + kProjRows * LMAX;               // kProjThreads x (LMAX + 1), GRAM only
@@ -141,7 +167,7 @@ k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restri
     for (int c2 = tid; c2 < l; ++c2) pairs[base + c2 - tid] = (unsigned short)((tid << 8) | c2);
   }
 
-  for (int64_t jb = blockIdx.x; jb * kProjThreads < v.J; jb += gridDim.x) {
+  for (int64_t jb = bx; jb * kProjThreads < v.J; jb += nb) {
     const int64_t j = jb * kProjThreads + tid;
     const bool ok = j < v.J;
     const int64_t a = ok ? j % v.L : 0, b = ok ? j / v.L : 0;
@@ -191,9 +217,18 @@ k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restri
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
       const int p = tid + s * kProjThreads;
-      if (p < npairs) gpart[(int64_t)blockIdx.x * npairs + p] = gacc[s];
+      if (p < npairs) gpart[(int64_t)bx * npairs + p] = gacc[s];
     }
   }
+}
+
+namespace {
+
+template <int LMAX, typename TIn, typename TA, bool GRAM>
+__global__ void __launch_bounds__(kProjThreads)
+k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
+            TA* __restrict__ W, double* __restrict__ gpart) {
+  col_sweep_body<LMAX, TIn, TA, GRAM>(T, v, l, Q, W, gpart, blockIdx.x, gridDim.x);
 }
 
 int lmax_bucket(int l) { return l <= 16 ? 16 : l <= 32 ? 32 : l <= 48 ? 48 : 64; }
@@ -284,6 +319,101 @@ int project_grid(const ModeView& v, int nsm) {
   const int64_t cap = 4LL * nsm;
   return (int)(blocks < cap ? (blocks < 1 ? 1 : blocks) : cap);
 }
+
+// ---------------------------------------------------------------- batched sweeps
+// One launch covers the same sweep of every tensor of a batch: persistent CTAs
+// pull work items (tensor b, block coordinates) from an atomic counter; the
+// host orders the items largest tensor first.
+
+namespace {
+
+template <int LMAX, int SRC>
+__global__ void __launch_bounds__(256)
+k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
+              unsigned* counter, const float* const* __restrict__ xptrs) {
+  __shared__ int item_sh;
+  const KrDims kr{};
+  for (;;) {
+    if (threadIdx.x == 0) item_sh = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item_sh;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BItem w = items[it];
+    const BRowSweep p = P[w.b];
+    const float* T = p.T ? p.T : xptrs[w.b];  // mode 1 reads the caller's tensor
+    if (p.normpart)
+      row_sweep_body<LMAX, float, float, SRC, true>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid,
+                                                    p.W, kr, p.jchunk, p.part, p.normpart, w.bx,
+                                                    w.by, p.gx);
+    else
+      row_sweep_body<LMAX, float, float, SRC, false>(T, p.v, p.rows_per_cta, p.l, p.seed,
+                                                     p.sid, p.W, kr, p.jchunk, p.part, nullptr,
+                                                     w.bx, w.by, p.gx);
+    __syncthreads();
+  }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(kProjThreads)
+k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
+              unsigned* counter, const float* const* __restrict__ xptrs) {
+  __shared__ int item_sh;
+  for (;;) {
+    if (threadIdx.x == 0) item_sh = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item_sh;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BItem w = items[it];
+    const BColSweep p = P[w.b];
+    col_sweep_body<LMAX, float, float, false>(p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr,
+                                              w.bx, p.nb);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitems, unsigned* counter,
+                               int lmax, bool use_w, const float* const* xptrs, int grid,
+                               cudaStream_t s) {
+  count_launches(1);
+  const int b = lmax_bucket(lmax);
+  if (use_w) {
+    if (b == 16) k_b_row_sweep<16, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else if (b == 32) k_b_row_sweep<32, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else return cudaErrorInvalidValue;
+  } else {
+    if (b == 16) k_b_row_sweep<16, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else if (b == 32) k_b_row_sweep<32, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitems, unsigned* counter,
+                               int lmax, const float* const* xptrs, int grid, cudaStream_t s) {
+  count_launches(1);
+  const int b = lmax_bucket(lmax);
+  if (b == 16) {
+    const size_t smem = (size_t)kProjRows * 16 * sizeof(double);
+    k_b_col_sweep<16><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+  } else if (b == 32) {
+    const size_t smem = (size_t)kProjRows * 32 * sizeof(double);
+    k_b_col_sweep<32><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int sweep_rows_per_cta(int64_t I) {
+  const int64_t nib = (I + 255) / 256;
+  return (int)((I + nib - 1) / nib);
+}
+
+int sweep_row_blocks(int64_t I) { return (int)((I + 255) / 256); }
 
 cudaError_t launch_sketch_f64(const void* T, int in_dtype, ModeView v, int l, uint64_t seed,
                               uint32_t stream_id, const double* W, int nsplit, double* part,

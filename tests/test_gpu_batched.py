@@ -1,0 +1,71 @@
+"""Batched form against the single-problem mixed path and the oracle (needs a GB300)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(count, seed, lo=20, hi=90, rlo=3, rhi=8, iters=30, tol=0.0):
+    shapes = synth.batch_shapes(count, seed, lo=lo, hi=hi, rlo=rlo, rhi=rhi)
+    ws, probs = [], []
+    for b, s in enumerate(shapes):
+        w = synth.cp_tensor(s["dims"], s["R"], seed=1000 + b, congruence=0.0,
+                            snr_db=25.0, dtype="f32", p=8, q=1)
+        ws.append(w)
+        probs.append(dict(dims=w.dims, rank=w.rank, oversample=8, power_iters=1, tol=tol,
+                          max_iters=iters, seed=77 + b))
+    return ws, probs
+
+
+def test_batched_matches_single_problem_mixed_path_and_replays():
+    from paper_1703_09074_gb300 import BatchedPlan, Plan
+    ws, probs = _problems(12, seed=3)
+    Xs = [torch.from_numpy(w.kolda).cuda() for w in ws]
+    with BatchedPlan(probs) as bp:
+        bp.run(Xs)
+        first = [bp.result(b) for b in range(len(ws))]
+        bp.run(Xs)  # graph replay
+        second = [bp.result(b) for b in range(len(ws))]
+        choice = bp.autotune(Xs)
+        bp.run(Xs)
+        third = [bp.result(b) for b in range(len(ws))]
+    assert all(c in (1, 2, 4, 8) for c in choice)
+    for b, (w, pr) in enumerate(zip(ws, probs)):
+        A1, l1, r1 = first[b]
+        assert r1["device_status"] == 0, (b, r1)
+        # replay and relaunch with other launch shapes give bit-identical results
+        for A2, l2, _r in (second[b], third[b]):
+            assert torch.equal(l1, l2)
+            for a, c in zip(A1, A2):
+                assert torch.equal(a, c)
+        # the reported relative error is the one of the returned factors: the
+        # identity 1 - rho |B|^2 / |X|^2 has FP32 sweep rounding (~3e-7) in |B|^2,
+        # amplified by 1 / rel_err^2 (<= 1e3 here) and halved by the square root
+        direct = oracle.rcp.rel_error(w.X, l1.cpu().numpy(), [a.cpu().numpy() for a in A1])
+        assert r1["rel_err"] == pytest.approx(direct, rel=2e-4)
+        # same problem through the single-problem mixed path
+        with Plan(w.dims, w.rank, 8, 1, 0.0, pr["max_iters"], seed=pr["seed"],
+                  in_dtype=torch.float32, precision="mixed") as p:
+            A, lam = p.decompose(Xs[b])
+            rs = p.result()
+        assert r1["rel_err"] == pytest.approx(rs["rel_err"], rel=1e-3)
+
+
+def test_batched_compression_matches_oracle_same_stream():
+    from paper_1703_09074_gb300 import BatchedPlan
+    ws, probs = _problems(6, seed=5, iters=200, tol=1e-12)
+    Xs = [torch.from_numpy(w.kolda).cuda() for w in ws]
+    with BatchedPlan(probs) as bp:
+        bp.run(Xs)
+        res = [bp.result(b) for b in range(len(ws))]
+    for b, (w, pr) in enumerate(zip(ws, probs)):
+        o = oracle.rcp.rcp_als(w.X, w.rank, 8, 1, 1e-12, 200, pr["seed"], omega="f32")
+        # |X|^2 and |B|^2 pin the compression: equal within FP32 sweep rounding
+        assert res[b][2]["norm_x2"] == pytest.approx(o["normX2"], rel=1e-5)
+        assert res[b][2]["norm_b2"] == pytest.approx(o["normB2"], rel=1e-4)
+        assert res[b][2]["rel_err"] == pytest.approx(o["rel_err_identity"], rel=1e-3)
