@@ -38,6 +38,9 @@ WORKLOADS = {
                                   "ALS <=50 sweeps or fit change <1e-10, seed 0"),
     "c4": ("c4_flow_512x1024x800_f32", "512x1024x800 FP32 flow-like, R=10, SNR 20 dB, p=10, q=2, "
                                        "ALS <=50 sweeps or fit change <1e-10, seed 0"),
+    "c5": ("batch256", "256 3-way FP32 tensors, I_n ~ U{32..256}, R ~ U{3..16}, congruence "
+                       "U[0,0.6], SNR U[10,30] dB, p=8, q=1, ALS <=50 sweeps or fit change <1e-10, "
+                       "one CUDA graph"),
 }
 
 # GB300 FP64 arithmetic peak used for ALU-bound FP64 kernels: 152 SMs x 2 FP64
@@ -130,6 +133,25 @@ def cpu_baseline(w, budget_s=30.0):
     return {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "one whole decomposition of the same workload (numpy FP64 oracle, "
                       "BLAS threads = all host cores)"}
+
+
+def cpu_baseline_batch(ws, budget_s=15.0):
+    """The FP64 oracle on the first tensors of the batch, scaled to the whole batch by bytes."""
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    nb = 0
+    for b, w in enumerate(ws):
+        oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, b)
+        done += 1
+        nb += w.kolda.nbytes
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    total = sum(w.kolda.nbytes for w in ws)
+    return {"value": dt * total / nb, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the first {done} of {len(ws)} tensors decomposed by the numpy FP64 "
+                      f"oracle in {dt:.1f} s, scaled to the batch by input bytes"}
 
 
 def run_reference(args):
@@ -316,10 +338,68 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched workload: one step = one replay of the batch's CUDA graph."""
+    import torch
+    import synth
+    from paper_1703_09074_gb300 import BatchedPlan
+    from paper_1703_09074_gb300 import _lib
+
+    ws_, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ws = synth.batch(256, seed=0, p=8, q=1)
+    Xs = [torch.from_numpy(w.kolda).to(dev) for w in ws]
+    probs = [dict(dims=w.dims, rank=w.rank, oversample=8, power_iters=1, tol=1e-10,
+                  max_iters=50, seed=b) for b, w in enumerate(ws)]
+    stream = torch.cuda.current_stream(dev)
+    bp = BatchedPlan(probs, stream=stream)
+    choice = bp.autotune(Xs)
+    for _ in range(args.warmup):
+        bp.run(Xs)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        bp.run(Xs)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    errs = [bp.result(b)[2]["rel_err"] for b in range(len(ws))]
+    # kernels in the graph: state reset; per mode a sketch sweep, its QR, q = 1 power
+    # iteration (two sweeps and a QR) and the TTM sweep; ALS, back-projection, lambda
+    nbytes = sum(X.numel() * 4 for X in Xs)
+    line = {"metric": METRIC + " [batched workload]", "value": total_ms / 1e3 / args.steps,
+            "unit": "s", "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 QR and Gram solves)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c5"][1], "tensors": len(ws), "bytes": nbytes,
+                       "autotuned_ctas_per_sm": list(choice),
+                       "l2": "inputs (3 GB) larger than L2, 512 MB flush between steps"},
+            "tensors_per_s": len(ws) / (total_ms / 1e3 / args.steps),
+            "input_gbs": nbytes / (total_ms / 1e3 / args.steps) / 1e9,
+            "rel_err_median": float(statistics.median(errs)),
+            "rel_err_max": float(max(errs)), "gpu_launches": 1 + 3 * (3 + 3 * 1) + 3,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(ws)
+    bp.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c5":
+        run_batched(args)
     else:
         run_ours(args)
 
