@@ -81,7 +81,8 @@ typedef enum {
 /* Informational bits returned in rcp_result.info. */
 enum {
   RCP_INFO_SHIFTED_QR = 1,     /* a sketch or power-iteration Gram needed the shifted fallback */
-  RCP_INFO_ALS_REGULARISED = 2 /* an ALS Gram solve needed a diagonal shift                    */
+  RCP_INFO_ALS_REGULARISED = 2, /* an ALS Gram solve needed a diagonal shift                   */
+  RCP_INFO_LEARNED_INIT = 4     /* ALS started from the warm-start network's factors          */
 };
 
 /* Flags for rcp_config.flags. */
@@ -323,6 +324,122 @@ rcp_status rcp_sketch_mode1_static(const void* X_dev, int32_t in_dtype, int32_t 
                                    const int64_t* dims, int32_t rank, int32_t oversample,
                                    uint64_t seed, double* Q_dev, int32_t* status_dev,
                                    void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start for CP-ALS (Algorithm 2 steps 1-2 choose the initial
+ * factors; Section 3.2 names eigenvector or random initialisation).  This is
+ * an addition to the paper: a 3-layer perceptron maps the compressed tensor
+ * B (3-way, l_n <= 24, R <= 16) to initial factors.
+ *
+ * Input encoding: B in its canonical basis -- for each mode the eigenvectors
+ * U_n of B_(n) B_(n)^T (descending eigenvalues, each vector's largest-
+ * magnitude entry positive) -- i.e. G = B x_1 U_1^T x_2 U_2^T x_3 U_3^T / |B|_F,
+ * zero-padded to 24 x 24 x 24, index i1 + 24 i2 + 576 i3 ("x rows", FP32,
+ * RCP_MLP_IN floats per sample).  Output Y: 3 x 24 x 16, index
+ * n * 384 + i * 16 + r ("y rows", RCP_MLP_OUT floats), read as a correction
+ * in the canonical basis: initial A_n = U_n (E + Y_n) on l_n rows and R
+ * columns, E = the first R unit vectors (Y = 0 gives the eigenvector
+ * initialisation).  meta rows: int32 (l1, l2, l3, R) per sample; all zeros
+ * marks a sample the network does not serve.
+ *
+ * Network: x -> relu(W1 x + b1) (512) -> relu(W2 h1 + b2) (512) -> W3 h2 + b3,
+ * BF16 weights and activations as tensor-core operands, FP32 accumulation,
+ * FP32 master parameters in the flat order W1 (512 x 13824, row-major), b1,
+ * W2 (512 x 512), b2, W3 (1152 x 512), b3.  Adam updates the master copy.
+ * ---------------------------------------------------------------------- */
+#define RCP_WS_LPAD 24
+#define RCP_WS_RPAD 16
+#define RCP_MLP_IN 13824
+#define RCP_MLP_HIDDEN 512
+#define RCP_MLP_OUT 1152
+
+typedef struct rcp_mlp_s* rcp_mlp_t;
+
+/* Number of FP32 master parameters (7,930,032). */
+int64_t rcp_mlp_param_count(void);
+
+/* Create a network that processes up to `batch` samples per pass (multiple of
+ * 128, <= 65536), with seeded initial weights W1, W2 ~ U(-1/sqrt(fan_in),
+ * 1/sqrt(fan_in)), W3 and biases zero (the untrained network outputs Y = 0),
+ * Adam moments zero.  stream: cudaStream_t borrowed for all
+ * of the network's work.  RCP_EINVAL / RCP_ENOMEM / RCP_ECUDA. */
+rcp_status rcp_mlp_create(int32_t batch, uint64_t seed, void* stream, rcp_mlp_t* out);
+rcp_status rcp_mlp_destroy(rcp_mlp_t net);
+
+/* Copy the master parameters, the Adam moments and the step count to host
+ * buffers of rcp_mlp_param_count() floats (any pointer may be NULL), or load
+ * them (checkpoint / resume).  Both synchronise the stream. */
+rcp_status rcp_mlp_get_params(rcp_mlp_t net, float* params, float* adam_m, float* adam_v,
+                              int64_t* step);
+rcp_status rcp_mlp_set_params(rcp_mlp_t net, const float* params, const float* adam_m,
+                              const float* adam_v, int64_t step);
+
+/* Forward pass of `count` x rows (device, count <= batch); train != 0 keeps
+ * what the backward pass needs.  y_dev: optional device output, count y rows.
+ * Asynchronous. */
+rcp_status rcp_mlp_forward(rcp_mlp_t net, const float* x_dev, int32_t count, int32_t train,
+                           float* y_dev);
+
+/* Backward pass of the last training forward: dy_dev holds batch y rows of
+ * dLoss/dY (rows >= count zero).  Writes the gradients of every parameter
+ * (flat order above) to grad_dev when not NULL.  RCP_EORDER without a
+ * training forward.  Asynchronous. */
+rcp_status rcp_mlp_backward(rcp_mlp_t net, const float* dy_dev, float* grad_dev);
+
+/* One Adam step (Kingma & Ba) with the gradients of the last backward pass. */
+rcp_status rcp_mlp_adam(rcp_mlp_t net, float lr, float beta1, float beta2, float eps);
+
+/* Device status word of the network (RCP_ETIMEOUT if a tensor-core pipeline
+ * wait gave up).  Synchronises. */
+rcp_status rcp_mlp_status(rcp_mlp_t net);
+
+/* x rows and canonical bases of `count` padded compressed tensors:
+ * Bpad_dev count x 24^3 FP32 (index i1 + 24 i2 + 576 i3), meta_dev count x 4;
+ * x_dev count x 24^3; U_dev count x 3 x 24 x 24 (U_n[i][j] at
+ * ((b * 3 + n) * 24 + i) * 24 + j, column j = eigenvector j).  Asynchronous. */
+rcp_status rcp_ws_canonicalize(const float* Bpad_dev, const int32_t* meta_dev, int32_t count,
+                               float* x_dev, float* U_dev, void* stream);
+
+/* Training loss of `count` y rows against targets t_dev (y-row layout: the
+ * converged factors in the canonical basis, unit columns): after the
+ * minimum-cost one-to-one matching of the R components (Hungarian method),
+ * loss_b = (1/R) sum_r sum_n (1 - cos^2(E + Y_n column r, target column
+ * match(r))).  Writes loss_dev[b] and dy_dev = scale * dloss_b/dY.  Async. */
+rcp_status rcp_ws_loss(const float* y_dev, const float* t_dev, const int32_t* meta_dev,
+                       int32_t count, float scale, float* dy_dev, float* loss_dev, void* stream);
+
+/* forward (train), loss with scale 1/count, backward, Adam(lr, 0.9, 0.999,
+ * 1e-8).  loss_dev: optional device output of the per-sample losses. */
+rcp_status rcp_mlp_train_step(rcp_mlp_t net, const float* x_dev, const float* t_dev,
+                              const int32_t* meta_dev, int32_t count, float lr, float* loss_dev);
+
+/* Training data from a batch plan after a run: per tensor b the padded
+ * compressed tensor (Bpad_dev, count x 24^3), meta (count x 4), x row
+ * (count x 24^3), canonical bases (count x 3 x 24 x 24) and the converged
+ * factors in the canonical basis with unit columns (t_dev, count x 1152).
+ * Tensors the network does not serve (ndim != 3, l_n > 24, R > 16) get zero
+ * meta.  Asynchronous on the plan's stream. */
+rcp_status rcp_batched_export(rcp_batched_t plan, float* Bpad_dev, int32_t* meta_dev,
+                              float* x_dev, float* U_dev, float* t_dev);
+
+/* Start the ALS of every eligible tensor from the network's factors in later
+ * runs (the captured graph gains the canonicalisation, the forward pass and
+ * the factor construction); net = NULL restores the random initialisation.
+ * Tensors the network does not serve, or whose predicted factors have a
+ * non-finite or zero column, keep the random initialisation; the others set
+ * RCP_INFO_LEARNED_INIT.  The network's batch must be >= the plan's count and
+ * its stream is not used by the plan.  Synchronises. */
+rcp_status rcp_batched_set_warm_start(rcp_batched_t plan, rcp_mlp_t net);
+
+/* Synthetic CP tensor for training and benchmarking (no counterpart in the
+ * method): X[i_1..i_N] = sum_r lambda_r prod_n A_n[i_n, r] + sigma z, z ~ N(0, 1)
+ * from the counter-based stream (key = seed, counter = linear index,
+ * purpose 3), written in the Kolda layout (FP32).  factors: host array of N
+ * device pointers (A_n: I_n x R column-major FP32); lambda_dev: R FP32.
+ * Asynchronous. */
+rcp_status rcp_synth_cp(int32_t ndim, const int64_t* dims, int32_t rank,
+                        const float* const* factors, const float* lambda_dev, float sigma,
+                        uint64_t seed, float* X_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,9 @@ RCP_OK, RCP_EINVAL, RCP_ENOMEM, RCP_ECUDA, RCP_ESINGULAR, RCP_ENAN, RCP_ETIMEOUT
 RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
 RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
 RCP_FLAG_HOST_STAGING = 1
-RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED = 1, 2
+RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED, RCP_INFO_LEARNED_INIT = 1, 2, 4
+WS_LPAD, WS_RPAD = 24, 16
+MLP_IN, MLP_HIDDEN, MLP_OUT = 13824, 512, 1152
 RCP_KT_SKETCH, RCP_KT_APPLY, RCP_KT_PROJECT, RCP_KT_TTM, RCP_KT_ALS, RCP_KT_ALL = range(6)
 
 
@@ -75,6 +77,23 @@ SIGNATURES = {
     "rcp_batched_result": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P), P,
                                           ctypes.POINTER(RcpResult)]),
     "rcp_batched_destroy": (ctypes.c_int, [P]),
+    "rcp_mlp_param_count": (ctypes.c_int64, []),
+    "rcp_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, P, ctypes.POINTER(P)]),
+    "rcp_mlp_destroy": (ctypes.c_int, [P]),
+    "rcp_mlp_get_params": (ctypes.c_int, [P, P, P, P, ctypes.POINTER(ctypes.c_int64)]),
+    "rcp_mlp_set_params": (ctypes.c_int, [P, P, P, P, ctypes.c_int64]),
+    "rcp_mlp_forward": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int32, P]),
+    "rcp_mlp_backward": (ctypes.c_int, [P, P, P]),
+    "rcp_mlp_adam": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float]),
+    "rcp_mlp_status": (ctypes.c_int, [P]),
+    "rcp_ws_canonicalize": (ctypes.c_int, [P, P, ctypes.c_int32, P, P, P]),
+    "rcp_ws_loss": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, P, P, P]),
+    "rcp_mlp_train_step": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_float, P]),
+    "rcp_batched_export": (ctypes.c_int, [P, P, P, P, P, P]),
+    "rcp_batched_set_warm_start": (ctypes.c_int, [P, P]),
+    "rcp_synth_cp": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                    ctypes.POINTER(P), P, ctypes.c_float, ctypes.c_uint64, P, P]),
     "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_uint64, P, P, P]),

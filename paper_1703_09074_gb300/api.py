@@ -271,6 +271,26 @@ class BatchedPlan:
         check(code, "rcp_batched_result")
         return [a.t() for a in A], lam, _result_dict(res, len(self.dims[b]))
 
+    def set_warm_start(self, net):
+        """Start ALS from the network's factors in later runs (None: random init)."""
+        self._net = net
+        check(self.lib.rcp_batched_set_warm_start(self.h, None if net is None else net.h),
+              "rcp_batched_set_warm_start")
+
+    def export(self):
+        """Training data of the last run: dict of device tensors B, meta, x, U, t."""
+        C = self.count
+        dev = self.device
+        out = dict(B=torch.empty((C, _lib.MLP_IN), dtype=torch.float32, device=dev),
+                   meta=torch.empty((C, 4), dtype=torch.int32, device=dev),
+                   x=torch.empty((C, _lib.MLP_IN), dtype=torch.float32, device=dev),
+                   U=torch.empty((C, 3, _lib.WS_LPAD, _lib.WS_LPAD), dtype=torch.float32, device=dev),
+                   t=torch.empty((C, _lib.MLP_OUT), dtype=torch.float32, device=dev))
+        check(self.lib.rcp_batched_export(self.h, out["B"].data_ptr(), out["meta"].data_ptr(),
+                                          out["x"].data_ptr(), out["U"].data_ptr(),
+                                          out["t"].data_ptr()), "rcp_batched_export")
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.rcp_batched_destroy(self.h)
@@ -287,3 +307,120 @@ class BatchedPlan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class WarmStartNet:
+    """The warm-start network (include/rcp.h, learned warm start) on one CUDA stream."""
+
+    def __init__(self, batch=256, seed=0, stream=None):
+        self.lib = _lib.load()
+        self.batch = int(batch)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        self.nparams = int(self.lib.rcp_mlp_param_count())
+        h = ctypes.c_void_p()
+        check(self.lib.rcp_mlp_create(self.batch, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+              "rcp_mlp_create")
+        self.h = h
+
+    def params(self):
+        """(params, adam_m, adam_v, step) as host FP32 tensors (synchronises)."""
+        w, m, v = (torch.empty(self.nparams, dtype=torch.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        check(self.lib.rcp_mlp_get_params(self.h, w.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                          ctypes.byref(step)), "rcp_mlp_get_params")
+        return w, m, v, step.value
+
+    def set_params(self, w, m=None, v=None, step=0):
+        w = w.detach().to("cpu", torch.float32).contiguous()
+        m = None if m is None else m.detach().to("cpu", torch.float32).contiguous()
+        v = None if v is None else v.detach().to("cpu", torch.float32).contiguous()
+        check(self.lib.rcp_mlp_set_params(self.h, w.data_ptr(), None if m is None else m.data_ptr(),
+                                          None if v is None else v.data_ptr(), int(step)),
+              "rcp_mlp_set_params")
+
+    def save(self, path):
+        w, m, v, step = self.params()
+        torch.save(dict(params=w, adam_m=m, adam_v=v, step=step), path)
+
+    def load(self, path):
+        d = torch.load(path, map_location="cpu")
+        self.set_params(d["params"], d["adam_m"], d["adam_v"], d["step"])
+
+    def forward(self, x, train=False):
+        count = x.shape[0]
+        y = torch.empty((count, _lib.MLP_OUT), dtype=torch.float32, device=self.device)
+        check(self.lib.rcp_mlp_forward(self.h, x.data_ptr(), count, 1 if train else 0, y.data_ptr()),
+              "rcp_mlp_forward")
+        return y
+
+    def backward(self, dy):
+        g = torch.empty(self.nparams, dtype=torch.float32, device=self.device)
+        check(self.lib.rcp_mlp_backward(self.h, dy.data_ptr(), g.data_ptr()), "rcp_mlp_backward")
+        return g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(self.lib.rcp_mlp_adam(self.h, lr, beta1, beta2, eps), "rcp_mlp_adam")
+
+    def train_step(self, x, t, meta, lr):
+        count = x.shape[0]
+        loss = torch.empty(count, dtype=torch.float32, device=self.device)
+        check(self.lib.rcp_mlp_train_step(self.h, x.data_ptr(), t.data_ptr(), meta.data_ptr(), count,
+                                          lr, loss.data_ptr()), "rcp_mlp_train_step")
+        return loss
+
+    def status(self):
+        return self.lib.rcp_mlp_status(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rcp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ws_canonicalize(Bpad, meta, stream=None):
+    """(x rows, canonical bases U) of padded compressed tensors (device tensors)."""
+    lib = _lib.load()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    C = Bpad.shape[0]
+    x = torch.empty((C, _lib.MLP_IN), dtype=torch.float32, device=Bpad.device)
+    U = torch.empty((C, 3, _lib.WS_LPAD, _lib.WS_LPAD), dtype=torch.float32, device=Bpad.device)
+    check(lib.rcp_ws_canonicalize(Bpad.data_ptr(), meta.data_ptr(), C, x.data_ptr(), U.data_ptr(),
+                                  ctypes.c_void_p(stream.cuda_stream)), "rcp_ws_canonicalize")
+    return x, U
+
+
+def ws_loss(y, t, meta, scale=1.0, stream=None):
+    """(per-sample loss, dLoss/dY * scale) of the matched-cosine warm-start loss."""
+    lib = _lib.load()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    C = y.shape[0]
+    loss = torch.empty(C, dtype=torch.float32, device=y.device)
+    dy = torch.empty_like(y)
+    check(lib.rcp_ws_loss(y.data_ptr(), t.data_ptr(), meta.data_ptr(), C, scale, dy.data_ptr(),
+                          loss.data_ptr(), ctypes.c_void_p(stream.cuda_stream)), "rcp_ws_loss")
+    return loss, dy
+
+
+def synth_cp(factors, lam, sigma, seed, out=None, stream=None):
+    """Device synthetic CP tensor (Kolda layout) from FP32 device factors (I_n x R each)."""
+    lib = _lib.load()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    dims = [int(F.shape[0]) for F in factors]
+    R = int(factors[0].shape[1])
+    Fs = [F.t().contiguous() for F in factors]   # column-major I_n x R
+    if out is None:
+        out = torch.empty(tuple(reversed(dims)), dtype=torch.float32, device=factors[0].device)
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    check(lib.rcp_synth_cp(len(dims), d, R, _ptr_array(Fs), lam.data_ptr(), float(sigma),
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
+                           ctypes.c_void_p(stream.cuda_stream)), "rcp_synth_cp")
+    out._keep = Fs
+    return out

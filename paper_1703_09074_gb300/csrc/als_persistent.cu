@@ -79,7 +79,8 @@ __device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
   return grid_sync(a.bar, (unsigned)G, a.abort_flag);
 }
 
-template <typename TM>
+// KACC: MTTKRP outputs (l_n x R) per thread, at most KACC * kThreads.
+template <typename TM, int KACC>
 __device__ void als_body(const PersArgs& a, int g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -144,9 +145,9 @@ __device__ void als_body(const PersArgs& a, int g) {
       const int J = L * Rt;
       const int nout = ln * R;
       // ---- phase A: MTTKRP partial over this CTA's column tiles
-      double acc[16];
+      double acc[KACC];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+      for (int k = 0; k < KACC; ++k) acc[k] = 0.0;
       double nbpart = 0.0;
       // column tiles of tj <= kTileJ columns, narrow enough to keep the GA CTAs busy
       const int tj = max(1, min(kTileJ, (J + GA - 1) / GA));
@@ -190,7 +191,7 @@ __device__ void als_body(const PersArgs& a, int g) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < KACC; ++k) {
           const int o = tid + k * kThreads;
           if (o < nout) {
             const int i = o % ln, r = o / ln;
@@ -202,7 +203,7 @@ __device__ void als_body(const PersArgs& a, int g) {
         __syncthreads();
       }
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
+      for (int k = 0; k < KACC; ++k) {
         const int o = tid + k * kThreads;
         if (o < nout && g < GA) a.part[(int64_t)g * nout + o] = acc[k];
       }
@@ -237,7 +238,9 @@ __device__ void als_body(const PersArgs& a, int g) {
           // path 2: FP32 inverse Z ~ V^{-1} in registers (R <= 32); path 1: FP32
           // Cholesky factor (R > 32); path 0: FP64 Cholesky of V itself
           int path = 0;
-          if (R <= 32) {
+          if (a.direct64) {
+            // path 0 below
+          } else if (R <= 32) {
             if (warp_inverse32(V, R, U32, floor32)) path = 2;
           } else {
             bool f32ok = warp_chol(U32, R, floor32);
@@ -563,14 +566,16 @@ __device__ void als_body(const PersArgs& a, int g) {
 
 template <typename TM>
 __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
-  als_body<TM>(a, blockIdx.x);
+  als_body<TM, 16>(a, blockIdx.x);
 }
 
 // Batched form: CTA b runs the whole ALS of problem b alone (G = 1).
+// Batched problems have l_n <= 32 and R <= 32: at most 4 outputs per thread,
+// which leaves registers for two CTAs per SM.
 template <typename TM>
-__global__ void __launch_bounds__(kThreads, 1) k_als_batched(const PersArgs* __restrict__ args) {
+__global__ void __launch_bounds__(kThreads, 2) k_als_batched(const PersArgs* __restrict__ args) {
   const PersArgs a = args[blockIdx.x];
-  als_body<TM>(a, 0);
+  als_body<TM, 4>(a, 0);
 }
 
 template <typename TM>
@@ -619,6 +624,9 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.tol = p->cfg.tol;
   a.max_iters = p->cfg.max_iters;
   a.user_init = p->user_init ? 1 : 0;
+  // rows are spread over the CTAs: the FP32 inverse plus FP64 refinement of one
+  // row per CTA is faster here than every CTA factoring V in FP64 (measured)
+  a.direct64 = 0;
   void* args[] = {&a};
   count_launches(1);
   return cudaLaunchCooperativeKernel((const void*)k_als_persistent<TM>, dim3(a.G), dim3(kThreads),

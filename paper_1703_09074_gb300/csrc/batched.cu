@@ -22,7 +22,9 @@
 #include <numeric>
 #include <vector>
 
-#include "rcp_internal.cuh"
+#include <stddef.h>
+
+#include "mlp_internal.cuh"
 #include "small_la.cuh"
 
 using namespace rcp;
@@ -311,6 +313,14 @@ struct rcp_batched_s {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t gstream = nullptr;    // own stream: the graph is captured and replayed here
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // learned warm start
+  rcp_mlp_s* net = nullptr;
+  WsItem* ws_items = nullptr;        // [count]
+  float* ws_B = nullptr;             // count x 24^3 padded compressed tensors
+  float* ws_x = nullptr;             // count x 24^3 network inputs
+  float* ws_U = nullptr;             // count x 3 x 24 x 24 canonical bases
+  int* ws_meta = nullptr;            // count x 4
+  std::vector<PersArgs> als_host;    // host copy of the ALS argument table
 };
 
 namespace {
@@ -343,6 +353,11 @@ void free_batched(rcp_batched_t p) {
   cudaFree(p->xptrs_dev);
   cudaFree(p->dummy_bar);
   cudaFree(p->dummy_abort);
+  cudaFree(p->ws_items);
+  cudaFree(p->ws_B);
+  cudaFree(p->ws_x);
+  cudaFree(p->ws_U);
+  cudaFree(p->ws_meta);
   if (p->xptrs_host) cudaFreeHost(p->xptrs_host);
   delete p;
 }
@@ -381,6 +396,13 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
     }
     RCPB_TRY(launch_b_col_sweep(cT, ci, p->colItemCnt[n], p->counters + ctr++, p->lmax,
                                 p->xptrs_dev, cgrid, s));
+  }
+  if (p->net) {
+    // learned warm start: canonical inputs, one forward pass, initial factors
+    RCPB_TRY(launch_ws_gather(p->ws_items, C, p->ws_B, p->ws_meta, s));
+    RCPB_TRY(launch_ws_canon(p->ws_B, p->ws_meta, C, p->ws_x, p->ws_U, s));
+    if (mlp_forward_enqueue(p->net, p->ws_x, C, false, s) != RCP_OK) return RCP_ECUDA;
+    RCPB_TRY(launch_ws_init(p->net->Y, p->ws_U, p->ws_meta, p->ws_items, C, s));
   }
   RCPB_TRY(launch_als_batched(p->alsP, C, p->als_smem, s));
   count_launches(2);
@@ -491,6 +513,9 @@ rcp_status build_tables(rcp_batched_t p) {
     a.tol = p->cfg[b].tol;
     a.max_iters = p->cfg[b].max_iters;
     a.user_init = 0;
+    // one CTA per problem: the FP64 Cholesky solve of each row costs less than
+    // FP32 solves plus FP64 refinement steps on GB300's narrow FP64 pipe
+    a.direct64 = 1;
     als[b] = a;
     BProj pr{};
     pr.N = N;
@@ -516,6 +541,39 @@ rcp_status build_tables(rcp_batched_t p) {
   if (!up(&p->rowP, rowP) || !up(&p->colP, colP) || !up(&p->qrP, qrP) || !up(&p->rowItems, rItems) ||
       !up(&p->colItems, cItems) || !up(&p->alsP, als) || !up(&p->projP, proj) || !up(&p->stPtrs, sts))
     return RCP_ENOMEM;
+  p->als_host = als;
+  // warm-start items: 3-way tensors with l_n <= 24 and R <= 16
+  std::vector<WsItem> ws(C);
+  for (int b = 0; b < C; ++b) {
+    auto& t = p->t[b];
+    WsItem w{};
+    bool ok = N == 3 && t.R <= kWsR;
+    for (int n = 0; n < N && n < 3; ++n) {
+      ok = ok && t.l[n] <= kWsL;
+      w.l[n] = t.l[n];
+      w.At[n] = t.At[n];
+    }
+    w.core = ok ? t.buf[(N - 1) % 2] : nullptr;
+    w.R = t.R;
+    w.user_init = (int*)((char*)(p->alsP + b) + offsetof(PersArgs, user_init));
+    w.st = t.st;
+    ws[b] = w;
+  }
+  if (!up(&p->ws_items, ws)) return RCP_ENOMEM;
+  return RCP_OK;
+}
+
+rcp_status ensure_ws(rcp_batched_t p) {
+  if (p->ws_B) return RCP_OK;
+  const size_t C = p->count;
+  if (cudaMalloc((void**)&p->ws_B, C * kMlpIn * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&p->ws_x, C * kMlpIn * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&p->ws_U, C * 3 * kWsL * kWsL * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&p->ws_meta, C * 4 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return RCP_ENOMEM;
+  }
+  if (prepare_ws() != cudaSuccess) return RCP_ECUDA;
   return RCP_OK;
 }
 
@@ -765,6 +823,41 @@ rcp_status rcp_batched_autotune(rcp_batched_t p, const void* const* X_dev, int32
     choice[0] = br;
     choice[1] = bc;
   }
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_set_warm_start(rcp_batched_t p, rcp_mlp_t net) {
+  if (!p) return RCP_EINVAL;
+  if (net && net->batch < p->count) return RCP_EINVAL;
+  RCPB_TRY(cudaStreamSynchronize(p->stream));
+  RCPB_TRY(cudaStreamSynchronize(p->gstream));
+  if (net) {
+    const rcp_status st = ensure_ws(p);
+    if (st != RCP_OK) return st;
+  } else {
+    // every tensor back to the random initialisation
+    RCPB_TRY(cudaMemcpy(p->alsP, p->als_host.data(), sizeof(PersArgs) * p->count,
+                        cudaMemcpyHostToDevice));
+  }
+  p->net = net;
+  if (p->exec) {  // re-capture on the next run
+    cudaGraphExecDestroy(p->exec);
+    cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+  }
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_export(rcp_batched_t p, float* Bpad_dev, int32_t* meta_dev, float* x_dev,
+                              float* U_dev, float* t_dev) {
+  if (!p || !Bpad_dev || !meta_dev || !x_dev || !U_dev || !t_dev) return RCP_EINVAL;
+  if (prepare_ws() != cudaSuccess) return RCP_ECUDA;
+  cudaStream_t s = p->stream;
+  const int C = p->count;
+  RCPB_TRY(launch_ws_gather(p->ws_items, C, Bpad_dev, meta_dev, s));
+  RCPB_TRY(launch_ws_canon(Bpad_dev, meta_dev, C, x_dev, U_dev, s));
+  RCPB_TRY(launch_ws_targets(p->ws_items, U_dev, C, t_dev, s));
   return RCP_OK;
 }
 

@@ -205,6 +205,7 @@ struct PersArgs {
   double tol;
   int max_iters;
   int user_init;
+  int direct64;          // solve with the FP64 Cholesky factor only (no FP32 factor + refinement)
 };
 
 // ---------------------------------------------------------------- batched form
