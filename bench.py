@@ -59,6 +59,8 @@ def parse():
                     help="default: mixed for FP32 inputs, f64 for FP64 inputs")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f64-compare", action="store_true",
+                    help="skip the FP64 GPU path comparison (profiling runs)")
     ap.add_argument("--warm-start", choices=["learned", "random"], default="learned",
                     help="ALS initialisation of the batched workload")
     return ap.parse_args()
@@ -317,7 +319,7 @@ def run_ours(args):
 
     # the plain FP64 GPU path on the same tensor, for the equal-fit comparison
     f64_cmp = None
-    if args.precision == "mixed":
+    if args.precision == "mixed" and not args.no_f64_compare:
         p64 = Plan(w.dims, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, seed=0,
                    in_dtype=in_dt, precision="f64", stream=stream)
         p64.decompose(X)

@@ -79,12 +79,41 @@ __device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
   return grid_sync(a.bar, (unsigned)G, a.abort_flag);
 }
 
+// Gauss-Jordan inverse of the symmetric positive definite V (row pitch R + 1)
+// by the whole CTA in FP64, without pivoting; V^{-1} lands in columns R..2R-1
+// of Aug (row pitch 64, R <= 32).  At step k only the R columns k+1..R+k
+// change.  Returns false (uniformly) when a pivot is not above floor_.
+__device__ bool cta_gj_inverse64(const double* V, int R, double* Aug, double* fcol,
+                                 double floor_) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 2 * R * R; e += kThreads) {
+    const int i = e / (2 * R), j = e % (2 * R);
+    Aug[i * 64 + j] = j < R ? V[i * (R + 1) + j] : (j - R == i ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    const double piv = Aug[k * 64 + k];
+    if (!(piv > floor_)) return false;
+    const double pinv = 1.0 / piv;
+    if (tid < R) fcol[tid] = Aug[tid * 64 + k];
+    __syncthreads();
+    for (int j = k + 1 + tid; j <= R + k; j += kThreads) Aug[k * 64 + j] *= pinv;
+    __syncthreads();
+    for (int e = tid; e < R * R; e += kThreads) {
+      const int i = e / R, j = k + 1 + e % R;
+      if (i != k) Aug[i * 64 + j] = fma(-fcol[i], Aug[k * 64 + j], Aug[i * 64 + j]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // KACC: MTTKRP outputs (l_n x R) per thread, at most KACC * kThreads.
 template <typename TM, int KACC>
 __device__ void als_body(const PersArgs& a, int g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int N = a.N, R = a.R, G = a.G, GA = a.GA;
+  const int N = a.N, R = a.R, G = a.G;
   int lmax = 1, ftot = 0;
   int foff[kMaxN];
   for (int m = 0; m < N; ++m) {
@@ -106,6 +135,7 @@ __device__ void als_body(const PersArgs& a, int g) {
   TM* Fac = (TM*)(((uintptr_t)(invd32 + R) + 15) & ~(uintptr_t)15);  // factor copies
   TM* Bs = Fac + ftot;                          // lmax x kBP
   TM* Ks = Bs + lmax * kBP;                     // kTileJ x R
+  double* Aug = (double*)(((uintptr_t)(Ks + kTileJ * R) + 15) & ~(uintptr_t)15);  // 32 x 64
   DevState* st = a.st;
 
   // ---- initial factors (modes 2..N) and their Grams, identical in every CTA
@@ -133,9 +163,76 @@ __device__ void als_body(const PersArgs& a, int g) {
     __syncthreads();
   }
 
+  // V = Hadamard product of the Grams of every mode but n0 (FP64, and an FP32
+  // copy), and the solve it needs: path 3 (R <= 32) the FP64 inverse by the whole
+  // CTA, path 1 an FP32 Cholesky factor plus FP64 refinement (R > 32), path 0 the
+  // FP64 Cholesky of V itself (with a diagonal shift as last resort).  The path
+  // goes to red[0].
+  auto prepare_solve = [&](int n0) {
+        // V = Hadamard product of the other Grams (FP64) and its FP32 copy
+        for (int e = tid; e < R * R; e += kThreads) {
+          const int r = e % R, c = e / R;
+          double v = 1.0;
+          for (int m = 0; m < N; ++m)
+            if (m != n0) v *= Gr[m * R * R + e];
+          V[r * (R + 1) + c] = v;
+          U32[r * (R + 1) + c] = (float)v;
+        }
+        __syncthreads();
+        // path 3 (R <= 32): FP64 inverse by the whole CTA, one FP64 product per row
+        bool gj = false;
+        if (!a.direct64 && R <= 32) {
+          double trd = 0.0;
+          for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
+          gj = cta_gj_inverse64(V, R, Aug, invd64, (double)R * 2.220446049250313e-16 * trd);
+        }
+        if (warp == 0) {
+          float tr = 0.0f;
+          for (int c = 0; c < R; ++c) tr += U32[c * (R + 1) + c];
+          const float floor32 = 64.0f * 5.9604645e-08f * tr;
+          int path = 0;
+          if (gj) {
+            path = 3;
+          } else if (a.direct64 || R <= 32) {
+            // path 0 below (a failed path-3 pivot means V is nearly singular)
+          } else {
+            bool f32ok = warp_chol(U32, R, floor32);
+            if (f32ok)
+              for (int k = lane; k < R; k += 32) invd32[k] = 1.0f / U32[k * (R + 1) + k];
+            if (__all_sync(0xffffffffu, f32ok)) path = 1;
+          }
+          path = __shfl_sync(0xffffffffu, path, 0);
+          if (path == 0) {
+            // FP64 Cholesky of V itself; a diagonal shift R u trace(V) as last resort
+            double trd = 0.0;
+            for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
+            const double shift = (double)R * 1.1102230246251565e-16 * trd;
+            bool ok64 = warp_chol(V, R, shift);
+            if (!ok64) {
+              for (int e = lane; e < R * R; e += 32) {
+                const int r = e % R, c = e / R;
+                double v = 1.0;
+                for (int m = 0; m < N; ++m)
+                  if (m != n0) v *= Gr[m * R * R + e];
+                V[r * (R + 1) + c] = v + (r == c ? shift : 0.0);
+              }
+              __syncwarp();
+              ok64 = warp_chol(V, R, 0.0);
+              if (lane == 0) atomicOr(&st->info, RCP_INFO_ALS_REGULARISED);
+            }
+            if (!ok64 && lane == 0) set_status(st, RCP_ESINGULAR);
+            for (int k = lane; k < R; k += 32) invd64[k] = 1.0 / V[k * (R + 1) + k];
+          }
+          if (lane == 0) red[0] = (double)path;
+        }
+        __syncthreads();
+  };
+
   double rho_prev = 0.0, nb2 = 0.0;
   int done = 0;
   bool ok = true;
+  // partial writers of mode 1 (the |B|^2 partials are written in its first phase A)
+  const int GW0 = G - ((G > 1 && G >= 2 * a.dims[0]) ? a.dims[0] : 0);
   for (int it = 1; it <= a.max_iters && ok && !done; ++it) {
     for (int n0 = 0; n0 < N && ok; ++n0) {
       const int ln = a.dims[n0];
@@ -144,14 +241,18 @@ __device__ void als_body(const PersArgs& a, int g) {
       for (int m = n0 + 1; m < N; ++m) Rt *= a.dims[m];
       const int J = L * Rt;
       const int nout = ln * R;
+      // With at least two CTAs per row, the row owners (g < ln) skip the MTTKRP
+      // and prepare the Gram solve during phase A; the others write partials.
+      const int gw0 = (G > 1 && G >= 2 * ln) ? ln : 0;
+      const int GW = G - gw0, gi = g - gw0;
       // ---- phase A: MTTKRP partial over this CTA's column tiles
       double acc[KACC];
 #pragma unroll
       for (int k = 0; k < KACC; ++k) acc[k] = 0.0;
       double nbpart = 0.0;
-      // column tiles of tj <= kTileJ columns, narrow enough to keep the GA CTAs busy
-      const int tj = max(1, min(kTileJ, (J + GA - 1) / GA));
-      for (int t0 = g * tj; g < GA && t0 < J; t0 += GA * tj) {
+      // column tiles of tj <= kTileJ columns, narrow enough to keep the GW writers busy
+      const int tj = max(1, min(kTileJ, (J + GW - 1) / GW));
+      for (int t0 = gi * tj; gi >= 0 && t0 < J; t0 += GW * tj) {
         const int nj = min(tj, J - t0);
         // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], coalesced along the contiguous index
         for (int e = tid; e < ln * kTileJ; e += kThreads) {
@@ -205,76 +306,36 @@ __device__ void als_body(const PersArgs& a, int g) {
 #pragma unroll
       for (int k = 0; k < KACC; ++k) {
         const int o = tid + k * kThreads;
-        if (o < nout && g < GA) a.part[(int64_t)g * nout + o] = acc[k];
+        if (o < nout && gi >= 0) a.part[(int64_t)gi * nout + o] = acc[k];
       }
-      if (it == 1 && n0 == 0 && g < GA) {
+      if (it == 1 && n0 == 0 && gi >= 0) {
         for (int o = 16; o > 0; o >>= 1) nbpart += __shfl_down_sync(0xffffffffu, nbpart, o);
         if (lane == 0) red[8 + warp] = nbpart;
         __syncthreads();
         if (tid == 0) {
           double s = 0.0;
           for (int w = 0; w < kWarps; ++w) s += red[8 + w];
-          a.nbp[g] = s;
+          a.nbp[gi] = s;
         }
       }
+      if (gw0 > 0 && g < ln) prepare_solve(n0);
       if (!phase_sync(a, G)) { ok = false; break; }
 
       // ---- phase B: rows owned by this CTA (rows i = g, g + G, ...)
       if (g < ln) {
-        // V = Hadamard product of the other Grams (FP64) and its FP32 copy
-        for (int e = tid; e < R * R; e += kThreads) {
-          const int r = e % R, c = e / R;
-          double v = 1.0;
-          for (int m = 0; m < N; ++m)
-            if (m != n0) v *= Gr[m * R * R + e];
-          V[r * (R + 1) + c] = v;
-          U32[r * (R + 1) + c] = (float)v;
-        }
-        __syncthreads();
-        if (warp == 0) {
-          float tr = 0.0f;
-          for (int c = 0; c < R; ++c) tr += U32[c * (R + 1) + c];
-          const float floor32 = 64.0f * 5.9604645e-08f * tr;
-          // path 2: FP32 inverse Z ~ V^{-1} in registers (R <= 32); path 1: FP32
-          // Cholesky factor (R > 32); path 0: FP64 Cholesky of V itself
-          int path = 0;
-          if (a.direct64) {
-            // path 0 below
-          } else if (R <= 32) {
-            if (warp_inverse32(V, R, U32, floor32)) path = 2;
-          } else {
-            bool f32ok = warp_chol(U32, R, floor32);
-            if (f32ok)
-              for (int k = lane; k < R; k += 32) invd32[k] = 1.0f / U32[k * (R + 1) + k];
-            if (__all_sync(0xffffffffu, f32ok)) path = 1;
-          }
-          path = __shfl_sync(0xffffffffu, path, 0);
-          if (path == 0) {
-            // FP64 Cholesky of V itself; a diagonal shift R u trace(V) as last resort
-            double trd = 0.0;
-            for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
-            const double shift = (double)R * 1.1102230246251565e-16 * trd;
-            bool ok64 = warp_chol(V, R, shift);
-            if (!ok64) {
-              for (int e = lane; e < R * R; e += 32) {
-                const int r = e % R, c = e / R;
-                double v = 1.0;
-                for (int m = 0; m < N; ++m)
-                  if (m != n0) v *= Gr[m * R * R + e];
-                V[r * (R + 1) + c] = v + (r == c ? shift : 0.0);
-              }
-              __syncwarp();
-              ok64 = warp_chol(V, R, 0.0);
-              if (lane == 0) atomicOr(&st->info, RCP_INFO_ALS_REGULARISED);
-            }
-            if (!ok64 && lane == 0) set_status(st, RCP_ESINGULAR);
-            for (int k = lane; k < R; k += 32) invd64[k] = 1.0 / V[k * (R + 1) + k];
-          }
-          if (lane == 0) red[0] = (double)path;
-        }
-        __syncthreads();
+        if (gw0 == 0) prepare_solve(n0);
         const int path = (int)red[0];
-        const bool use32 = path != 0;
+        const bool use32 = path == 1 || path == 2;
+        // path 3: x_c = sum_k m_k (V^{-1})_{kc}, lane c (R <= 32)
+        auto gjmatvec = [&](double (&v)[2]) {
+          double d = 0.0;
+          for (int k = 0; k < R; ++k) {
+            const double vk = __shfl_sync(0xffffffffu, v[0], k);
+            if (lane < R) d = fma(vk, Aug[k * 64 + R + lane], d);
+          }
+          v[0] = lane < R ? d : 0.0;
+          v[1] = 0.0;
+        };
         if (G == 1) {
           // one CTA per problem: warp w solves rows w, w + 8, ... on its own
           double* wsc = wsum + warp * 64;  // this warp's broadcast scratch
@@ -294,11 +355,12 @@ __device__ void als_body(const PersArgs& a, int g) {
               const int r = lane + 32 * h;
               double sm_ = 0.0;
               if (r < R)
-                for (int gg = 0; gg < GA; ++gg) sm_ += a.part[(int64_t)gg * nout + i + ln * r];
+                for (int gg = 0; gg < GW; ++gg) sm_ += a.part[(int64_t)gg * nout + i + ln * r];
               m[h] = sm_;
               x[h] = sm_;
             }
-            if (path == 2) wmatvec(x);
+            if (path == 3) gjmatvec(x);
+            else if (path == 2) wmatvec(x);
             else if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
             for (int step = 0; use32 && step < 6; ++step) {
@@ -351,13 +413,13 @@ __device__ void als_body(const PersArgs& a, int g) {
             if (r < R) {
               const double* src = a.part + i + (int64_t)ln * r;
               int gg = warp;
-              for (; gg + 3 * kWarps < GA; gg += 4 * kWarps) {
+              for (; gg + 3 * kWarps < GW; gg += 4 * kWarps) {
                 s0 += src[(int64_t)gg * nout];
                 s1 += src[(int64_t)(gg + kWarps) * nout];
                 s2 += src[(int64_t)(gg + 2 * kWarps) * nout];
                 s3 += src[(int64_t)(gg + 3 * kWarps) * nout];
               }
-              for (; gg < GA; gg += kWarps) s0 += src[(int64_t)gg * nout];
+              for (; gg < GW; gg += kWarps) s0 += src[(int64_t)gg * nout];
             }
             wsum[warp * 64 + r] = (s0 + s1) + (s2 + s3);
           }
@@ -383,7 +445,8 @@ __device__ void als_body(const PersArgs& a, int g) {
               m[h] = s;
               x[h] = s;
             }
-            if (path == 2) matvec_z(x);
+            if (path == 3) gjmatvec(x);
+            else if (path == 2) matvec_z(x);
             else if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
           }
@@ -520,7 +583,7 @@ __device__ void als_body(const PersArgs& a, int g) {
         double sb = 0.0, si = 0.0;
         if (warp == 0) {
           if (it == 1)
-            for (int gg = lane; gg < GA; gg += 32) sb += a.nbp[gg];
+            for (int gg = lane; gg < GW0; gg += 32) sb += a.nbp[gg];
           for (int i = lane; i < ln; i += 32) si += a.ipp[i];
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -589,7 +652,8 @@ size_t smem_bytes(const rcp_plan_s* p) {
   const size_t d = N * R * R + R * (R + 1) + R + (size_t)lmax * R + R + 64 + kWarps * 64;
   const size_t f = (R * (R + 1) > 1024 ? R * (R + 1) : 1024) + R;
   return d * sizeof(double) + f * sizeof(float) + 16 +
-         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * R) * sizeof(TM);
+         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * R) * sizeof(TM) + 16 +
+         (size_t)32 * 64 * sizeof(double);
 }
 
 template <typename TM>
@@ -605,8 +669,15 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   PersArgs a{};
   a.N = p->N;
   a.R = p->R;
-  a.G = p->nsm;  // one CTA per SM
-  a.GA = a.G;  // every CTA computes MTTKRP partials (fewer CTAs leave L2 latency exposed)
+  // CTAs: one per SM when the MTTKRP is large; for a small core, about two per
+  // row of the largest factor (each row needs an owner) -- fewer CTAs mean fewer
+  // partials to reduce per row and cheaper grid barriers
+  int lmax = 1;
+  for (int m = 0; m < p->N; ++m) lmax = lmax > p->l[m] ? lmax : p->l[m];
+  const double work = (double)p->core_elems * p->R;
+  a.G = work >= 16.0e6 ? p->nsm : (2 * lmax < p->nsm ? (2 * lmax > 32 ? 2 * lmax : 32) : p->nsm);
+  if (a.G > p->nsm) a.G = p->nsm;
+  a.GA = a.G;  // every CTA computes MTTKRP partials
   for (int m = 0; m < p->N; ++m) {
     a.dims[m] = p->l[m];
     a.At[m] = p->At[m];
@@ -624,8 +695,7 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.tol = p->cfg.tol;
   a.max_iters = p->cfg.max_iters;
   a.user_init = p->user_init ? 1 : 0;
-  // rows are spread over the CTAs: the FP32 inverse plus FP64 refinement of one
-  // row per CTA is faster here than every CTA factoring V in FP64 (measured)
+  // R <= 32: each row-owning CTA inverts V in FP64 with all its threads (path 3)
   a.direct64 = 0;
   void* args[] = {&a};
   count_launches(1);
@@ -656,7 +726,8 @@ size_t als_smem_bytes_f32(int N, int R, const int* l) {
   const size_t d = NN * RR * RR + RR * (RR + 1) + RR + (size_t)lmax * RR + RR + 64 + kWarps * 64;
   const size_t f = (RR * (RR + 1) > 1024 ? RR * (RR + 1) : 1024) + RR;
   return d * sizeof(double) + f * sizeof(float) + 16 +
-         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * RR) * sizeof(float);
+         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * RR) * sizeof(float) + 16 +
+         (size_t)32 * 64 * sizeof(double);
 }
 
 cudaError_t prepare_als_batched(size_t smem) {

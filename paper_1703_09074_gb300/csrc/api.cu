@@ -13,7 +13,7 @@ cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStrea
 cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
                         int round, int als_mode, cudaStream_t s);
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s);
+                          cudaStream_t s, bool final_qr);
 cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
                          cudaStream_t s);
@@ -329,7 +329,7 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
-  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
   // q normalised power iterations (steps 7-11)
   const int ng = project_grid(v, p->nsm);
   const int npairs = l * (l + 1) / 2;
@@ -348,7 +348,8 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
     }
     RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
     RCP_TRY(launch_trmm(p->Y, v.I, l, p->RWinv, p->Y, p->dstate, 0, s));
-    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
+                          it == p->cfg.power_iters - 1));
   }
   return RCP_OK;
 }
@@ -378,7 +379,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
     const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
-    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
     for (int it = 0; it < p->cfg.power_iters; ++it) {
       RCP_TRY(launch_q_to_qt32(p->Y, v.I, l, p->QT32, s));
       {
@@ -391,7 +392,8 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
                                p->dstate, s));
       }
       RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
-      RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+      RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
+                          it == p->cfg.power_iters - 1));
     }
     return RCP_OK;
   }
@@ -407,7 +409,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
-  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
   const int ng = project_grid(v, p->nsm);
   for (int it = 0; it < p->cfg.power_iters; ++it) {
     {
@@ -419,7 +421,8 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
       RCP_TRY(launch_sketch_f32(T, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
     }
     RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
-    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
+                          it == p->cfg.power_iters - 1));
   }
   return RCP_OK;
 }

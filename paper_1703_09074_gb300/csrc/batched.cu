@@ -513,9 +513,8 @@ rcp_status build_tables(rcp_batched_t p) {
     a.tol = p->cfg[b].tol;
     a.max_iters = p->cfg[b].max_iters;
     a.user_init = 0;
-    // one CTA per problem: the FP64 Cholesky solve of each row costs less than
-    // FP32 solves plus FP64 refinement steps on GB300's narrow FP64 pipe
-    a.direct64 = 1;
+    // one CTA per problem: the CTA-wide FP64 inverse (path 3) serves every row
+    a.direct64 = 0;
     als[b] = a;
     BProj pr{};
     pr.N = N;

@@ -62,113 +62,135 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
   if (threadIdx.x == 0) Gp[p] = s;
 }
 
-// Cholesky G = R^T R of a packed SPD matrix (one CTA, in place: the upper
-// triangle of A becomes R), then R^{-1} column by column.
+// Cholesky G = R^T R of a packed SPD matrix by one CTA, then R^{-1}.
+// Right-looking, one barrier per step: at step k every thread reads the same
+// pivot d = S[k][k] of the Schur complement S (upper triangle), so the pivot
+// test is uniform; the trailing update uses S[k][i] S[k][j] / d (the unscaled
+// row), while row k of R goes to the strictly lower triangle (R[k][j] at
+// S[j][k]) and the reciprocal of its diagonal to rdiag, which no update touches.  R^{-1} then
+// overwrites the upper triangle by back substitution, one column per thread.
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
-__global__ void k_chol(const double* __restrict__ Gp, int l, double* __restrict__ Rinv,
-                       DevState* st, double shift_rows, int round, int als_mode) {
-  __shared__ double A[kMaxL][kMaxL + 1];
-  __shared__ int fail;
-  __shared__ double shift;
+__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int l,
+                                              double* __restrict__ Rinv, DevState* st,
+                                              double shift_rows, int round, int als_mode) {
+  __shared__ double S[kMaxL][kMaxL + 1];   // Schur complement / R^{-1} (upper), R (lower)
+  __shared__ double rdiag[kMaxL];
+  __shared__ double red[32];
+  __shared__ int bad_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (round == 2 && !st->extra_round) return;
   if (round == 0 && tid == 0) st->extra_round = 0;
+  const int np = l * (l + 1) / 2;
 
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    __syncthreads();
-    for (int p = tid; p < l * (l + 1) / 2; p += nt) {
+  // trace and finiteness, all threads
+  if (tid == 0) bad_sh = 0;
+  __syncthreads();
+  double tr = 0.0;
+  for (int p = tid; p < np; p += nt) {
+    int c1 = 0, rem = p;
+    while (rem >= l - c1) { rem -= l - c1; ++c1; }
+    const double g = Gp[p];
+    if (!isfinite(g)) bad_sh = 1;
+    if (rem == 0) tr += g;
+  }
+  tr = block_sum(tr, red);
+  if (tid == 0) red[31] = tr;
+  __syncthreads();
+  tr = red[31];
+  if (bad_sh) {
+    if (tid == 0) set_status(st, RCP_ENAN);
+    return;
+  }
+  const double u = 1.1102230246251565e-16;
+  const double shift = 11.0 * (shift_rows * l + (double)l * (l + 1)) * u * tr;
+
+  bool ok = false;
+  for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+    for (int p = tid; p < np; p += nt) {
       int c1 = 0, rem = p;
       while (rem >= l - c1) { rem -= l - c1; ++c1; }
-      A[c1][c1 + rem] = Gp[p];
+      S[c1][c1 + rem] = Gp[p] + ((attempt == 1 && rem == 0) ? shift : 0.0);
     }
     __syncthreads();
-    if (tid == 0) {
-      double tr = 0.0;
-      int bad = 0;
-      for (int c = 0; c < l; ++c) {
-        tr += A[c][c];
-        for (int d = c; d < l; ++d)
-          if (!isfinite(A[c][d])) bad = 1;
-      }
-      fail = bad ? 2 : 0;
-      const double u = 1.1102230246251565e-16;
-      shift = 11.0 * (shift_rows * l + (double)l * (l + 1)) * u * tr;
-      if (attempt == 1) {
-        for (int c = 0; c < l; ++c) A[c][c] += shift;
-      }
-    }
-    __syncthreads();
-    if (fail == 2) {
-      if (tid == 0) set_status(st, RCP_ENAN);
-      return;
-    }
+    const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
+    ok = true;
     for (int k = 0; k < l; ++k) {
-      if (tid == 0) {
-        const double d = A[k][k];
-        const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
-        if (!(d > floor_) || !(d > 0.0)) fail = 1;
-        A[k][k] = (d > 0.0) ? sqrt(d) : 1.0;
+      const double d = S[k][k];
+      if (!(d > floor_) || !(d > 0.0)) {  // uniform: every thread read the same d
+        ok = false;
+        break;
       }
-      __syncthreads();
-      if (fail) break;
-      const double rkk = A[k][k];
-      for (int j = k + 1 + tid; j < l; j += nt) A[k][j] /= rkk;
-      __syncthreads();
-      const int m = l - k - 1;
-      for (int q = tid; q < m * m; q += nt) {
-        const int i = k + 1 + q / m, j = k + 1 + q % m;
-        if (j >= i) A[i][j] -= A[k][i] * A[k][j];
+      const double rs = rsqrt(d), dinv = rs * rs;
+      const int m = l - k;  // row k of R: columns k..l-1
+      for (int j = k + tid; j < l; j += nt) {
+        if (j == k) rdiag[k] = rs;  // the reciprocal of R[k][k], for the back substitution
+        else S[j][k] = S[k][j] * rs;
+      }
+      const int mm = m - 1;
+      for (int q = tid; q < mm * mm; q += nt) {
+        const int i = k + 1 + q / mm, j = k + 1 + q % mm;
+        if (j >= i) S[i][j] = fma(-S[k][i] * dinv, S[k][j], S[i][j]);
       }
       __syncthreads();
     }
-    if (!fail) break;
-    if (attempt == 0 && shift_rows > 0.0) {
+    __syncthreads();
+    if (!ok && attempt == 0 && shift_rows > 0.0) {
       if (tid == 0) {
         atomicOr(&st->info, als_mode ? RCP_INFO_ALS_REGULARISED : RCP_INFO_SHIFTED_QR);
         if (round == 0) st->extra_round = 1;
       }
       continue;
     }
-    if (tid == 0) set_status(st, RCP_ESINGULAR);
-    return;
-  }
-  // R^{-1}: thread c solves R x = e_c by back substitution into column c
-  for (int c = tid; c < l; c += nt) {
-    for (int i = l - 1; i >= 0; --i) {
-      double v = 0.0;
-      if (i <= c) {
-        v = (i == c) ? 1.0 : 0.0;
-        for (int k = i + 1; k <= c; ++k) v -= A[i][k] * Rinv[k + l * c];
-        v /= A[i][i];
-      }
-      Rinv[i + l * c] = v;
+    if (!ok) {
+      if (tid == 0) set_status(st, RCP_ESINGULAR);
+      return;
     }
+  }
+  // R^{-1} = X: thread c solves R x = e_c from the bottom; X[i][c] overwrites
+  // S[i][c] (i <= c), R[i][k] is read from S[k][i] (k > i)
+  for (int c = tid; c < l; c += nt) {
+    for (int i = c; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) v = fma(-S[k][i], S[k][c], v);
+      S[i][c] = v * rdiag[i];
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < l * l; q += nt) {
+    const int i = q % l, c = q / l;
+    Rinv[q] = (i <= c) ? S[i][c] : 0.0;
   }
 }
 
-// out[i, c] = sum_{k <= c} Y[i, k] Rinv[k, c]; one thread per row, in place allowed.
+// out[i, c] = sum_{k <= c} Y[i, k] Rinv[k, c] (in place allowed).  A CTA owns
+// kTrRows rows: it stages them in shared memory, then one thread per (row,
+// column) forms the product, so the FP64 work spreads over I * l / 256 CTAs.
+constexpr int kTrRows = 8;
 template <int LMAX>
-__global__ void k_trmm(const double* Y, int64_t I, int l, const double* __restrict__ Rinv,
-                       double* out, const DevState* st, int only_if_extra) {
+__global__ void __launch_bounds__(256) k_trmm(const double* Y, int64_t I, int l,
+                                              const double* __restrict__ Rinv, double* out,
+                                              const DevState* st, int only_if_extra) {
   __shared__ double Rs[LMAX * LMAX];
+  __shared__ double Ys[kTrRows][LMAX];
   if (only_if_extra && !st->extra_round) return;
   if (st->status) return;
-  for (int q = threadIdx.x; q < l * l; q += blockDim.x) Rs[(q % l) + LMAX * (q / l)] = Rinv[q];
+  const int tid = threadIdx.x;
+  for (int q = tid; q < l * l; q += blockDim.x) Rs[(q % l) + LMAX * (q / l)] = Rinv[q];
+  const int64_t i0 = (int64_t)blockIdx.x * kTrRows;
+  for (int q = tid; q < kTrRows * l; q += blockDim.x) {
+    const int r = q % kTrRows, k = q / kTrRows;
+    const int64_t i = i0 + r;
+    Ys[r][k] = (i < I) ? Y[i + I * k] : 0.0;
+  }
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= I) return;
-  double y[LMAX];
-#pragma unroll
-  for (int k = 0; k < LMAX; ++k) y[k] = (k < l) ? Y[i + I * k] : 0.0;
-#pragma unroll
-  for (int c = 0; c < LMAX; ++c) {
-    if (c < l) {
-      double acc = 0.0;
-#pragma unroll
-      for (int k = 0; k <= c; ++k) acc = fma(y[k], Rs[k + LMAX * c], acc);
-      out[i + I * c] = acc;
-    }
+  for (int q = tid; q < kTrRows * l; q += blockDim.x) {
+    const int r = q % kTrRows, c = q / kTrRows;
+    const int64_t i = i0 + r;
+    if (i >= I) continue;
+    double acc = 0.0;
+    for (int k = 0; k <= c; ++k) acc = fma(Ys[r][k], Rs[k + LMAX * c], acc);
+    out[i + I * c] = acc;
   }
 }
 
@@ -230,8 +252,8 @@ cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, dou
 
 cudaError_t launch_trmm(const double* Y, int64_t I, int l, const double* Rinv, double* out,
                         const DevState* st, int only_if_extra, cudaStream_t s) {
-  const int threads = 64;
-  const unsigned grid = (unsigned)((I + threads - 1) / threads);
+  const int threads = 256;
+  const unsigned grid = (unsigned)((I + kTrRows - 1) / kTrRows);
   count_launches(1);
   if (l <= 16) k_trmm<16><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
   else if (l <= 32) k_trmm<32><<<grid, threads, 0, s>>>(Y, I, l, Rinv, out, st, only_if_extra);
@@ -241,9 +263,13 @@ cudaError_t launch_trmm(const double* Y, int64_t I, int l, const double* Rinv, d
 }
 
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s) {
-  // round 0 (shift allowed), round 1, round 2 (only after a shifted round); in place on Y
-  for (int round = 0; round < 3; ++round) {
+                          cudaStream_t s, bool final_qr) {
+  // round 0 (shift allowed), round 1, round 2 (only after a shifted round); in place on Y.
+  // A normalisation inside the power iterations needs a well-conditioned basis
+  // of the same span, not an orthonormal one: one round (CholeskyQR) serves it,
+  // and the final QR of each mode (CholeskyQR2) removes the difference.
+  const int rounds = final_qr ? 3 : 1;
+  for (int round = 0; round < rounds; ++round) {
     cudaError_t e = launch_gram(Y, I, l, Gp, s);
     if (e != cudaSuccess) return e;
     e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s);

@@ -11,7 +11,7 @@
 
 namespace rcp {
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s);
+                          cudaStream_t s, bool final_qr);
 }  // namespace rcp
 
 namespace {
@@ -96,7 +96,7 @@ extern "C" rcp_status rcp_sketch_mode1_static(const void* X_dev, int32_t in_dtyp
                         s) != cudaSuccess)
     return RCP_ECUDA;
   if (launch_reduce(part, nsplit, I * l, Y, nullptr, 0, s) != cudaSuccess) return RCP_ECUDA;
-  if (launch_cholqr(Y, I, (int)l, Gp, Rinv, dst, s) != cudaSuccess) return RCP_ECUDA;
+  if (launch_cholqr(Y, I, (int)l, Gp, Rinv, dst, s, true) != cudaSuccess) return RCP_ECUDA;
   if (cudaMemcpyAsync(Q_dev, Y, sizeof(double) * I * l, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return RCP_ECUDA;
   if (status_dev) {

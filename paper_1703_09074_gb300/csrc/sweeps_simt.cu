@@ -103,12 +103,29 @@ __device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeVi
     }
     __syncthreads();
     if (row_ok) {
-      for (int jj = 0; jj < nj; ++jj) {
+      // U loads in flight per thread before their products (latency, not FMAs, bounds
+      // this loop); the |X|^2 of the mixed form is summed per tile in FP32
+      constexpr int U = sizeof(TA) == 4 ? 8 : 4;
+      TA tn = (TA)0;
+      int jj = 0;
+      for (; jj + U <= nj; jj += U) {
+        TA xs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xs[u] = (TA)__ldg(T + offs[jj + u] + v.L * i);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (NORM) tn = fma(xs[u], xs[u], tn);
+#pragma unroll
+          for (int c = 0; c < LMAX; ++c) acc[c] = fma(xs[u], Vs[jj + u][c], acc[c]);
+        }
+      }
+      for (; jj < nj; ++jj) {
         const TA x = (TA)__ldg(T + offs[jj] + v.L * i);
-        if (NORM) nrm = fma((double)x, (double)x, nrm);
+        if (NORM) tn = fma(x, x, tn);
 #pragma unroll
         for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Vs[jj][c], acc[c]);
       }
+      if (NORM) nrm += (double)tn;
     }
     __syncthreads();
   }
@@ -184,7 +201,18 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
       }
       __syncthreads();
       if (ok) {
-        for (int ii = 0; ii < ni; ++ii) {
+        constexpr int U = sizeof(TA) == 4 ? 8 : 4;  // loads in flight per thread
+        int ii = 0;
+        for (; ii + U <= ni; ii += U) {
+          TA xs[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) xs[u] = (TA)__ldg(T + base + v.L * (i0 + ii + u));
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < LMAX; ++c) acc[c] = fma(xs[u], Qs[(ii + u) * LMAX + c], acc[c]);
+        }
+        for (; ii < ni; ++ii) {
           const TA x = (TA)__ldg(T + base + v.L * (i0 + ii));
 #pragma unroll
           for (int c = 0; c < LMAX; ++c) acc[c] = fma(x, Qs[ii * LMAX + c], acc[c]);

@@ -1,6 +1,6 @@
 // Inline-PTX helpers for the 5th-generation tensor cores of sm_103a (tcgen05):
-// tensor-memory allocation, shared-memory matrix descriptors, kind::tf32 MMA
-// issue, completion tracking through mbarriers (with bounded waits), and
+// tensor-memory allocation, shared-memory matrix descriptors, kind::tf32 and
+// kind::f16 (BF16) MMA issue, completion tracking through mbarriers (with bounded waits), and
 // tensor-memory loads.  Written from the public PTX ISA description of
 // tcgen05; no other code is involved.
 #pragma once

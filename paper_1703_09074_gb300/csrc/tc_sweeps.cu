@@ -14,11 +14,14 @@
 //   Eq. sampleMatrix; Gaussian entries from the reduced-precision counter
 //   stream) or V = W of a power iteration (step 10).  Tensor-core problem:
 //   M = I (rows i), N = l, K = J.  The A operand needs K (= j) contiguous, the
-//   transpose of X's layout, so each thread loads one row i for 32 columns j
-//   (coalesced across the warp) and writes it as one 128-byte swizzled row.
+//   transpose of X's layout, so each thread loads one row i for 16 of the 32
+//   columns j of a chunk (coalesced across the warp) and writes them as half of
+//   the row's 128-byte swizzled line.  (A variant that landed X in a six-chunk
+//   cp.async ring in shared memory, one CTA per SM, measured slower: the
+//   per-chunk split and hand-off, not the loads, bound these sweeps.)
 //   Each CTA owns 128 rows and a contiguous range of j (split over J).  Two
-//   shared-memory stages and two register buffers: the loads of chunks k + 1
-//   and k + 2 are in flight while the MMAs of chunk k run.
+//   shared-memory stages and two register buffers: the loads of chunk k + 2 are
+//   in flight while chunk k + 1 is staged and the MMAs of chunk k run.
 // Column sweep (k_tc_cols): W = X_(1)^T Q (Algorithm 1 step 9) or the mode
 //   product T_2 = X x_1 Q_1^T (step 13).  M = J (128 columns j per block),
 //   N = l, K = I: K is X's contiguous direction, so 16-byte loads go straight
@@ -30,6 +33,8 @@ namespace rcp {
 namespace {
 
 constexpr int kATile = 16384;  // 128 rows x 128 bytes
+constexpr int kTT = 256;       // threads per CTA: two per tile row, 8 warps
+constexpr int kNB = 2;         // register buffers: chunk k + 2 loads while k + 1 waits to be staged
 constexpr long long kWaitBudget = 1LL << 31;  // clock cycles (about 1 s)
 
 // FP32 = hi + lo with hi = the value truncated to TF32 (10 fraction bits) and
@@ -60,18 +65,18 @@ __device__ __forceinline__ void issue_3xtf32(uint32_t d, uint32_t ahi, uint32_t 
   }
 }
 
-// Row sweep, one M = 128 block of rows per CTA (128 threads, thread = row).
+// Row sweep, one M = 128 block of rows per CTA (256 threads, two per row).
 template <int NP, int SRC, bool NORM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTT, 2)
 k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
           const float* __restrict__ WT, int64_t jchunk, float* __restrict__ part,
           double* __restrict__ normpart, DevState* st) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[2];   // stage s free: the MMAs that read it completed
   __shared__ uint32_t tbase_sh;
   __shared__ int abort_sh;
-  __shared__ double red[4];
+  __shared__ double red[8];
   __shared__ uint16_t boff[32 * 64];  // element t = jj * l + c of a chunk -> its byte offset in B
   using S = Stage<NP>;
   constexpr uint32_t NCOLS = NP;
@@ -88,11 +93,11 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(&tbase_sh, NCOLS);
-  for (int k = tid; k < 2 * 2 * NP * 32; k += 128) {  // B rows c >= l stay zero
+  for (int k = tid; k < 2 * 2 * NP * 32; k += kTT) {  // B rows c >= l stay zero
     const int s = k / (2 * NP * 32), e = k % (2 * NP * 32);
     *(float*)(sm + s * S::kBytes + 2 * S::kA + 4 * e) = 0.0f;
   }
-  for (int t = tid; t < 32 * l; t += 128) {
+  for (int t = tid; t < 32 * l; t += kTT) {
     const int jj = t / l, c = t - jj * l;
     boff[t] = (uint16_t)tc::sw128_offset((uint32_t)c, (uint32_t)jj);
   }
@@ -101,28 +106,30 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   tc::tc_fence_after_sync();
   const uint32_t tbase = tbase_sh;
 
-  const int64_t row = i0 + tid;
+  const int rl = tid & 127, half = tid >> 7;  // tile row, and which 16 of the 32 columns
+  const int64_t row = i0 + rl;
   const bool row_ok = row < I;
   const int nk = (int)((je - jb + 31) / 32);
-  float xa[32], xb[32];
-  float wa[NP / 4], wb[NP / 4];  // SRC 1: this thread's W^T values of a chunk (t = tid + 128 k)
+  constexpr int WV = NP * 32 / kTT;  // W^T values per thread and chunk
+  float xbuf[kNB][16];
+  float wbuf[kNB][WV];  // SRC 1: this thread's W^T values of a chunk (t = tid + kTT k)
   float nrm = 0.0f;
   uint32_t par0 = 0, par1 = 0;
-  auto load_w = [&](float (&wr)[NP / 4], int kc) {
+  auto load_w = [&](float (&wr)[WV], int kc) {
     const int64_t j0 = jb + 32LL * kc;
 #pragma unroll
-    for (int k = 0; k < NP / 4; ++k) {
-      const int t = tid + 128 * k;  // t = c * 32 + jj, covering NP x 32
+    for (int k = 0; k < WV; ++k) {
+      const int t = tid + kTT * k;  // t = c * 32 + jj, covering NP x 32
       const int c = t >> 5, jj = t & 31;
       const int64_t j = j0 + jj;
       wr[k] = (c < l && j < je) ? __ldg(WT + (int64_t)c * J + j) : 0.0f;
     }
   };
 
-  auto load = [&](float (&xr)[32], int kc) {
-    const int64_t j0 = jb + 32LL * kc;
+  auto load = [&](float (&xr)[16], int kc) {
+    const int64_t j0 = jb + 32LL * kc + 16 * half;
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
+    for (int jj = 0; jj < 16; ++jj) {
       const int64_t j = j0 + jj;
       xr[jj] = (row_ok && j < je) ? __ldg(X + row + I * j) : 0.0f;
     }
@@ -133,7 +140,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     *(float*)(Bl + off) = v - h;
   };
   // one 32-column chunk: stage it, prefetch chunk kc + 2 into the same registers, issue MMAs
-  auto step = [&](float (&xr)[32], float (&wr)[NP / 4], int kc) -> bool {
+  auto step = [&](float (&xr)[16], float (&wr)[WV], int kc) -> bool {
     const int s = kc & 1;
     uint8_t* Ah = sm + s * S::kBytes;
     uint8_t* Al = Ah + S::kA;
@@ -144,9 +151,9 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) atomicExch(&abort_sh, 1);
       if (s) par1 ^= 1; else par0 ^= 1;
     }
-    const uint32_t rr = (uint32_t)tid;
+    const uint32_t rr = (uint32_t)rl;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 4; ++c) {
       float4 h, lo;
       h.x = tf32_hi(xr[4 * c]);     lo.x = xr[4 * c] - h.x;
       h.y = tf32_hi(xr[4 * c + 1]); lo.y = xr[4 * c + 1] - h.y;
@@ -155,20 +162,21 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       if (NORM)
         nrm += xr[4 * c] * xr[4 * c] + xr[4 * c + 1] * xr[4 * c + 1] +
                xr[4 * c + 2] * xr[4 * c + 2] + xr[4 * c + 3] * xr[4 * c + 3];
-      const uint32_t off = rr * 128 + ((((uint32_t)c ^ (rr & 7u)) & 7u) << 4);
+      const uint32_t cc = (uint32_t)(4 * half + c);  // 16-byte chunk of the 128-byte row
+      const uint32_t off = rr * 128 + (((cc ^ (rr & 7u)) & 7u) << 4);
       *(float4*)(Ah + off) = h;
       *(float4*)(Al + off) = lo;
     }
     const int64_t j0 = jb + 32LL * kc;
     if (SRC == 0) {
-      if (kc + 2 < nk) load(xr, kc + 2);
+      if (kc + kNB < nk) load(xr, kc + kNB);
       // Omega_1[j, c] = element e = j l + c of the reduced-precision stream; local
       // index t = e - j0 l in [0, 32 l), counters g = e / 4 from g0 = (j0 l) / 4
       const int64_t e0 = j0 * l;
       const int lead = (int)(e0 & 3);                      // elements of quad g0 before e0
       const int tend = (int)min((int64_t)32, je - j0) * l;  // valid elements of this chunk
       const int nq = (32 * l + lead + 3) >> 2;
-      for (int q = tid; q < nq; q += 128) {
+      for (int q = tid; q < nq; q += kTT) {
         const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)((e0 >> 2) + q));
         const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
@@ -179,16 +187,18 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < NP / 4; ++k) {
-        const int t = tid + 128 * k;
+      for (int k = 0; k < WV; ++k) {
+        const int t = tid + kTT * k;
         const int c = t >> 5, jj = t & 31;
         if (c < l) put_b(Bh, Bl, tc::sw128_offset((uint32_t)c, (uint32_t)jj), wr[k]);
       }
-      if (kc + 2 < nk) {
-        load(xr, kc + 2);
-        load_w(wr, kc + 2);
+      if (kc + kNB < nk) {
+        load(xr, kc + kNB);
+        load_w(wr, kc + kNB);
       }
     }
+    // (a variant that handed stages over through an mbarrier with one arrival per
+    // thread instead of this CTA barrier measured slower)
     tc::fence_proxy_async_smem();
     __syncthreads();
     if (abort_sh) return false;
@@ -201,16 +211,18 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     return true;
   };
 
-  if (nk > 0) load(xa, 0);
-  if (nk > 1) load(xb, 1);
-  if (SRC == 1) {
-    if (nk > 0) load_w(wa, 0);
-    if (nk > 1) load_w(wb, 1);
+#pragma unroll
+  for (int b = 0; b < kNB; ++b) {
+    if (b < nk) {
+      load(xbuf[b], b);
+      if (SRC == 1) load_w(wbuf[b], b);
+    }
   }
   bool ok = true;
-  for (int kc = 0; kc < nk && ok; kc += 2) {
-    ok = step(xa, wa, kc);
-    if (ok && kc + 1 < nk) ok = step(xb, wb, kc + 1);
+  for (int kc = 0; kc < nk && ok; kc += kNB) {
+#pragma unroll
+    for (int b = 0; b < kNB; ++b)
+      if (ok && kc + b < nk) ok = step(xbuf[b], wbuf[b], kc + b);
   }
   for (int kc = (nk >= 2 ? nk - 2 : 0); kc < nk && ok; ++kc) {
     const int s = kc & 1;
@@ -221,7 +233,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   tc::tc_fence_after_sync();
   if (!ok && tid == 0) set_status(st, RCP_ETIMEOUT);
 
-  {
+  if (warp < 4) {  // warp w reads tensor-memory lanes 32 w .. 32 w + 31
     const int64_t r = i0 + warp * 32 + lane;
 #pragma unroll
     for (int cg = 0; cg < NP / 32; ++cg) {
@@ -243,7 +255,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   tc::tc_fence_before_sync();
   __syncthreads();
   if (NORM && tid == 0) normpart[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] =
-      red[0] + red[1] + red[2] + red[3];
+      ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
   if (warp == 0) tc::tmem_dealloc(tbase, NCOLS);
 }
 
@@ -252,13 +264,13 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
 // Two tensor-memory accumulators: the epilogue of j-block b runs while the
 // MMAs of block b + 1 are queued.
 template <int NP, bool TTM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTT, 2)
 k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad,
           const float* __restrict__ QTh, const float* __restrict__ QTl, float* __restrict__ out,
           DevState* st) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t mbar[3];  // two stages + accumulator ready
+  __shared__ uint64_t mbar[3];  // two stages free + accumulator ready
   __shared__ uint32_t tbase_sh;
   __shared__ int abort_sh;
   using S = Stage<NP>;
@@ -280,16 +292,17 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
   const int64_t njb = (J + 127) / 128;
   const int64_t my_blocks = (njb > blockIdx.x) ? (njb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t total = my_blocks * nkc;
-  const int c16 = tid & 7, r0 = tid >> 3;
-  constexpr int QV = NP / 16;  // float4 of Q^T hi (and lo) per thread and chunk
-  float4 xa[8], xb[8];
-  float4 qa[2 * QV], qb[2 * QV];
+  const int c16 = tid & 7, r0 = tid >> 3;  // 16-byte chunk along i; rows r0 + 32 p
+  constexpr int QV = NP * 8 / kTT;  // float4 of Q^T hi (and lo) per thread and chunk
+  constexpr int NB = kNB;
+  float4 xbuf[NB][4];
+  float4 qbuf[NB][2 * QV];
   uint32_t par0 = 0, par1 = 0, pacc = 0;
   auto load_q = [&](float4 (&qv)[2 * QV], int64_t g) {
     const int kc = (int)(g % nkc);
 #pragma unroll
     for (int k = 0; k < QV; ++k) {
-      const int t = tid + 128 * k;  // t = c * 8 + cc
+      const int t = tid + kTT * k;  // t = c * 8 + cc
       const int c = t >> 3, cc = t & 7;
       const int64_t src = (int64_t)c * Ipad + 32LL * kc + 4 * cc;
       qv[k] = __ldg((const float4*)(QTh + src));
@@ -297,13 +310,13 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     }
   };
 
-  auto load = [&](float4 (&xv)[8], int64_t g) {
+  auto load = [&](float4 (&xv)[4], int64_t g) {
     const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
     const int kc = (int)(g % nkc);
     const int64_t i = 32LL * kc + 4 * c16;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const int64_t j = jblk * 128 + r0 + 16 * p;
+    for (int p = 0; p < 4; ++p) {
+      const int64_t j = jblk * 128 + r0 + 32 * p;
       xv[p] = (j < J && i < I) ? __ldg((const float4*)(X + j * I + i)) : make_float4(0, 0, 0, 0);
     }
   };
@@ -315,7 +328,7 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     const int64_t j = jblk * 128 + warp * 32 + lane;
     const uint32_t acc = tbase + (uint32_t)((blk_local & 1) * NP);
 #pragma unroll
-    for (int cg = 0; cg < NP / 32; ++cg) {
+    for (int cg = 0; cg < NP / 32 && warp < 4; ++cg) {  // warp w: tensor-memory lanes 32 w ..
       float v[32];
       tc::tmem_ld32(acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), v);
       if (j < J && good) {
@@ -332,7 +345,7 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     tc::tc_fence_before_sync();
     return good;
   };
-  auto step = [&](float4 (&xv)[8], float4 (&qv)[2 * QV], int64_t g) -> bool {
+  auto step = [&](float4 (&xv)[4], float4 (&qv)[2 * QV], int64_t g) -> bool {
     const int s = (int)(g & 1);
     const int kc = (int)(g % nkc);
     const int64_t blk = g / nkc;
@@ -346,8 +359,8 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
       if (s) par1 ^= 1; else par0 ^= 1;
     }
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const uint32_t r = (uint32_t)(r0 + 16 * p);
+    for (int p = 0; p < 4; ++p) {
+      const uint32_t r = (uint32_t)(r0 + 32 * p);
       const uint32_t off = r * 128 + ((((uint32_t)c16 ^ (r & 7u)) & 7u) << 4);
       float4 h, lo;
       h.x = tf32_hi(xv[p].x); lo.x = xv[p].x - h.x;
@@ -359,15 +372,15 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
     }
 #pragma unroll
     for (int k = 0; k < QV; ++k) {
-      const int t = tid + 128 * k;
+      const int t = tid + kTT * k;
       const int c = t >> 3, cc = t & 7;
       const uint32_t off = c * 128 + ((((uint32_t)cc ^ ((uint32_t)c & 7u)) & 7u) << 4);
       *(float4*)(Bh + off) = qv[k];
       *(float4*)(Bl + off) = qv[QV + k];
     }
-    if (g + 2 < total) {
-      load(xv, g + 2);
-      load_q(qv, g + 2);
+    if (g + NB < total) {
+      load(xv, g + NB);
+      load_q(qv, g + NB);
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -385,17 +398,19 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
   };
 
   if (total > 0) {
-    load(xa, 0);
-    load_q(qa, 0);
-  }
-  if (total > 1) {
-    load(xb, 1);
-    load_q(qb, 1);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (b < total) {
+        load(xbuf[b], b);
+        load_q(qbuf[b], b);
+      }
+    }
   }
   bool ok = true;
-  for (int64_t g = 0; g < total && ok; g += 2) {
-    ok = step(xa, qa, g);
-    if (ok && g + 1 < total) ok = step(xb, qb, g + 1);
+  for (int64_t g = 0; g < total && ok; g += NB) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (ok && g + b < total) ok = step(xbuf[b], qbuf[b], g + b);
   }
   if (ok && total > 0) ok = epilogue(my_blocks - 1);
   for (int64_t g = (total >= 2 ? total - 2 : 0); g < total && ok; ++g) {
@@ -442,7 +457,7 @@ cudaError_t rows_launch(const float* X, int64_t I, int64_t J, int l, uint64_t se
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((I + 127) / 128), (unsigned)nsplit);
   count_launches(1);
-  kern<<<grid, 128, Stage<NP>::kSmem, s>>>(X, I, J, l, seed, sid, WT, jchunk, part, normpart, st);
+  kern<<<grid, kTT, Stage<NP>::kSmem, s>>>(X, I, J, l, seed, sid, WT, jchunk, part, normpart, st);
   return cudaGetLastError();
 }
 
@@ -454,7 +469,7 @@ cudaError_t cols_launch(const float* X, int64_t I, int64_t J, int l, int64_t Ipa
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<NP>::kSmem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<grid, 128, Stage<NP>::kSmem, s>>>(X, I, J, l, Ipad, QT, QT + (int64_t)NP * Ipad, out, st);
+  kern<<<grid, kTT, Stage<NP>::kSmem, s>>>(X, I, J, l, Ipad, QT, QT + (int64_t)NP * Ipad, out, st);
   return cudaGetLastError();
 }
 

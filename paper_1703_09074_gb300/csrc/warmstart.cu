@@ -52,52 +52,88 @@ __global__ void __launch_bounds__(256) k_ws_gather(const WsItem* __restrict__ it
 }
 
 // ---------------------------------------------------------------- canonical basis
-// Cyclic Jacobi (Golub & Van Loan, Section 8.5) on the symmetric l x l matrix A
-// (row pitch L, FP64, shared memory) by one warp: A <- J^T A J and V <- V J for
-// each pair (p, q), lane k updating entry k of the two rows / columns.  FP64
-// keeps the eigenvectors of the small, clustered eigenvalues (the noise
-// directions) reproducible to the oracle's eigensolver.  Returns after the
-// off-diagonal part is negligible or after 30 sweeps.
+// Parallel-order Jacobi (Golub & Van Loan, Section 8.5; round-robin ordering
+// after Brent & Luk) on the symmetric l x l matrix A (row pitch L, FP64, shared
+// memory) by one warp.  A sweep is n - 1 rounds (n = l rounded up to even); a
+// round rotates n / 2 disjoint pairs at once: lane i forms the rotation of pair
+// i from the round's A, then the lanes apply all of them to the columns (and to
+// V) and then to the rows, A <- J^T A J, V <- V J.  FP64 keeps the eigenvectors
+// of the small, clustered noise eigenvalues reproducible to the oracle's
+// eigensolver.  Stops when the off-diagonal part is negligible or after 30
+// sweeps.
 __device__ void warp_jacobi(double* A, double* V, int l) {
   const int lane = threadIdx.x & 31;
+  __shared__ double cs_sh[3][kWsL / 2][2];  // per calling warp (warps 0-2): c, s of each pair
+  __shared__ int pq_sh[3][kWsL / 2][2];
+  const int w = (threadIdx.x >> 5) % 3;
+  double (*cs)[2] = cs_sh[w];
+  int (*pq)[2] = pq_sh[w];
   for (int k = lane; k < L2; k += 32) V[k] = ((k / L) == (k % L)) ? 1.0 : 0.0;
   __syncwarp();
+  const int n = (l + 1) & ~1, np = n / 2;  // player n - 1 is a dummy when l is odd
   for (int sweep = 0; sweep < 30; ++sweep) {
-    // stop once every |a_pq| <= 1e-15 sqrt(a_pp a_qq) (computed by all lanes alike)
-    double worst = 0.0;
+    // stop once every |a_pq| <= 1e-14 max_k a_kk (a threshold relative to the
+    // largest eigenvalue: the small, clustered noise eigenvalues would never meet
+    // one relative to sqrt(a_pp a_qq) in FP64)
+    double worst = 0.0, dmax = 0.0;
     for (int e = lane; e < l * l; e += 32) {
       const int p = e / l, q = e % l;
-      if (p < q) {
-        const double d = sqrt(fabs(A[p * L + p] * A[q * L + q]));
-        worst = fmax(worst, fabs(A[p * L + q]) / fmax(d, 1e-300));
-      }
+      if (p < q) worst = fmax(worst, fabs(A[p * L + q]));
+      if (p == q) dmax = fmax(dmax, A[p * L + p]);
     }
-    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-    if (!(worst > 1e-15)) break;
-    for (int p = 0; p < l - 1; ++p) {
-      for (int q = p + 1; q < l; ++q) {
-        const double apq = A[p * L + q];
-        if (apq == 0.0) continue;
-        const double tau = (A[q * L + q] - A[p * L + p]) / (2.0 * apq);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        __syncwarp();
-        if (lane < l) {  // columns p, q
-          const double akp = A[lane * L + p], akq = A[lane * L + q];
-          A[lane * L + p] = c * akp - s * akq;
-          A[lane * L + q] = s * akp + c * akq;
-          const double vkp = V[lane * L + p], vkq = V[lane * L + q];
-          V[lane * L + p] = c * vkp - s * vkq;
-          V[lane * L + q] = s * vkp + c * vkq;
+    for (int o = 16; o > 0; o >>= 1) {
+      worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    }
+    if (!(worst > 1e-14 * dmax)) break;
+    const double skip = 1e-17 * dmax;  // rotations below this change nothing representable
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < np) {
+        // circle method: position 0 holds player 0, position k >= 1 player (k - 1 + r) mod (n - 1) + 1
+        const int pa = lane == 0 ? 0 : (lane - 1 + r) % (n - 1) + 1;
+        const int pb = (n - 1 - lane - 1 + r) % (n - 1) + 1;
+        int p = min(pa, pb), q = max(pa, pb);
+        double c = 1.0, sn = 0.0;
+        if (q < l) {
+          const double apq = A[p * L + q];
+          if (fabs(apq) > skip) {
+            const double tau = (A[q * L + q] - A[p * L + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        } else {
+          p = q = -1;  // the dummy's partner sits out this round
         }
-        __syncwarp();
-        if (lane < l) {  // rows p, q
-          const double apk = A[p * L + lane], aqk = A[q * L + lane];
-          A[p * L + lane] = c * apk - s * aqk;
-          A[q * L + lane] = s * apk + c * aqk;
-        }
-        __syncwarp();
+        cs[lane][0] = c;
+        cs[lane][1] = sn;
+        pq[lane][0] = p;
+        pq[lane][1] = q;
       }
+      __syncwarp();
+      for (int task = lane; task < l * np; task += 32) {  // columns p, q of A and V
+        const int i = task % np, k = task / np;
+        const int p = pq[i][0], q = pq[i][1];
+        if (p < 0 || cs[i][1] == 0.0) continue;
+        const double c = cs[i][0], sn = cs[i][1];
+        const double akp = A[k * L + p], akq = A[k * L + q];
+        A[k * L + p] = c * akp - sn * akq;
+        A[k * L + q] = sn * akp + c * akq;
+        const double vkp = V[k * L + p], vkq = V[k * L + q];
+        V[k * L + p] = c * vkp - sn * vkq;
+        V[k * L + q] = sn * vkp + c * vkq;
+      }
+      __syncwarp();
+      for (int task = lane; task < l * np; task += 32) {  // rows p, q of A
+        const int i = task % np, k = task / np;
+        const int p = pq[i][0], q = pq[i][1];
+        if (p < 0 || cs[i][1] == 0.0) continue;
+        const double c = cs[i][0], sn = cs[i][1];
+        const double apk = A[p * L + k], aqk = A[q * L + k];
+        A[p * L + k] = c * apk - sn * aqk;
+        A[q * L + k] = sn * apk + c * aqk;
+      }
+      __syncwarp();
     }
   }
 }
