@@ -82,7 +82,8 @@ __device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
 // Gauss-Jordan inverse of the symmetric positive definite V (row pitch R + 1)
 // by the whole CTA in FP64, without pivoting; V^{-1} lands in columns R..2R-1
 // of Aug (row pitch 64, R <= 32).  At step k only the R columns k+1..R+k
-// change.  Returns false (uniformly) when a pivot is not above floor_.
+// change.  fcol: 64 doubles of scratch.  Returns false (uniformly) when a
+// pivot is not above floor_.
 __device__ bool cta_gj_inverse64(const double* V, int R, double* Aug, double* fcol,
                                  double floor_) {
   const int tid = threadIdx.x;
@@ -91,17 +92,19 @@ __device__ bool cta_gj_inverse64(const double* V, int R, double* Aug, double* fc
     Aug[i * 64 + j] = j < R ? V[i * (R + 1) + j] : (j - R == i ? 1.0 : 0.0);
   }
   __syncthreads();
+  double* rowk = fcol + 32;  // the scaled pivot row, columns k + 1 .. R + k
   for (int k = 0; k < R; ++k) {
     const double piv = Aug[k * 64 + k];
     if (!(piv > floor_)) return false;
     const double pinv = 1.0 / piv;
+    // column k and the scaled row k go to scratch, so the update below reads
+    // nothing that it writes: two barriers per step
     if (tid < R) fcol[tid] = Aug[tid * 64 + k];
-    __syncthreads();
-    for (int j = k + 1 + tid; j <= R + k; j += kThreads) Aug[k * 64 + j] *= pinv;
+    for (int j = tid; j < R; j += kThreads) rowk[j] = Aug[k * 64 + k + 1 + j] * pinv;
     __syncthreads();
     for (int e = tid; e < R * R; e += kThreads) {
-      const int i = e / R, j = k + 1 + e % R;
-      if (i != k) Aug[i * 64 + j] = fma(-fcol[i], Aug[k * 64 + j], Aug[i * 64 + j]);
+      const int i = e / R, jj = e % R, j = k + 1 + jj;
+      Aug[i * 64 + j] = (i == k) ? rowk[jj] : fma(-fcol[i], rowk[jj], Aug[i * 64 + j]);
     }
     __syncthreads();
   }
@@ -184,7 +187,7 @@ __device__ void als_body(const PersArgs& a, int g) {
         if (!a.direct64 && R <= 32) {
           double trd = 0.0;
           for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
-          gj = cta_gj_inverse64(V, R, Aug, invd64, (double)R * 2.220446049250313e-16 * trd);
+          gj = cta_gj_inverse64(V, R, Aug, wsum, (double)R * 2.220446049250313e-16 * trd);
         }
         if (warp == 0) {
           float tr = 0.0f;

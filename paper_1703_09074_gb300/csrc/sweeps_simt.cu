@@ -146,8 +146,8 @@ __device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeVi
   }
 }
 
-// Column sweep body for CTA bx of nb persistent CTAs.
-template <int LMAX, typename TIn, typename TA, bool GRAM>
+// Column sweep body for CTA bx of nb persistent CTAs of NT threads (columns j) each.
+template <int LMAX, typename TIn, typename TA, bool GRAM, int NT = kProjThreads>
 __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
                                                const double* __restrict__ Q, TA* __restrict__ W,
                                                double* __restrict__ gpart, int bx, int nb);
@@ -165,15 +165,15 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
 
 }  // namespace
 
-template <int LMAX, typename TIn, typename TA, bool GRAM>
+template <int LMAX, typename TIn, typename TA, bool GRAM, int NT>
 __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
                                                const double* __restrict__ Q, TA* __restrict__ W,
                                                double* __restrict__ gpart, int bx, int nb) {
   extern __shared__ double sm[];
   TA* Qs = (TA*)sm;                                 // kProjRows x LMAX
-  double* Ws = sm + kProjRows * LMAX;               // kProjThreads x (LMAX + 1), GRAM only
+  double* Ws = sm + kProjRows * LMAX;               // NT x (LMAX + 1), GRAM only
   __shared__ unsigned short pairs[kMaxL * (kMaxL + 1) / 2];
-  constexpr int kSlots = (LMAX * (LMAX + 1) / 2 + kProjThreads - 1) / kProjThreads;
+  constexpr int kSlots = (LMAX * (LMAX + 1) / 2 + NT - 1) / NT;
   const int tid = threadIdx.x;
   const int npairs = l * (l + 1) / 2;
   double gacc[GRAM ? kSlots : 1];
@@ -184,8 +184,8 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
     for (int c2 = tid; c2 < l; ++c2) pairs[base + c2 - tid] = (unsigned short)((tid << 8) | c2);
   }
 
-  for (int64_t jb = bx; jb * kProjThreads < v.J; jb += nb) {
-    const int64_t j = jb * kProjThreads + tid;
+  for (int64_t jb = bx; jb * NT < v.J; jb += nb) {
+    const int64_t j = jb * NT + tid;
     const bool ok = j < v.J;
     const int64_t a = ok ? j % v.L : 0, b = ok ? j / v.L : 0;
     const int64_t base = a + v.L * v.I * b;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
     for (int64_t i0 = 0; i0 < v.I; i0 += kProjRows) {
       const int ni = (int)min((int64_t)kProjRows, v.I - i0);
       __syncthreads();
-      for (int k = tid; k < kProjRows * LMAX; k += kProjThreads) {
+      for (int k = tid; k < kProjRows * LMAX; k += NT) {
         const int ii = k / LMAX, c = k - ii * LMAX;
         Qs[k] = (ii < ni && c < l) ? (TA)Q[(i0 + ii) + v.I * c] : (TA)0;
       }
@@ -230,11 +230,11 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
       __syncthreads();
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        const int p = tid + s * kProjThreads;
+        const int p = tid + s * NT;
         if (p < npairs) {
           const int c1 = pairs[p] >> 8, c2 = pairs[p] & 0xff;
           double sum = 0.0;
-          for (int t = 0; t < kProjThreads; ++t)
+          for (int t = 0; t < NT; ++t)
             sum = fma(Ws[t * (LMAX + 1) + c1], Ws[t * (LMAX + 1) + c2], sum);
           gacc[s] += sum;
         }
@@ -244,7 +244,7 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
   if (GRAM) {
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
-      const int p = tid + s * kProjThreads;
+      const int p = tid + s * NT;
       if (p < npairs) gpart[(int64_t)bx * npairs + p] = gacc[s];
     }
   }
@@ -252,12 +252,13 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
 
 namespace {
 
-template <int LMAX, typename TIn, typename TA, bool GRAM>
-__global__ void __launch_bounds__(kProjThreads)
+template <int LMAX, typename TIn, typename TA, bool GRAM, int NT>
+__global__ void __launch_bounds__(NT)
 k_col_sweep(const TIn* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
             TA* __restrict__ W, double* __restrict__ gpart) {
-  col_sweep_body<LMAX, TIn, TA, GRAM>(T, v, l, Q, W, gpart, blockIdx.x, gridDim.x);
+  col_sweep_body<LMAX, TIn, TA, GRAM, NT>(T, v, l, Q, W, gpart, blockIdx.x, gridDim.x);
 }
+
 
 int lmax_bucket(int l) { return l <= 16 ? 16 : l <= 32 ? 32 : l <= 48 ? 48 : 64; }
 
@@ -309,12 +310,14 @@ cudaError_t col_sweep_typed(const TIn* T, ModeView v, int l, const double* Q, TA
   count_launches(1);
   if (gpart) {
     const size_t smem = smem_q + (size_t)kProjThreads * (LMAX + 1) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, TA, true>,
+    cudaError_t e = cudaFuncSetAttribute(k_col_sweep<LMAX, TIn, TA, true, kProjThreads>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_col_sweep<LMAX, TIn, TA, true><<<nblocks, kProjThreads, smem, s>>>(T, v, l, Q, W, gpart);
+    k_col_sweep<LMAX, TIn, TA, true, kProjThreads>
+        <<<nblocks, kProjThreads, smem, s>>>(T, v, l, Q, W, gpart);
   } else {
-    k_col_sweep<LMAX, TIn, TA, false><<<nblocks, kProjThreads, smem_q, s>>>(T, v, l, Q, W, gpart);
+    k_col_sweep<LMAX, TIn, TA, false, kProjThreads>
+        <<<nblocks, kProjThreads, smem_q, s>>>(T, v, l, Q, W, gpart);
   }
   return cudaGetLastError();
 }

@@ -21,7 +21,8 @@
 //   per-chunk split and hand-off, not the loads, bound these sweeps.)
 //   Each CTA owns 128 rows and a contiguous range of j (split over J).  Two
 //   shared-memory stages and two register buffers: the loads of chunk k + 2 are
-//   in flight while chunk k + 1 is staged and the MMAs of chunk k run.
+//   in flight while chunk k + 1 is staged and the MMAs of chunk k run.  A ninth
+//   warp only issues the MMAs, so no staging warp waits for the issue.
 // Column sweep (k_tc_cols): W = X_(1)^T Q (Algorithm 1 step 9) or the mode
 //   product T_2 = X x_1 Q_1^T (step 13).  M = J (128 columns j per block),
 //   N = l, K = I: K is X's contiguous direction, so 16-byte loads go straight
@@ -33,7 +34,13 @@ namespace rcp {
 namespace {
 
 constexpr int kATile = 16384;  // 128 rows x 128 bytes
-constexpr int kTT = 256;       // threads per CTA: two per tile row, 8 warps
+constexpr int kTT = 256;       // staging threads per CTA: two per tile row, 8 warps
+constexpr int kCTA = kTT + 32; // plus one warp that only issues the MMAs
+
+// Barrier 1 between the staging warps and the issuing warp (every thread of the CTA).
+__device__ __forceinline__ void stage_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kCTA) : "memory");
+}
 constexpr int kNB = 2;         // register buffers: chunk k + 2 loads while k + 1 waits to be staged
 constexpr long long kWaitBudget = 1LL << 31;  // clock cycles (about 1 s)
 
@@ -67,7 +74,7 @@ __device__ __forceinline__ void issue_3xtf32(uint32_t d, uint32_t ahi, uint32_t 
 
 // Row sweep, one M = 128 block of rows per CTA (256 threads, two per row).
 template <int NP, int SRC, bool NORM>
-__global__ void __launch_bounds__(kTT, 2)
+__global__ void __launch_bounds__(kCTA, 2)
 k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t seed, uint32_t sid,
           const float* __restrict__ WT, int64_t jchunk, float* __restrict__ part,
           double* __restrict__ normpart, DevState* st) {
@@ -93,11 +100,12 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(&tbase_sh, NCOLS);
-  for (int k = tid; k < 2 * 2 * NP * 32; k += kTT) {  // B rows c >= l stay zero
+  const bool issuer = warp == kTT / 32;
+  for (int k = issuer ? 2 * 2 * NP * 32 : tid; k < 2 * 2 * NP * 32; k += kTT) {  // B rows c >= l stay zero
     const int s = k / (2 * NP * 32), e = k % (2 * NP * 32);
     *(float*)(sm + s * S::kBytes + 2 * S::kA + 4 * e) = 0.0f;
   }
-  for (int t = tid; t < 32 * l; t += kTT) {
+  for (int t = issuer ? 32 * l : tid; t < 32 * l; t += kTT) {
     const int jj = t / l, c = t - jj * l;
     boff[t] = (uint16_t)tc::sw128_offset((uint32_t)c, (uint32_t)jj);
   }
@@ -197,34 +205,47 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
         load_w(wr, kc + kNB);
       }
     }
-    // (a variant that handed stages over through an mbarrier with one arrival per
-    // thread instead of this CTA barrier measured slower)
+    // hand the stage to the issuing warp (variants that used a CTA barrier with the
+    // issue by thread 0, or an mbarrier with one arrival per thread, measured slower)
     tc::fence_proxy_async_smem();
-    __syncthreads();
-    if (abort_sh) return false;
-    if (tid == 0) {
-      tc::tc_fence_after_sync();
-      issue_3xtf32(tbase, tc::smem_u32(Ah), tc::smem_u32(Al), tc::smem_u32(Bh), tc::smem_u32(Bl),
-                   IDESC, kc == 0);
-      tc::mma_commit(&mbar[s]);
-    }
-    return true;
+    stage_barrier();
+    return !abort_sh;
   };
 
+  bool ok = true;
+  if (issuer) {
+    for (int kc = 0; kc < nk; ++kc) {
+      stage_barrier();
+      if (abort_sh) break;
+      if (lane == 0) {
+        const int s = kc & 1;
+        uint8_t* Ah = sm + s * S::kBytes;
+        uint8_t* Al = Ah + S::kA;
+        uint8_t* Bh = Al + S::kA;
+        uint8_t* Bl = Bh + S::kB;
+        tc::tc_fence_after_sync();
+        issue_3xtf32(tbase, tc::smem_u32(Ah), tc::smem_u32(Al), tc::smem_u32(Bh),
+                     tc::smem_u32(Bl), IDESC, kc == 0);
+        tc::mma_commit(&mbar[s]);
+      }
+      __syncwarp();
+    }
+  } else {
 #pragma unroll
-  for (int b = 0; b < kNB; ++b) {
-    if (b < nk) {
-      load(xbuf[b], b);
-      if (SRC == 1) load_w(wbuf[b], b);
+    for (int b = 0; b < kNB; ++b) {
+      if (b < nk) {
+        load(xbuf[b], b);
+        if (SRC == 1) load_w(wbuf[b], b);
+      }
+    }
+    for (int kc = 0; kc < nk && ok; kc += kNB) {
+#pragma unroll
+      for (int b = 0; b < kNB; ++b)
+        if (ok && kc + b < nk) ok = step(xbuf[b], wbuf[b], kc + b);
     }
   }
-  bool ok = true;
-  for (int kc = 0; kc < nk && ok; kc += kNB) {
-#pragma unroll
-    for (int b = 0; b < kNB; ++b)
-      if (ok && kc + b < nk) ok = step(xbuf[b], wbuf[b], kc + b);
-  }
-  for (int kc = (nk >= 2 ? nk - 2 : 0); kc < nk && ok; ++kc) {
+  // the staging warps (whose phase bits track the stage barriers) wait for the last MMAs
+  for (int kc = (nk >= 2 ? nk - 2 : 0); kc < nk && ok && !issuer; ++kc) {
     const int s = kc & 1;
     const uint32_t par = s ? par1 : par0;
     if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) ok = false;
@@ -264,7 +285,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
 // Two tensor-memory accumulators: the epilogue of j-block b runs while the
 // MMAs of block b + 1 are queued.
 template <int NP, bool TTM>
-__global__ void __launch_bounds__(kTT, 2)
+__global__ void __launch_bounds__(kCTA, 2)
 k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad,
           const float* __restrict__ QTh, const float* __restrict__ QTl, float* __restrict__ out,
           DevState* st) {
@@ -382,38 +403,58 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
       load(xv, g + NB);
       load_q(qv, g + NB);
     }
+    // hand the stage to the issuing warp; that barrier also orders the epilogue of
+    // block blk - 2 (same accumulator, read by warps 0-3 before they staged chunk 0
+    // of block blk) before the MMAs into it
     tc::fence_proxy_async_smem();
-    __syncthreads();
+    stage_barrier();
     if (abort_sh) return false;
-    if (tid == 0) {
-      tc::tc_fence_after_sync();
-      issue_3xtf32(tbase + (uint32_t)((blk & 1) * NP), tc::smem_u32(Ah), tc::smem_u32(Al),
-                   tc::smem_u32(Bh), tc::smem_u32(Bl), IDESC, kc == 0);
-      tc::mma_commit(&mbar[s]);
-    }
     bool good = true;
     if (kc == 0 && blk > 0) good = epilogue(blk - 1);
-    if (tid == 0 && kc == nkc - 1) tc::mma_commit(&mbar[2]);
     return good;
   };
 
-  if (total > 0) {
+  const bool issuer = warp == kTT / 32;
+  bool ok = true;
+  if (issuer) {
+    for (int64_t g = 0; g < total; ++g) {
+      stage_barrier();
+      if (abort_sh) break;
+      if (lane == 0) {
+        const int s = (int)(g & 1);
+        const int kc = (int)(g % nkc);
+        const int64_t blk = g / nkc;
+        uint8_t* Ah = sm + s * S::kBytes;
+        uint8_t* Al = Ah + S::kA;
+        uint8_t* Bh = Al + S::kA;
+        uint8_t* Bl = Bh + S::kB;
+        tc::tc_fence_after_sync();
+        issue_3xtf32(tbase + (uint32_t)((blk & 1) * NP), tc::smem_u32(Ah), tc::smem_u32(Al),
+                     tc::smem_u32(Bh), tc::smem_u32(Bl), IDESC, kc == 0);
+        tc::mma_commit(&mbar[s]);
+        if (kc == nkc - 1) tc::mma_commit(&mbar[2]);
+      }
+      __syncwarp();
+    }
+  } else {
+    if (total > 0) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      if (b < total) {
-        load(xbuf[b], b);
-        load_q(qbuf[b], b);
+      for (int b = 0; b < NB; ++b) {
+        if (b < total) {
+          load(xbuf[b], b);
+          load_q(qbuf[b], b);
+        }
       }
     }
-  }
-  bool ok = true;
-  for (int64_t g = 0; g < total && ok; g += NB) {
+    for (int64_t g = 0; g < total && ok; g += NB) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (ok && g + b < total) ok = step(xbuf[b], qbuf[b], g + b);
+      for (int b = 0; b < NB; ++b)
+        if (ok && g + b < total) ok = step(xbuf[b], qbuf[b], g + b);
+    }
+    if (ok && total > 0) ok = epilogue(my_blocks - 1);
   }
-  if (ok && total > 0) ok = epilogue(my_blocks - 1);
-  for (int64_t g = (total >= 2 ? total - 2 : 0); g < total && ok; ++g) {
+  // the staging warps (whose phase bits track the stage barriers) wait for the last MMAs
+  for (int64_t g = (total >= 2 ? total - 2 : 0); g < total && ok && !issuer; ++g) {
     const int s = (int)(g & 1);
     const uint32_t par = s ? par1 : par0;
     if (!tc::mbar_wait(&mbar[s], par, kWaitBudget)) ok = false;
@@ -457,7 +498,7 @@ cudaError_t rows_launch(const float* X, int64_t I, int64_t J, int l, uint64_t se
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((I + 127) / 128), (unsigned)nsplit);
   count_launches(1);
-  kern<<<grid, kTT, Stage<NP>::kSmem, s>>>(X, I, J, l, seed, sid, WT, jchunk, part, normpart, st);
+  kern<<<grid, kCTA, Stage<NP>::kSmem, s>>>(X, I, J, l, seed, sid, WT, jchunk, part, normpart, st);
   return cudaGetLastError();
 }
 
@@ -469,7 +510,7 @@ cudaError_t cols_launch(const float* X, int64_t I, int64_t J, int l, int64_t Ipa
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<NP>::kSmem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<grid, kTT, Stage<NP>::kSmem, s>>>(X, I, J, l, Ipad, QT, QT + (int64_t)NP * Ipad, out, st);
+  kern<<<grid, kCTA, Stage<NP>::kSmem, s>>>(X, I, J, l, Ipad, QT, QT + (int64_t)NP * Ipad, out, st);
   return cudaGetLastError();
 }
 
