@@ -43,6 +43,11 @@ WORKLOADS = {
                        "one CUDA graph"),
 }
 
+# DRAM bytes (read + written) per launch of the mode-1 tensor-core sweeps, from one ncu
+# capture of the current kernels (profiles/tc_sweeps_mode1_400cubed.md); None elsewhere.
+NCU_TRAFFIC = {("c2", "mixed", "apply"): 275.27e6 + 3.58e6,
+               ("c2", "mixed", "project"): 256.86e6 + 14.30e6}
+
 # GB300 FP64 arithmetic peak used for ALU-bound FP64 kernels: 152 SMs x 2 FP64
 # FMA per clock per SM x 2 FLOP x 2.07 GHz ("Roofline").
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -293,7 +298,8 @@ def run_ours(args):
         achieved = xbytes / per_launch_s / 1e9
         roof = {"bound": "hbm", "kernel": f"mode-1 {dom} sweep", "achieved": achieved,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": None, "peak_source": src,
+                "traffic": NCU_TRAFFIC.get((args.workload, args.precision, dom)),
+                "peak_source": src,
                 "algorithmic": f"{xbytes} B per launch (one read of X)"}
     sketch_gbs = xbytes / (sk_ms / sk_n / 1e3) / 1e9 if sk_n else None
 
