@@ -133,7 +133,7 @@ __device__ void als_body(const PersArgs& a, int g) {
   double* nu = Xs + lmax * R;                   // R
   double* red = nu + R;                         // 64 scalars
   double* wsum = red + 64;                      // kWarps x 64 row / norm partials
-  float* U32 = (float*)(wsum + kWarps * 64);    // R x (R + 1) FP32 factor, or 32 x 32 Z ~ V^{-1}
+  float* U32 = (float*)(wsum + kWarps * 64);    // R x (R + 1) FP32 copy of V / its factor
   float* invd32 = U32 + max(R * (R + 1), 1024); // R
   TM* Fac = (TM*)(((uintptr_t)(invd32 + R) + 15) & ~(uintptr_t)15);  // factor copies
   TM* Bs = Fac + ftot;                          // lmax x kBP
@@ -328,7 +328,7 @@ __device__ void als_body(const PersArgs& a, int g) {
       if (g < ln) {
         if (gw0 == 0) prepare_solve(n0);
         const int path = (int)red[0];
-        const bool use32 = path == 1 || path == 2;
+        const bool use32 = path == 1;  // FP32 factor: FP64 refinement follows
         // path 3: x_c = sum_k m_k (V^{-1})_{kc}, lane c (R <= 32)
         auto gjmatvec = [&](double (&v)[2]) {
           double d = 0.0;
@@ -341,16 +341,6 @@ __device__ void als_body(const PersArgs& a, int g) {
         };
         if (G == 1) {
           // one CTA per problem: warp w solves rows w, w + 8, ... on its own
-          double* wsc = wsum + warp * 64;  // this warp's broadcast scratch
-          auto wmatvec = [&](double (&v)[2]) {
-            wsc[lane] = v[0];
-            __syncwarp();
-            float d = 0.0f;
-            for (int k = 0; k < R; ++k) d = fmaf((float)wsc[k], U32[k * 32 + lane], d);
-            __syncwarp();
-            v[0] = (lane < R) ? (double)d : 0.0;
-            v[1] = 0.0;
-          };
           for (int i = warp; i < ln; i += kWarps) {
             double m[2], x[2];
 #pragma unroll
@@ -363,7 +353,6 @@ __device__ void als_body(const PersArgs& a, int g) {
               x[h] = sm_;
             }
             if (path == 3) gjmatvec(x);
-            else if (path == 2) wmatvec(x);
             else if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
             for (int step = 0; use32 && step < 6; ++step) {
@@ -379,8 +368,7 @@ __device__ void als_body(const PersArgs& a, int g) {
 #pragma unroll
               for (int h = 0; h < 2; ++h)
                 if (lane + 32 * h >= R) rr[h] = 0.0;
-              if (path == 2) wmatvec(rr);
-              else warp_solve(U32, invd32, R, rr);
+              warp_solve(U32, invd32, R, rr);
               x[0] += rr[0];
               x[1] += rr[1];
               double dm = fmax(fabs(rr[0]), fabs(rr[1])), xm = fmax(fabs(x[0]), fabs(x[1]));
@@ -428,16 +416,6 @@ __device__ void als_body(const PersArgs& a, int g) {
           }
           __syncthreads();
           double m[2] = {0.0, 0.0}, x[2] = {0.0, 0.0};
-          // d = v Z for the inverse path: lane c sums v_k Z[k][c] (v broadcast from shared memory)
-          auto matvec_z = [&](double (&v)[2]) {
-            xs[lane] = v[0];
-            __syncwarp();
-            float d = 0.0f;
-            for (int k = 0; k < R; ++k) d = fmaf((float)xs[k], U32[k * 32 + lane], d);
-            __syncwarp();
-            v[0] = (lane < R) ? (double)d : 0.0;
-            v[1] = 0.0;
-          };
           if (warp == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -449,7 +427,6 @@ __device__ void als_body(const PersArgs& a, int g) {
               x[h] = s;
             }
             if (path == 3) gjmatvec(x);
-            else if (path == 2) matvec_z(x);
             else if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
           }
@@ -484,8 +461,7 @@ __device__ void als_body(const PersArgs& a, int g) {
                   for (int w = 0; w < kWarps; ++w) sum += wsum[w * 64 + lane + 32 * h];
                   rr[h] = (lane + 32 * h < R) ? m[h] - sum : 0.0;
                 }
-                if (path == 2) matvec_z(rr);
-                else warp_solve(U32, invd32, R, rr);
+                warp_solve(U32, invd32, R, rr);
                 x[0] += rr[0];
                 x[1] += rr[1];
                 // stop once max |correction| <= 2^-52 max |x| (warp-uniform)

@@ -71,14 +71,17 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
 // overwrites the upper triangle by back substitution, one column per thread.
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
+// after32 != 0: runs only when the FP32 attempt of the same round failed.
 __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int l,
                                               double* __restrict__ Rinv, DevState* st,
-                                              double shift_rows, int round, int als_mode) {
+                                              double shift_rows, int round, int als_mode,
+                                              int after32) {
   __shared__ double S[kMaxL][kMaxL + 1];   // Schur complement / R^{-1} (upper), R (lower)
   __shared__ double rdiag[kMaxL];
   __shared__ double red[32];
   __shared__ int bad_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (after32 && !st->chol32_fail) return;
   if (round == 2 && !st->extra_round) return;
   if (round == 0 && tid == 0) st->extra_round = 0;
   const int np = l * (l + 1) / 2;
@@ -161,6 +164,77 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
     const int i = q % l, c = q / l;
     Rinv[q] = (i <= c) ? S[i][c] : 0.0;
   }
+}
+
+// The same factorisation in FP32 for the rounds that tolerate it: the
+// normalisations inside the power iterations (any well-conditioned basis of
+// the span serves) and the first round of each final CholeskyQR2 (whose second
+// round, in FP64, restores orthonormality to FP64 rounding; Q is the unique
+// qr+ factor whatever R the first round used).  FP32 steps are short where
+// FP64 steps are chains of slow operations.  No shift: a pivot at or below
+// 64 l u_32 trace(G), or a non-finite entry, sets chol32_fail and the FP64
+// kernel that follows redoes the round (with its shifted fallback).
+__global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, int l,
+                                                double* __restrict__ Rinv, DevState* st,
+                                                int round) {
+  __shared__ float S[kMaxL][kMaxL + 1];   // Schur complement / R^{-1} (upper), R (lower)
+  __shared__ float rdiag[kMaxL];
+  __shared__ double red[32];
+  __shared__ int bad_sh;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (round == 0 && tid == 0) st->extra_round = 0;
+  const int np = l * (l + 1) / 2;
+  if (tid == 0) bad_sh = 0;
+  __syncthreads();
+  double tr = 0.0;
+  for (int p = tid; p < np; p += nt) {
+    int c1 = 0, rem = p;
+    while (rem >= l - c1) { rem -= l - c1; ++c1; }
+    const double g = Gp[p];
+    if (!isfinite(g)) bad_sh = 1;
+    if (rem == 0) tr += g;
+    S[c1][c1 + rem] = (float)g;
+  }
+  tr = block_sum(tr, red);
+  if (tid == 0) red[31] = tr;
+  __syncthreads();
+  const float floor_ = 64.0f * (float)l * 5.9604645e-08f * (float)red[31];
+  bool ok = !bad_sh;
+  for (int k = 0; k < l && ok; ++k) {
+    const float d = S[k][k];
+    if (!(d > floor_)) {  // uniform: every thread read the same d
+      ok = false;
+      break;
+    }
+    const float rs = rsqrtf(d), dinv = rs * rs;
+    for (int j = k + tid; j < l; j += nt) {
+      if (j == k) rdiag[k] = rs;
+      else S[j][k] = S[k][j] * rs;
+    }
+    const int mm = l - k - 1;
+    for (int q = tid; q < mm * mm; q += nt) {
+      const int i = k + 1 + q / mm, j = k + 1 + q % mm;
+      if (j >= i) S[i][j] = fmaf(-S[k][i] * dinv, S[k][j], S[i][j]);
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) st->chol32_fail = 1;
+    return;
+  }
+  for (int c = tid; c < l; c += nt) {
+    for (int i = c; i >= 0; --i) {
+      float v = (i == c) ? 1.0f : 0.0f;
+      for (int k = i + 1; k <= c; ++k) v = fmaf(-S[k][i], S[k][c], v);
+      S[i][c] = v * rdiag[i];
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < l * l; q += nt) {
+    const int i = q % l, c = q / l;
+    Rinv[q] = (i <= c) ? (double)S[i][c] : 0.0;
+  }
+  if (tid == 0) st->chol32_fail = 0;
 }
 
 // out[i, c] = sum_{k <= c} Y[i, k] Rinv[k, c] (in place allowed).  A CTA owns
@@ -246,7 +320,7 @@ cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStrea
 cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
                         int round, int als_mode, cudaStream_t s) {
   count_launches(1);
-  k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode);
+  k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode, 0);
   return cudaGetLastError();
 }
 
@@ -268,11 +342,22 @@ cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv,
   // A normalisation inside the power iterations needs a well-conditioned basis
   // of the same span, not an orthonormal one: one round (CholeskyQR) serves it,
   // and the final QR of each mode (CholeskyQR2) removes the difference.
+  // Round 0 is factored in FP32 first (FP64 only when that fails); the later
+  // rounds of the final QR in FP64.
   const int rounds = final_qr ? 3 : 1;
   for (int round = 0; round < rounds; ++round) {
     cudaError_t e = launch_gram(Y, I, l, Gp, s);
     if (e != cudaSuccess) return e;
-    e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s);
+    if (round == 0 && l <= kMaxL) {
+      count_launches(2);
+      k_chol32<<<1, 256, 0, s>>>(Gp, l, Rinv, st, round);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, (double)I, round, 0, 1);
+      e = cudaGetLastError();
+    } else {
+      e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s);
+    }
     if (e != cudaSuccess) return e;
     e = launch_trmm(Y, I, l, Rinv, Y, st, round == 2, s);
     if (e != cudaSuccess) return e;

@@ -38,7 +38,7 @@ struct DevState {
   int extra_round;     // set when a QR needed the shifted fallback (one more CholQR round)
   int als_done;        // ALS converged or hit the cap
   int als_iters;       // sweeps run
-  int pad;
+  int chol32_fail;     // the FP32 Cholesky of a CholeskyQR round fell back to FP64
   double norm_x2;
   double norm_b2;
   double fit;

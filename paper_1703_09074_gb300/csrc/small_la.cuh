@@ -71,38 +71,4 @@ __device__ void warp_solve(const T* U, const T* invd, int R, double (&b)[2]) {
   b[1] = (double)y[1];
 }
 
-// One warp inverts the SPD matrix V (FP64 in shared memory, row pitch R + 1,
-// R <= 32) in FP32 registers by Gauss-Jordan elimination without pivoting
-// (lane j holds column j; the pivot column travels by shuffles), and writes
-// Z ~ V^{-1} (row pitch 32) to shared memory.  False on a pivot <= floor.
-__device__ inline bool warp_inverse32(const double* V, int R, float* Z, float floor_) {
-  const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) a[i] = (i < R && lane < R) ? (float)V[i * (R + 1) + lane] : 0.0f;
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < R) {
-      // the pivot column first, all shuffles back to back, then the updates
-      float f[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) f[i] = __shfl_sync(0xffffffffu, a[i], k);
-      const float p = f[k];
-      ok = ok && (p > floor_);
-      const float pinv = 1.0f / p;
-      const float rowk = (lane == k) ? pinv : a[k] * pinv;
-      const bool pivot_lane = lane == k;
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i != k) a[i] = fmaf(-f[i], rowk, pivot_lane ? 0.0f : a[i]);
-      a[k] = rowk;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i)
-    if (i < R && lane < R) Z[i * 32 + lane] = a[i];
-  return ok;
-}
-
 }  // namespace rcp

@@ -121,7 +121,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   constexpr int WV = NP * 32 / kTT;  // W^T values per thread and chunk
   float xbuf[kNB][16];
   float wbuf[kNB][WV];  // SRC 1: this thread's W^T values of a chunk (t = tid + kTT k)
-  float nrm = 0.0f;
+  double nrm = 0.0;  // |X|^2 of this thread's elements: FP32 per chunk, FP64 across chunks
   uint32_t par0 = 0, par1 = 0;
   auto load_w = [&](float (&wr)[WV], int kc) {
     const int64_t j0 = jb + 32LL * kc;
@@ -160,6 +160,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       if (s) par1 ^= 1; else par0 ^= 1;
     }
     const uint32_t rr = (uint32_t)rl;
+    float cn = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float4 h, lo;
@@ -168,13 +169,14 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
       h.z = tf32_hi(xr[4 * c + 2]); lo.z = xr[4 * c + 2] - h.z;
       h.w = tf32_hi(xr[4 * c + 3]); lo.w = xr[4 * c + 3] - h.w;
       if (NORM)
-        nrm += xr[4 * c] * xr[4 * c] + xr[4 * c + 1] * xr[4 * c + 1] +
-               xr[4 * c + 2] * xr[4 * c + 2] + xr[4 * c + 3] * xr[4 * c + 3];
+        cn += xr[4 * c] * xr[4 * c] + xr[4 * c + 1] * xr[4 * c + 1] +
+              xr[4 * c + 2] * xr[4 * c + 2] + xr[4 * c + 3] * xr[4 * c + 3];
       const uint32_t cc = (uint32_t)(4 * half + c);  // 16-byte chunk of the 128-byte row
       const uint32_t off = rr * 128 + (((cc ^ (rr & 7u)) & 7u) << 4);
       *(float4*)(Ah + off) = h;
       *(float4*)(Al + off) = lo;
     }
+    if (NORM) nrm += (double)cn;
     const int64_t j0 = jb + 32LL * kc;
     if (SRC == 0) {
       if (kc + kNB < nk) load(xr, kc + kNB);
@@ -269,7 +271,7 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
     }
   }
   if (NORM) {
-    double d = (double)nrm;
+    double d = nrm;
     for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
     if (lane == 0) red[warp] = d;
   }
