@@ -195,6 +195,7 @@ def run_ours(args):
     import synth
     from paper_1703_09074_gb300 import Plan
     from paper_1703_09074_gb300 import _lib
+    from paper_1703_09074_gb300 import parallel
 
     ws, rank, local = dist()
     torch.cuda.set_device(local)
@@ -238,11 +239,7 @@ def run_ours(args):
     if pg:
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = parallel.max_over_ranks(sum(step_ms), device=dev)
     res = plan.result()
 
     # per-kernel device times over the timed region
@@ -316,12 +313,8 @@ def run_ours(args):
             t0 = time.perf_counter()
             plan.decompose_host(Xh, Ah, lh)
             e2e.append(time.perf_counter() - t0)
-    e2e_v = statistics.mean(e2e) if e2e else float("nan")
+    e2e_v = parallel.max_over_ranks(statistics.mean(e2e) if e2e else float("nan"), device=dev)
     d2h = sum(d * w.rank * 8 for d in w.dims) + w.rank * 8
-    if pg:
-        t = torch.tensor([e2e_v], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_v = float(t.item())
 
     # the plain FP64 GPU path on the same tensor, for the equal-fit comparison
     f64_cmp = None
@@ -385,11 +378,17 @@ def run_batched(args):
     import torch
     import synth
     from paper_1703_09074_gb300 import BatchedPlan, WarmStartNet
+    from paper_1703_09074_gb300 import parallel
     from paper_1703_09074_gb300 import warmstart as W
 
     ws_, rank, local = dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    pg = None
+    if ws_ > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=dev)
+        pg = td
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
     net = None
@@ -404,7 +403,8 @@ def run_batched(args):
                       "val_fit_at_10_sweeps": [h.get("val_fit") for h in hist],
                       "setup_s": time.perf_counter() - t0}
         del data
-    ws = synth.batch(256, seed=0, p=8, q=1)
+    # weak scaling: every rank decomposes its own batch of 256 (seed = rank)
+    ws = synth.batch(256, seed=rank, p=8, q=1)
     Xs = [torch.from_numpy(w.kolda).to(dev) for w in ws]
     probs = [dict(dims=w.dims, rank=w.rank, oversample=8, power_iters=1, tol=1e-10,
                   max_iters=50, seed=b) for b, w in enumerate(ws)]
@@ -432,7 +432,10 @@ def run_batched(args):
         return sum(a.elapsed_time(b) for a, b in ev) / steps, res, clk
 
     clocks = Clocks(local)
+    if pg:
+        pg.barrier()
     ms, res, clk = timed(net, args.steps, clocks)
+    ms = parallel.max_over_ranks(ms, device=dev)
     ms_rnd, res_rnd, _ = timed(None, max(1, min(args.steps, 3))) if net is not None else (ms, res, None)
     nbytes = sum(X.numel() * 4 for X in Xs)
     fits = [r["fit"] for r in res]
@@ -441,6 +444,7 @@ def run_batched(args):
     # iteration (two sweeps and a QR) and the TTM sweep; ALS, back-projection, lambda;
     # with the warm start also gather, canonicalisation, the network's 7 kernels, init
     launches = 1 + 3 * (3 + 3 * 1) + 3 + (10 if net is not None else 0)
+    total_tensors = parallel.sum_over_ranks(len(ws), device=dev)
     line = {"metric": METRIC + " [batched workload]", "value": ms / 1e3, "unit": "s",
             "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -449,7 +453,7 @@ def run_batched(args):
             "config": {"workload": WORKLOADS["c5"][1], "tensors": len(ws), "bytes": nbytes,
                        "warm_start": args.warm_start, "autotuned_ctas_per_sm": list(choice),
                        "l2": "inputs (3 GB) larger than L2, 512 MB flush between steps"},
-            "tensors_per_s": len(ws) / (ms / 1e3),
+            "tensors_per_s": total_tensors / (ms / 1e3),
             "input_gbs": nbytes / (ms / 1e3) / 1e9,
             "fit_mean": float(statistics.mean(fits)),
             "rel_err_median": float(statistics.median(errs)), "rel_err_max": float(max(errs)),
@@ -466,7 +470,11 @@ def run_batched(args):
     bp.close()
     if net is not None:
         net.close()
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
 
 
 def main():
