@@ -8,11 +8,13 @@
 //   barrier;
 //   phase B (row owners): M[i, :] = sum_g M_g[i, :] in fixed order, then the
 //             row of Definition 2's solve x = M[i, :] V^{-1} with V the Hadamard
-//             product of the other Grams: an FP32 Cholesky factor of V and up to
-//             six steps of FP64 iterative refinement (residual m - x V in FP64)
-//             until the correction falls below FP64 roundoff; if the FP32
-//             factorisation meets a pivot below 64 u_32 trace(V), an FP64
-//             Cholesky (with a diagonal shift as last resort) is used instead;
+//             product of the other Grams.  R <= 32: V^{-1} by Gauss-Jordan in
+//             double-word FP32 arithmetic (prepared by the row owners while the
+//             others compute MTTKRP partials), x0 = m V^{-1} in FP64 and one
+//             step of FP64 iterative refinement x = x0 + (m - x0 V) V^{-1}.
+//             R > 32: an FP32 Cholesky factor of V and up to six FP64
+//             refinement steps.  If a pivot is too small, an FP64 Cholesky
+//             (with a diagonal shift as last resort) is used instead;
 //   barrier;
 //   phase C (every CTA, identically): column norms of the new factor,
 //             normalisation (lambda = the norms at n = N), its Gram, and after
@@ -27,6 +29,7 @@
 // mixed form, whose factor Grams are also accumulated in FP32).
 #include <math.h>
 
+#include "dw_arith.cuh"
 #include "rcp_internal.cuh"
 #include "small_la.cuh"
 
@@ -79,38 +82,6 @@ __device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
   return grid_sync(a.bar, (unsigned)G, a.abort_flag);
 }
 
-// Gauss-Jordan inverse of the symmetric positive definite V (row pitch R + 1)
-// by the whole CTA in FP64, without pivoting; V^{-1} lands in columns R..2R-1
-// of Aug (row pitch 64, R <= 32).  At step k only the R columns k+1..R+k
-// change.  fcol: 64 doubles of scratch.  Returns false (uniformly) when a
-// pivot is not above floor_.
-__device__ bool cta_gj_inverse64(const double* V, int R, double* Aug, double* fcol,
-                                 double floor_) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < 2 * R * R; e += kThreads) {
-    const int i = e / (2 * R), j = e % (2 * R);
-    Aug[i * 64 + j] = j < R ? V[i * (R + 1) + j] : (j - R == i ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  double* rowk = fcol + 32;  // the scaled pivot row, columns k + 1 .. R + k
-  for (int k = 0; k < R; ++k) {
-    const double piv = Aug[k * 64 + k];
-    if (!(piv > floor_)) return false;
-    const double pinv = 1.0 / piv;
-    // column k and the scaled row k go to scratch, so the update below reads
-    // nothing that it writes: two barriers per step
-    if (tid < R) fcol[tid] = Aug[tid * 64 + k];
-    for (int j = tid; j < R; j += kThreads) rowk[j] = Aug[k * 64 + k + 1 + j] * pinv;
-    __syncthreads();
-    for (int e = tid; e < R * R; e += kThreads) {
-      const int i = e / R, jj = e % R, j = k + 1 + jj;
-      Aug[i * 64 + j] = (i == k) ? rowk[jj] : fma(-fcol[i], rowk[jj], Aug[i * 64 + j]);
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
 // KACC: MTTKRP outputs (l_n x R) per thread, at most KACC * kThreads.
 template <typename TM, int KACC>
 __device__ void als_body(const PersArgs& a, int g) {
@@ -138,7 +109,13 @@ __device__ void als_body(const PersArgs& a, int g) {
   TM* Fac = (TM*)(((uintptr_t)(invd32 + R) + 15) & ~(uintptr_t)15);  // factor copies
   TM* Bs = Fac + ftot;                          // lmax x kBP
   TM* Ks = Bs + lmax * kBP;                     // kTileJ x R
-  double* Aug = (double*)(((uintptr_t)(Ks + kTileJ * R) + 15) & ~(uintptr_t)15);  // 32 x 64
+  // the double-word Gauss-Jordan copies, 32 x 64 float2 each; after the inverse
+  // one holds V^{-1} in FP64 (Zd, row pitch 32) and the other is scratch (Sx)
+  float2* A0 = (float2*)(((uintptr_t)(Ks + kTileJ * R) + 15) & ~(uintptr_t)15);
+  float2* A1 = A0 + 32 * 64;
+  float* Gr32 = (float*)(A1 + 32 * 64);         // N x R x R FP32 Grams (mixed form)
+  double* Zd = (double*)((R & 1) ? A0 : A1);
+  double* Sx = (double*)((R & 1) ? A1 : A0);
   DevState* st = a.st;
 
   // ---- initial factors (modes 2..N) and their Grams, identical in every CTA
@@ -159,46 +136,74 @@ __device__ void als_body(const PersArgs& a, int g) {
     __syncthreads();
     for (int e = tid; e < R * R; e += kThreads) {
       const int r = e % R, c = e / R;
-      double acc = 0.0;
-      for (int i = 0; i < lm; ++i) acc = fma(Xs[i + lm * r], Xs[i + lm * c], acc);
-      Gr[m * R * R + e] = acc;
+      if (sizeof(TM) == 4) {
+        // mixed form: from the FP32 copies, as after every update
+        float acc = 0.0f;
+        for (int i = 0; i < lm; ++i)
+          acc = fmaf((float)Fac[foff[m] + i + lm * r], (float)Fac[foff[m] + i + lm * c], acc);
+        Gr32[m * R * R + e] = acc;
+        Gr[m * R * R + e] = (double)acc;
+      } else {
+        double acc = 0.0;
+        for (int i = 0; i < lm; ++i) acc = fma(Xs[i + lm * r], Xs[i + lm * c], acc);
+        Gr[m * R * R + e] = acc;
+      }
     }
     __syncthreads();
   }
 
-  // V = Hadamard product of the Grams of every mode but n0 (FP64, and an FP32
-  // copy), and the solve it needs: path 3 (R <= 32) the FP64 inverse by the whole
-  // CTA, path 1 an FP32 Cholesky factor plus FP64 refinement (R > 32), path 0 the
+  // V = Hadamard product of the Grams of every mode but n0 (FP64) and the
+  // solve it needs: path 3 (R <= 32) V^{-1} by double-word Gauss-Jordan into Zd,
+  // path 1 (R > 32) an FP32 Cholesky factor plus FP64 refinement, path 0 the
   // FP64 Cholesky of V itself (with a diagonal shift as last resort).  The path
   // goes to red[0].
   auto prepare_solve = [&](int n0) {
-        // V = Hadamard product of the other Grams (FP64) and its FP32 copy
+        // (with one CTA per problem the path-3 solve keeps l_n x R outputs in 8 KB)
+        const bool dw = !a.direct64 && R <= 32 && (G > 1 || lmax * R <= 1024);
         for (int e = tid; e < R * R; e += kThreads) {
           const int r = e % R, c = e / R;
           double v = 1.0;
           for (int m = 0; m < N; ++m)
             if (m != n0) v *= Gr[m * R * R + e];
           V[r * (R + 1) + c] = v;
-          U32[r * (R + 1) + c] = (float)v;
+          if (!dw) {
+            U32[r * (R + 1) + c] = (float)v;
+          } else if (sizeof(TM) == 4) {
+            // the FP32 Grams' product in double-word form (exact for N = 3)
+            dwf w = {1.0f, 0.0f};
+            bool first = true;
+            for (int m = 0; m < N; ++m) {
+              if (m == n0) continue;
+              const float gm = Gr32[m * R * R + e];
+              if (first) {
+                w = {gm, 0.0f};
+                first = false;
+              } else {
+                w = dw_mul(w, {gm, 0.0f});
+              }
+            }
+            A0[r * 64 + c] = make_float2(w.hi, w.lo);
+          } else {
+            const dwf w = dw_from_double(v);
+            A0[r * 64 + c] = make_float2(w.hi, w.lo);
+          }
         }
         __syncthreads();
-        // path 3 (R <= 32): FP64 inverse by the whole CTA, one FP64 product per row
         bool gj = false;
-        if (!a.direct64 && R <= 32) {
-          double trd = 0.0;
-          for (int c = 0; c < R; ++c) trd += V[c * (R + 1) + c];
-          gj = cta_gj_inverse64(V, R, Aug, wsum, (double)R * 2.220446049250313e-16 * trd);
+        if (dw) {
+          double* zd = nullptr;
+          gj = cta_gj_inverse_dw<kThreads>(R, A0, A1, &zd);
         }
         if (warp == 0) {
-          float tr = 0.0f;
-          for (int c = 0; c < R; ++c) tr += U32[c * (R + 1) + c];
-          const float floor32 = 64.0f * 5.9604645e-08f * tr;
           int path = 0;
           if (gj) {
             path = 3;
-          } else if (a.direct64 || R <= 32) {
+          } else if (dw || a.direct64) {
             // path 0 below (a failed path-3 pivot means V is nearly singular)
           } else {
+            float tr = 0.0f;
+            for (int c = 0; c < R; ++c) tr += U32[c * (R + 1) + c];
+            const float floor32 = 64.0f * 5.9604645e-08f * tr;
             bool f32ok = warp_chol(U32, R, floor32);
             if (f32ok)
               for (int k = lane; k < R; k += 32) invd32[k] = 1.0f / U32[k * (R + 1) + k];
@@ -329,18 +334,66 @@ __device__ void als_body(const PersArgs& a, int g) {
         if (gw0 == 0) prepare_solve(n0);
         const int path = (int)red[0];
         const bool use32 = path == 1;  // FP32 factor: FP64 refinement follows
-        // path 3: x_c = sum_k m_k (V^{-1})_{kc}, lane c (R <= 32)
-        auto gjmatvec = [&](double (&v)[2]) {
-          double d = 0.0;
-          for (int k = 0; k < R; ++k) {
-            const double vk = __shfl_sync(0xffffffffu, v[0], k);
-            if (lane < R) d = fma(vk, Aug[k * 64 + R + lane], d);
-          }
-          v[0] = lane < R ? d : 0.0;
-          v[1] = 0.0;
+        const bool want_ip = n0 == N - 1;  // <Bhat, B> is needed after the last mode only
+        // sum of the four partial vectors the split products leave in wsum
+        auto sum4 = [&](int c) {
+          return (wsum[c] + wsum[64 + c]) + (wsum[128 + c] + wsum[192 + c]);
         };
-        if (G == 1) {
-          // one CTA per problem: warp w solves rows w, w + 8, ... on its own
+        // out_c = sum_k v_k Mt[k][c] (R <= 32, lane c), split over warps 0..3 (one
+        // per sub-partition: FP64 issues at one warp instruction per 64 cycles
+        // per sub-partition) into wsum[w][c]
+        auto split_mv = [&](const double* v, const double* Mt, int ld) {
+          if (warp < 4) {
+            double d = 0.0;
+            if (lane < R)
+              for (int k = warp; k < R; k += 4) d = fma(v[k], Mt[k * ld + lane], d);
+            wsum[warp * 64 + lane] = d;
+          }
+        };
+        if (G == 1 && path == 3) {
+          // one CTA per problem, R <= 32 and ln R <= 1024: outputs (i, c) over all
+          // threads; m, x0 in Sx, the residual in Xs (free until phase C)
+          double* Mm = Sx;
+          double* X0 = Sx + 1024;
+          for (int e = tid; e < nout; e += kThreads) {
+            double sm_ = 0.0;
+            for (int gg = 0; gg < GW; ++gg) sm_ += a.part[(int64_t)gg * nout + e];
+            Mm[e] = sm_;
+          }
+          __syncthreads();
+          for (int e = tid; e < nout; e += kThreads) {
+            const int c = e / ln, i = e - c * ln;
+            double d = 0.0;
+            for (int k = 0; k < R; ++k) d = fma(Mm[i + ln * k], Zd[k * 32 + c], d);
+            X0[e] = d;
+          }
+          __syncthreads();
+          for (int e = tid; e < nout; e += kThreads) {
+            const int c = e / ln, i = e - c * ln;
+            double d = 0.0;
+            for (int k = 0; k < R; ++k) d = fma(X0[i + ln * k], V[k * (R + 1) + c], d);
+            Xs[e] = Mm[e] - d;
+          }
+          __syncthreads();
+          for (int e = tid; e < nout; e += kThreads) {
+            const int c = e / ln, i = e - c * ln;
+            double d = 0.0;
+            for (int k = 0; k < R; ++k) d = fma(Xs[i + ln * k], Zd[k * 32 + c], d);
+            const double x = X0[e] + d;
+            a.rows[e] = x;
+            X0[e] = Mm[e] * x;
+          }
+          if (want_ip) {
+            __syncthreads();
+            for (int i = tid; i < ln; i += kThreads) {
+              double ip = 0.0;
+              for (int c = 0; c < R; ++c) ip += X0[i + ln * c];
+              a.ipp[i] = ip;
+            }
+          }
+          __syncthreads();
+        } else if (G == 1) {
+          // one CTA per problem, paths 0 and 1: warp w solves rows w, w + 8, ...
           for (int i = warp; i < ln; i += kWarps) {
             double m[2], x[2];
 #pragma unroll
@@ -352,8 +405,7 @@ __device__ void als_body(const PersArgs& a, int g) {
               m[h] = sm_;
               x[h] = sm_;
             }
-            if (path == 3) gjmatvec(x);
-            else if (path == 1) warp_solve(U32, invd32, R, x);
+            if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
             for (int step = 0; use32 && step < 6; ++step) {
               double rr[2] = {m[0], m[1]};
@@ -387,14 +439,17 @@ __device__ void als_body(const PersArgs& a, int g) {
                 ip += m[h] * x[h];
               }
             }
-            for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
-            if (lane == 0) a.ipp[i] = ip;
+            if (want_ip) {
+              for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
+              if (lane == 0) a.ipp[i] = ip;
+            }
           }
           __syncthreads();
         } else
         {
-        // all warps reduce one row's partials; warp 0 solves with the FP32 factor;
-        // the FP64 residuals m - x V of the refinement are split over all warps
+        // all warps reduce one row's partials; path 3 splits its three FP64
+        // products over warps 0..3; paths 0 and 1 solve on warp 0 and split the
+        // FP64 residuals of the refinement over all warps
         double* xs = wsum + (kWarps - 1) * 64;  // x broadcast (the last warp's slot is read first)
         for (int i = g; i < ln; i += G) {
 #pragma unroll
@@ -416,6 +471,31 @@ __device__ void als_body(const PersArgs& a, int g) {
           }
           __syncthreads();
           double m[2] = {0.0, 0.0}, x[2] = {0.0, 0.0};
+          if (path == 3) {
+            // m, x0 and the residual in Sx[0..95]
+            if (warp == 0) {
+              double sm_ = 0.0;
+              if (lane < R)
+                for (int w = 0; w < kWarps; ++w) sm_ += wsum[w * 64 + lane];
+              m[0] = sm_;
+              Sx[lane] = sm_;
+            }
+            __syncthreads();
+            split_mv(Sx, Zd, 32);  // x0 = m V^{-1}
+            __syncthreads();
+            if (warp == 0) {
+              x[0] = lane < R ? sum4(lane) : 0.0;
+              Sx[32 + lane] = x[0];
+            }
+            __syncthreads();
+            split_mv(Sx + 32, V, R + 1);  // x0 V
+            __syncthreads();
+            if (warp == 0) Sx[64 + lane] = lane < R ? m[0] - sum4(lane) : 0.0;
+            __syncthreads();
+            split_mv(Sx + 64, Zd, 32);  // (m - x0 V) V^{-1}
+            __syncthreads();
+            if (warp == 0 && lane < R) x[0] += sum4(lane);
+          } else {
           if (warp == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -426,8 +506,7 @@ __device__ void als_body(const PersArgs& a, int g) {
               m[h] = s;
               x[h] = s;
             }
-            if (path == 3) gjmatvec(x);
-            else if (path == 1) warp_solve(U32, invd32, R, x);
+            if (path == 1) warp_solve(U32, invd32, R, x);
             else warp_solve(V, invd64, R, x);
           }
           if (use32) {
@@ -477,6 +556,7 @@ __device__ void als_body(const PersArgs& a, int g) {
               if (red[6] != 0.0) break;
             }
           }
+          }
           if (warp == 0) {
             double ip = 0.0;
 #pragma unroll
@@ -487,8 +567,10 @@ __device__ void als_body(const PersArgs& a, int g) {
                 ip += m[h] * x[h];
               }
             }
-            for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
-            if (lane == 0) a.ipp[i] = ip;
+            if (want_ip) {
+              for (int o = 16; o > 0; o >>= 1) ip += __shfl_xor_sync(0xffffffffu, ip, o);
+              if (lane == 0) a.ipp[i] = ip;
+            }
           }
           __syncthreads();
         }
@@ -535,6 +617,7 @@ __device__ void als_body(const PersArgs& a, int g) {
           const TM* fr = Fac + foff[n0] + ln * r;
           const TM* fc = Fac + foff[n0] + ln * c;
           for (int i = 0; i < ln; ++i) s = fmaf((float)fr[i], (float)fc[i], s);
+          Gr32[n0 * R * R + e] = s;
           Gr[n0 * R * R + e] = (double)s;
         }
       } else {
@@ -632,7 +715,7 @@ size_t smem_bytes(const rcp_plan_s* p) {
   const size_t f = (R * (R + 1) > 1024 ? R * (R + 1) : 1024) + R;
   return d * sizeof(double) + f * sizeof(float) + 16 +
          ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * R) * sizeof(TM) + 16 +
-         (size_t)32 * 64 * sizeof(double);
+         (size_t)2 * 32 * 64 * sizeof(float2) + N * R * R * sizeof(float);
 }
 
 template <typename TM>
@@ -674,7 +757,7 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.tol = p->cfg.tol;
   a.max_iters = p->cfg.max_iters;
   a.user_init = p->user_init ? 1 : 0;
-  // R <= 32: each row-owning CTA inverts V in FP64 with all its threads (path 3)
+  // R <= 32: each row-owning CTA inverts V in double-word arithmetic (path 3)
   a.direct64 = 0;
   void* args[] = {&a};
   count_launches(1);
@@ -706,7 +789,7 @@ size_t als_smem_bytes_f32(int N, int R, const int* l) {
   const size_t f = (RR * (RR + 1) > 1024 ? RR * (RR + 1) : 1024) + RR;
   return d * sizeof(double) + f * sizeof(float) + 16 +
          ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * RR) * sizeof(float) + 16 +
-         (size_t)32 * 64 * sizeof(double);
+         (size_t)2 * 32 * 64 * sizeof(float2) + NN * RR * RR * sizeof(float);
 }
 
 cudaError_t prepare_als_batched(size_t smem) {
