@@ -43,43 +43,46 @@ constexpr int kBP = kTileJ + 1;                   // padded pitch of the B tile
 constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
 
 
-__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag) {
+// Grid barrier over nblocks CTAs on a monotonic arrival counter (zeroed before
+// the launch): barrier number e completes when the counter reaches e nblocks.
+// Thread 0 publishes its CTA's writes (ordered before it by __syncthreads) with
+// one release add and waits with acquire loads, so a single L2 round trip
+// follows the last arrival.  The wait has a clock budget; on expiry the CTA
+// raises the abort flag and returns false.  The other CTAs then run out their
+// own budgets at this barrier or the next, neither of which can complete, so
+// every CTA leaves.
+__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag, unsigned& epoch) {
   __syncthreads();
   __shared__ int ok_sh;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    epoch += 1u;
+    const unsigned target = epoch * nblocks;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int ok = 1;
-    if (arrived == nblocks) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (clock64() - t0 > kBarrierBudget) {
-          ok = 0;
-          break;
-        }
+    const long long t0 = clock64();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (clock64() - t0 > kBarrierBudget) {
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     if (!ok) atomicExch(abort_flag, 1);
-    ok_sh = ok && (*(volatile int*)abort_flag == 0);
+    ok_sh = ok;
   }
   __syncthreads();
   return ok_sh != 0;
 }
 
 // Block-wide barrier for the G CTAs of one problem (a plain __syncthreads when G == 1).
-__device__ __forceinline__ bool phase_sync(const PersArgs& a, int G) {
+__device__ __forceinline__ bool phase_sync(const PersArgs& a, int G, unsigned& epoch) {
   if (G == 1) {
     __syncthreads();
     return true;
   }
-  return grid_sync(a.bar, (unsigned)G, a.abort_flag);
+  return grid_sync(a.bar, (unsigned)G, a.abort_flag, epoch);
 }
 
 // KACC: MTTKRP outputs (l_n x R) per thread, at most KACC * kThreads.
@@ -237,6 +240,7 @@ __device__ void als_body(const PersArgs& a, int g) {
   };
 
   double rho_prev = 0.0, nb2 = 0.0;
+  unsigned epoch = 0;  // grid barriers passed (thread 0)
   int done = 0;
   bool ok = true;
   // partial writers of mode 1 (the |B|^2 partials are written in its first phase A)
@@ -327,7 +331,7 @@ __device__ void als_body(const PersArgs& a, int g) {
         }
       }
       if (gw0 > 0 && g < ln) prepare_solve(n0);
-      if (!phase_sync(a, G)) { ok = false; break; }
+      if (!phase_sync(a, G, epoch)) { ok = false; break; }
 
       // ---- phase B: rows owned by this CTA (rows i = g, g + G, ...)
       if (g < ln) {
@@ -576,15 +580,19 @@ __device__ void als_body(const PersArgs& a, int g) {
         }
         }
       }
-      if (!phase_sync(a, G)) { ok = false; break; }
-      // every CTA reads the status once, after the barrier, so all leave together
-      if (tid == 0) red[3] = (double)*(volatile int*)&st->status;
+      if (!phase_sync(a, G, epoch)) { ok = false; break; }
+      // every CTA reads the status once, after the barrier, so all leave
+      // together (the load overlaps the load of the new rows)
+      {
+        int stv = 0;
+        if (tid == 0) stv = *(volatile int*)&st->status;
+        for (int e = tid; e < nout; e += kThreads) Xs[e] = a.rows[e];
+        if (tid == 0) red[3] = (double)stv;
+      }
       __syncthreads();
       if (red[3] != 0.0) { ok = false; break; }
 
       // ---- phase C (every CTA): norms, normalisation, Gram
-      for (int e = tid; e < nout; e += kThreads) Xs[e] = a.rows[e];
-      __syncthreads();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {  // column norms: warp w sums rows w, w + 8, ...
         const int r = lane + 32 * h;
