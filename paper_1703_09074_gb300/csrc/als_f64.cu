@@ -226,18 +226,18 @@ __global__ void k_als_update(AlsArgs a) {
   }
 }
 
-// A_n[i, r] = sum_c Q_n[i, c] Atilde_n[c, r] (unnormalised), one thread per row.
+// A_n[i, r] = sum_c Q_n[i, c] Atilde_n[c, r] (unnormalised), one thread per
+// output: each is an l-term FP64 chain, and I R of them spread over the GPU
+// (consecutive threads take consecutive rows i, so the loads of Q coalesce).
 __global__ void k_backproject(const double* __restrict__ Q, int64_t I, int l,
                               const double* __restrict__ At, int R, double* __restrict__ A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= I) return;
-  double q[kMaxL];
-  for (int c = 0; c < l; ++c) q[c] = Q[i + I * c];
-  for (int r = 0; r < R; ++r) {
-    double acc = 0.0;
-    for (int c = 0; c < l; ++c) acc = fma(q[c], At[c + l * r], acc);
-    A[i + I * r] = acc;
-  }
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= I * R) return;
+  const int64_t r = e / I, i = e - r * I;
+  const double* a = At + (int64_t)l * r;
+  double acc = 0.0;
+  for (int c = 0; c < l; ++c) acc = fma(Q[i + I * c], a[c], acc);
+  A[e] = acc;
 }
 
 struct ProjArgs {
@@ -359,8 +359,8 @@ cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lamb
     pa.A[n] = A_dev[n];
     const int64_t I = p->dims[n];
     count_launches(1);
-    k_backproject<<<(unsigned)((I + 63) / 64), 64, 0, s>>>(p->Q[n], I, p->l[n], p->At[n], p->R,
-                                                           A_dev[n]);
+    k_backproject<<<(unsigned)((I * p->R + 255) / 256), 256, 0, s>>>(p->Q[n], I, p->l[n],
+                                                                      p->At[n], p->R, A_dev[n]);
     if (I * p->R > maxe) maxe = I * p->R;
   }
   pa.nu = p->tmp;

@@ -62,13 +62,32 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
   if (threadIdx.x == 0) Gp[p] = s;
 }
 
-// Cholesky G = R^T R of a packed SPD matrix by one CTA, then R^{-1}.
-// Right-looking, one barrier per step: at step k every thread reads the same
-// pivot d = S[k][k] of the Schur complement S (upper triangle), so the pivot
-// test is uniform; the trailing update uses S[k][i] S[k][j] / d (the unscaled
-// row), while row k of R goes to the strictly lower triangle (R[k][j] at
-// S[j][k]) and the reciprocal of its diagonal to rdiag, which no update touches.  R^{-1} then
-// overwrites the upper triangle by back substitution, one column per thread.
+// 1 / sqrt(d) for a positive normal d: the FP32 hardware estimate and two
+// Newton steps y <- y + y (1 - d y^2) / 2 in FP64 (each doubles the correct
+// bits; the result is within a few ulp).  Outside the FP32 exponent range the
+// FP64 library square root is used instead.
+__device__ __forceinline__ double rsqrt64(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf(__double2float_rn(d));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double t = d * y;
+    y = fma(0.5 * y, fma(-t, y, 1.0), y);
+  }
+  return y;
+}
+
+// Cholesky G = R^T R of a packed SPD matrix by one CTA, together with
+// R^{-1}, in FP64.  Elimination on [G | I] by rows: step k scales row k by
+// 1 / sqrt(pivot) (giving row k of R, and of R^{-T} on the right) and
+// subtracts R[k][i] times it from every later row i, so the left part ends as
+// R and the right part as R^{-T} (the row operations E satisfy E G = R, hence
+// E = R^{-T}).  S holds the Schur complement in its upper triangle and R^{-T}
+// in its strict lower triangle (diagonal in tdiag).
+// FP64 issues at one warp instruction per 64 cycles per sub-partition, so the
+// pivot chain (update of row k+1, its reciprocal square root, the scaling)
+// runs on warp 0 one step ahead, while warps 1-3 and 5-7 (warp 4 shares warp
+// 0's sub-partition) update rows k+2.. of step k; one barrier per step.
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
 // after32 != 0: runs only when the FP32 attempt of the same round failed.
@@ -76,11 +95,13 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
                                               double* __restrict__ Rinv, DevState* st,
                                               double shift_rows, int round, int als_mode,
                                               int after32) {
-  __shared__ double S[kMaxL][kMaxL + 1];   // Schur complement / R^{-1} (upper), R (lower)
-  __shared__ double rdiag[kMaxL];
+  __shared__ double S[kMaxL][kMaxL + 1];
+  __shared__ double tdiag[kMaxL];
+  __shared__ double rowb[2][kMaxL];  // row k of R (double-buffered)
+  __shared__ double tb[2][kMaxL];    // row k of R^{-T}
   __shared__ double red[32];
-  __shared__ int bad_sh;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int bad_sh, fail_sh;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   if (after32 && !st->chol32_fail) return;
   if (round == 2 && !st->extra_round) return;
   if (round == 0 && tid == 0) st->extra_round = 0;
@@ -107,6 +128,9 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
   }
   const double u = 1.1102230246251565e-16;
   const double shift = 11.0 * (shift_rows * l + (double)l * (l + 1)) * u * tr;
+  // update threads: warps other than 0 and 4, as a flat index over rows k+2.. x columns
+  const int ut = warp == 0 || warp == 4 ? -1 : (warp < 4 ? tid - 32 : tid - 64);
+  const int nut = nt - 64;
 
   bool ok = false;
   for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
@@ -114,35 +138,79 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
       int c1 = 0, rem = p;
       while (rem >= l - c1) { rem -= l - c1; ++c1; }
       S[c1][c1 + rem] = Gp[p] + ((attempt == 1 && rem == 0) ? shift : 0.0);
+      if (rem > 0) S[c1 + rem][c1] = 0.0;  // R^{-T} starts as I (diagonal in tdiag)
     }
+    if (tid == 0) fail_sh = 0;
     __syncthreads();
     const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
-    ok = true;
-    for (int k = 0; k < l; ++k) {
-      const double d = S[k][k];
-      if (!(d > floor_) || !(d > 0.0)) {  // uniform: every thread read the same d
-        ok = false;
-        break;
+    // row 0
+    if (warp == 0) {
+      const double d = S[0][0];
+      const bool good = d > floor_ && d > 0.0;
+      const double rs = good ? rsqrt64(d) : 0.0;
+      for (int j = lane; j < l; j += 32) rowb[0][j] = S[0][j] * rs;
+      if (lane == 0) {
+        tb[0][0] = rs;
+        tdiag[0] = rs;
+        if (!good) fail_sh = 1;
       }
-      const double rs = rsqrt(d), dinv = rs * rs;
-      const int m = l - k;  // row k of R: columns k..l-1
-      for (int j = k + tid; j < l; j += nt) {
-        if (j == k) rdiag[k] = rs;  // the reciprocal of R[k][k], for the back substitution
-        else S[j][k] = S[k][j] * rs;
-      }
-      const int mm = m - 1;
-      for (int q = tid; q < mm * mm; q += nt) {
-        const int i = k + 1 + q / mm, j = k + 1 + q % mm;
-        if (j >= i) S[i][j] = fma(-S[k][i] * dinv, S[k][j], S[i][j]);
-      }
-      __syncthreads();
     }
     __syncthreads();
+    ok = fail_sh == 0;
+    for (int k = 0; ok && k + 1 < l; ++k) {
+      const double* rk = rowb[k & 1];
+      const double* tk = tb[k & 1];
+      if (warp == 0) {
+        // row k+1: its update by row k, the pivot, the scaling
+        const int i = k + 1;
+        const double f = rk[i];
+        double v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = lane + 32 * h;
+          v[h] = 0.0;
+          if (j < l) v[h] = fma(-f, j >= i ? rk[j] : (j < i ? tk[j] : 0.0), S[i][j]);
+        }
+        const double d = __shfl_sync(0xffffffffu, (i >> 5) ? v[1] : v[0], i & 31);
+        const bool good = d > floor_ && d > 0.0;
+        const double rs = good ? rsqrt64(d) : 0.0;
+        double* rn = rowb[(k + 1) & 1];
+        double* tn = tb[(k + 1) & 1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = lane + 32 * h;
+          if (j < l) {
+            const double w = v[h] * rs;
+            if (j > i) rn[j] = w;
+            else if (j < i) {
+              tn[j] = w;
+              S[i][j] = w;
+            }
+          }
+        }
+        if (lane == 0) {
+          tn[i] = rs;
+          tdiag[i] = rs;
+          if (!good) fail_sh = 1;
+        }
+      } else if (ut >= 0) {
+        // rows k+2..: S[i][j] -= R[k][i] R[k][j] (j >= i), T[i][j] -= R[k][i] T[k][j] (j <= k)
+        const int rows = l - k - 2;
+        for (int q = ut; q < rows * l; q += nut) {
+          const int i = k + 2 + q / l, j = q - (q / l) * l;
+          if (j >= i) S[i][j] = fma(-rk[i], rk[j], S[i][j]);
+          else if (j <= k) S[i][j] = fma(-rk[i], tk[j], S[i][j]);
+        }
+      }
+      __syncthreads();
+      ok = fail_sh == 0;
+    }
     if (!ok && attempt == 0 && shift_rows > 0.0) {
       if (tid == 0) {
         atomicOr(&st->info, als_mode ? RCP_INFO_ALS_REGULARISED : RCP_INFO_SHIFTED_QR);
         if (round == 0) st->extra_round = 1;
       }
+      __syncthreads();
       continue;
     }
     if (!ok) {
@@ -150,19 +218,10 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
       return;
     }
   }
-  // R^{-1} = X: thread c solves R x = e_c from the bottom; X[i][c] overwrites
-  // S[i][c] (i <= c), R[i][k] is read from S[k][i] (k > i)
-  for (int c = tid; c < l; c += nt) {
-    for (int i = c; i >= 0; --i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) v = fma(-S[k][i], S[k][c], v);
-      S[i][c] = v * rdiag[i];
-    }
-  }
-  __syncthreads();
+  // R^{-1} = (R^{-T})^T: (R^{-1})[i][c] = T[c][i], i <= c
   for (int q = tid; q < l * l; q += nt) {
     const int i = q % l, c = q / l;
-    Rinv[q] = (i <= c) ? S[i][c] : 0.0;
+    Rinv[q] = i < c ? S[c][i] : (i == c ? tdiag[c] : 0.0);
   }
 }
 
