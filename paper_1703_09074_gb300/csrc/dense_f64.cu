@@ -67,7 +67,9 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
 // bits; the result is within a few ulp).  Outside the FP32 exponent range the
 // FP64 library square root is used instead.
 __device__ __forceinline__ double rsqrt64(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  // range test on the exponent bits (integer compares keep it off the FP64 pipe)
+  const int ex = (__double2hiint(d) >> 20) & 0x7ff;
+  if (ex < 1023 - 99 || ex > 1023 + 99) return 1.0 / sqrt(d);
   double y = (double)rsqrtf(__double2float_rn(d));
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -77,17 +79,116 @@ __device__ __forceinline__ double rsqrt64(double d) {
   return y;
 }
 
-// Cholesky G = R^T R of a packed SPD matrix by one CTA, together with
-// R^{-1}, in FP64.  Elimination on [G | I] by rows: step k scales row k by
-// 1 / sqrt(pivot) (giving row k of R, and of R^{-T} on the right) and
-// subtracts R[k][i] times it from every later row i, so the left part ends as
-// R and the right part as R^{-T} (the row operations E satisfy E G = R, hence
-// E = R^{-T}).  S holds the Schur complement in its upper triangle and R^{-T}
-// in its strict lower triangle (diagonal in tdiag).
-// FP64 issues at one warp instruction per 64 cycles per sub-partition, so the
-// pivot chain (update of row k+1, its reciprocal square root, the scaling)
-// runs on warp 0 one step ahead, while warps 1-3 and 5-7 (warp 4 shares warp
-// 0's sub-partition) update rows k+2.. of step k; one barrier per step.
+__device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
+__device__ __forceinline__ double rsqrt_t(double d) { return rsqrt64(d); }
+
+// d > floor_ >= 0 and finite, as integer compares (positive IEEE numbers order
+// like their bit patterns), which keeps the test off the FP64 pipe
+__device__ __forceinline__ bool pivot_ok(double d, double floor_) {
+  const long long db = __double_as_longlong(d);
+  return db > __double_as_longlong(floor_) && db > 0 && db < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool pivot_ok(float d, float floor_) {
+  const int db = __float_as_int(d);
+  return db > __float_as_int(floor_) && db > 0 && db < 0x7f800000;
+}
+
+// Cholesky G = R^T R of the SPD matrix in the upper triangle of S (l x l, with
+// the strict lower triangle zero) by one CTA, together with R^{-1}.
+// Elimination on [G | I] by rows: step k scales row k by 1 / sqrt(pivot)
+// (giving row k of R, and of R^{-T} on the right) and subtracts R[k][i] times
+// it from every later row i, so the left part ends as R and the right part as
+// R^{-T} (the row operations E satisfy E G = R, hence E = R^{-T}).  S keeps
+// the Schur complement in its upper triangle and receives R^{-T} in its strict
+// lower triangle (diagonal in tdiag).  The pivot chain (update of row k+1, its
+// reciprocal square root, the scaling) runs on warp 0 one step ahead, while
+// warps 1-3 and 5-7 (warp 4 shares warp 0's sub-partition, whose FP64 unit
+// issues one warp instruction per 64 cycles) update rows k+2.. of step k: one
+// barrier per step.  Returns false, uniformly, when a pivot is not above
+// floor_ (>= 0); 256 threads.
+template <typename T>
+__device__ bool chol_elim(T (*S)[kMaxL + 1], T* tdiag, T (*rowb)[kMaxL], T (*tb)[kMaxL], int l,
+                          T floor_, int* fail_sh) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ut = warp == 0 || warp == 4 ? -1 : (warp < 4 ? tid - 32 : tid - 64);
+  constexpr int nut = 192;
+  if (tid == 0) *fail_sh = 0;
+  __syncthreads();
+  if (warp == 0) {
+    const T d = S[0][0];
+    const bool good = pivot_ok(d, floor_);
+    const T rs = good ? rsqrt_t(d) : T(0);
+    for (int j = lane; j < l; j += 32) rowb[0][j] = S[0][j] * rs;
+    if (lane == 0) {
+      tb[0][0] = rs;
+      tdiag[0] = rs;
+      if (!good) *fail_sh = 1;
+    }
+  }
+  __syncthreads();
+  bool ok = *fail_sh == 0;
+  for (int k = 0; ok && k + 1 < l; ++k) {
+    const T* rk = rowb[k & 1];
+    const T* tk = tb[k & 1];
+    if (warp == 0) {
+      // row k+1: its update by row k, the pivot, the scaling
+      const int i = k + 1;
+      const T f = rk[i];
+      T v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        v[h] = T(0);
+        if (j < l) v[h] = fma(-f, j >= i ? rk[j] : tk[j], S[i][j]);
+      }
+      const T d = __shfl_sync(0xffffffffu, (i >> 5) ? v[1] : v[0], i & 31);
+      const bool good = pivot_ok(d, floor_);
+      const T rs = good ? rsqrt_t(d) : T(0);
+      T* rn = rowb[(k + 1) & 1];
+      T* tn = tb[(k + 1) & 1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j < l) {
+          const T w = v[h] * rs;
+          if (j > i) {
+            rn[j] = w;
+          } else if (j < i) {
+            tn[j] = w;
+            S[i][j] = w;
+          }
+        }
+      }
+      if (lane == 0) {
+        tn[i] = rs;
+        tdiag[i] = rs;
+        if (!good) *fail_sh = 1;
+      }
+    } else if (ut >= 0) {
+      // rows k+2..: S[i][j] -= R[k][i] R[k][j] (j >= i), T[i][j] -= R[k][i] T[k][j] (j <= k)
+      const int rows = l - k - 2;
+      for (int q = ut; q < rows * l; q += nut) {
+        const int i = k + 2 + q / l, j = q - (q / l) * l;
+        if (j >= i) S[i][j] = fma(-rk[i], rk[j], S[i][j]);
+        else if (j <= k) S[i][j] = fma(-rk[i], tk[j], S[i][j]);
+      }
+    }
+    __syncthreads();
+    ok = *fail_sh == 0;
+  }
+  return ok;
+}
+
+// R^{-1} = (R^{-T})^T to Rinv (l x l column-major): (R^{-1})[i][c] = T[c][i], i <= c
+template <typename T>
+__device__ void write_rinv(const T (*S)[kMaxL + 1], const T* tdiag, int l, double* Rinv) {
+  for (int q = threadIdx.x; q < l * l; q += blockDim.x) {
+    const int i = q % l, c = q / l;
+    Rinv[q] = i < c ? (double)S[c][i] : (i == c ? (double)tdiag[c] : 0.0);
+  }
+}
+
+// The FP64 factorisation of one CholeskyQR round (chol_elim in FP64).
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
 // after32 != 0: runs only when the FP32 attempt of the same round failed.
@@ -97,11 +198,11 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
                                               int after32) {
   __shared__ double S[kMaxL][kMaxL + 1];
   __shared__ double tdiag[kMaxL];
-  __shared__ double rowb[2][kMaxL];  // row k of R (double-buffered)
-  __shared__ double tb[2][kMaxL];    // row k of R^{-T}
+  __shared__ double rowb[2][kMaxL];
+  __shared__ double tb[2][kMaxL];
   __shared__ double red[32];
   __shared__ int bad_sh, fail_sh;
-  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (after32 && !st->chol32_fail) return;
   if (round == 2 && !st->extra_round) return;
   if (round == 0 && tid == 0) st->extra_round = 0;
@@ -128,9 +229,6 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
   }
   const double u = 1.1102230246251565e-16;
   const double shift = 11.0 * (shift_rows * l + (double)l * (l + 1)) * u * tr;
-  // update threads: warps other than 0 and 4, as a flat index over rows k+2.. x columns
-  const int ut = warp == 0 || warp == 4 ? -1 : (warp < 4 ? tid - 32 : tid - 64);
-  const int nut = nt - 64;
 
   bool ok = false;
   for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
@@ -138,73 +236,10 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
       int c1 = 0, rem = p;
       while (rem >= l - c1) { rem -= l - c1; ++c1; }
       S[c1][c1 + rem] = Gp[p] + ((attempt == 1 && rem == 0) ? shift : 0.0);
-      if (rem > 0) S[c1 + rem][c1] = 0.0;  // R^{-T} starts as I (diagonal in tdiag)
+      if (rem > 0) S[c1 + rem][c1] = 0.0;
     }
-    if (tid == 0) fail_sh = 0;
-    __syncthreads();
     const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
-    // row 0
-    if (warp == 0) {
-      const double d = S[0][0];
-      const bool good = d > floor_ && d > 0.0;
-      const double rs = good ? rsqrt64(d) : 0.0;
-      for (int j = lane; j < l; j += 32) rowb[0][j] = S[0][j] * rs;
-      if (lane == 0) {
-        tb[0][0] = rs;
-        tdiag[0] = rs;
-        if (!good) fail_sh = 1;
-      }
-    }
-    __syncthreads();
-    ok = fail_sh == 0;
-    for (int k = 0; ok && k + 1 < l; ++k) {
-      const double* rk = rowb[k & 1];
-      const double* tk = tb[k & 1];
-      if (warp == 0) {
-        // row k+1: its update by row k, the pivot, the scaling
-        const int i = k + 1;
-        const double f = rk[i];
-        double v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = lane + 32 * h;
-          v[h] = 0.0;
-          if (j < l) v[h] = fma(-f, j >= i ? rk[j] : (j < i ? tk[j] : 0.0), S[i][j]);
-        }
-        const double d = __shfl_sync(0xffffffffu, (i >> 5) ? v[1] : v[0], i & 31);
-        const bool good = d > floor_ && d > 0.0;
-        const double rs = good ? rsqrt64(d) : 0.0;
-        double* rn = rowb[(k + 1) & 1];
-        double* tn = tb[(k + 1) & 1];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = lane + 32 * h;
-          if (j < l) {
-            const double w = v[h] * rs;
-            if (j > i) rn[j] = w;
-            else if (j < i) {
-              tn[j] = w;
-              S[i][j] = w;
-            }
-          }
-        }
-        if (lane == 0) {
-          tn[i] = rs;
-          tdiag[i] = rs;
-          if (!good) fail_sh = 1;
-        }
-      } else if (ut >= 0) {
-        // rows k+2..: S[i][j] -= R[k][i] R[k][j] (j >= i), T[i][j] -= R[k][i] T[k][j] (j <= k)
-        const int rows = l - k - 2;
-        for (int q = ut; q < rows * l; q += nut) {
-          const int i = k + 2 + q / l, j = q - (q / l) * l;
-          if (j >= i) S[i][j] = fma(-rk[i], rk[j], S[i][j]);
-          else if (j <= k) S[i][j] = fma(-rk[i], tk[j], S[i][j]);
-        }
-      }
-      __syncthreads();
-      ok = fail_sh == 0;
-    }
+    ok = chol_elim<double>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
     if (!ok && attempt == 0 && shift_rows > 0.0) {
       if (tid == 0) {
         atomicOr(&st->info, als_mode ? RCP_INFO_ALS_REGULARISED : RCP_INFO_SHIFTED_QR);
@@ -218,28 +253,25 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
       return;
     }
   }
-  // R^{-1} = (R^{-T})^T: (R^{-1})[i][c] = T[c][i], i <= c
-  for (int q = tid; q < l * l; q += nt) {
-    const int i = q % l, c = q / l;
-    Rinv[q] = i < c ? S[c][i] : (i == c ? tdiag[c] : 0.0);
-  }
+  write_rinv<double>(S, tdiag, l, Rinv);
 }
 
 // The same factorisation in FP32 for the rounds that tolerate it: the
 // normalisations inside the power iterations (any well-conditioned basis of
 // the span serves) and the first round of each final CholeskyQR2 (whose second
 // round, in FP64, restores orthonormality to FP64 rounding; Q is the unique
-// qr+ factor whatever R the first round used).  FP32 steps are short where
-// FP64 steps are chains of slow operations.  No shift: a pivot at or below
+// qr+ factor whatever R the first round used).  No shift: a pivot at or below
 // 64 l u_32 trace(G), or a non-finite entry, sets chol32_fail and the FP64
 // kernel that follows redoes the round (with its shifted fallback).
 __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, int l,
                                                 double* __restrict__ Rinv, DevState* st,
                                                 int round) {
-  __shared__ float S[kMaxL][kMaxL + 1];   // Schur complement / R^{-1} (upper), R (lower)
-  __shared__ float rdiag[kMaxL];
+  __shared__ float S[kMaxL][kMaxL + 1];
+  __shared__ float tdiag[kMaxL];
+  __shared__ float rowb[2][kMaxL];
+  __shared__ float tb[2][kMaxL];
   __shared__ double red[32];
-  __shared__ int bad_sh;
+  __shared__ int bad_sh, fail_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (round == 0 && tid == 0) st->extra_round = 0;
   const int np = l * (l + 1) / 2;
@@ -253,46 +285,18 @@ __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, i
     if (!isfinite(g)) bad_sh = 1;
     if (rem == 0) tr += g;
     S[c1][c1 + rem] = (float)g;
+    if (rem > 0) S[c1 + rem][c1] = 0.0f;
   }
   tr = block_sum(tr, red);
   if (tid == 0) red[31] = tr;
   __syncthreads();
   const float floor_ = 64.0f * (float)l * 5.9604645e-08f * (float)red[31];
-  bool ok = !bad_sh;
-  for (int k = 0; k < l && ok; ++k) {
-    const float d = S[k][k];
-    if (!(d > floor_)) {  // uniform: every thread read the same d
-      ok = false;
-      break;
-    }
-    const float rs = rsqrtf(d), dinv = rs * rs;
-    for (int j = k + tid; j < l; j += nt) {
-      if (j == k) rdiag[k] = rs;
-      else S[j][k] = S[k][j] * rs;
-    }
-    const int mm = l - k - 1;
-    for (int q = tid; q < mm * mm; q += nt) {
-      const int i = k + 1 + q / mm, j = k + 1 + q % mm;
-      if (j >= i) S[i][j] = fmaf(-S[k][i] * dinv, S[k][j], S[i][j]);
-    }
-    __syncthreads();
-  }
+  bool ok = !bad_sh && chol_elim<float>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
   if (!ok) {
     if (tid == 0) st->chol32_fail = 1;
     return;
   }
-  for (int c = tid; c < l; c += nt) {
-    for (int i = c; i >= 0; --i) {
-      float v = (i == c) ? 1.0f : 0.0f;
-      for (int k = i + 1; k <= c; ++k) v = fmaf(-S[k][i], S[k][c], v);
-      S[i][c] = v * rdiag[i];
-    }
-  }
-  __syncthreads();
-  for (int q = tid; q < l * l; q += nt) {
-    const int i = q % l, c = q / l;
-    Rinv[q] = (i <= c) ? (double)S[i][c] : 0.0;
-  }
+  write_rinv<float>(S, tdiag, l, Rinv);
   if (tid == 0) st->chol32_fail = 0;
 }
 

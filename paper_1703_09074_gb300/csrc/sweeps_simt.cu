@@ -333,7 +333,117 @@ cudaError_t col_sweep_any(const TIn* T, ModeView v, int l, const double* Q, TA* 
   }
 }
 
+// Column sweep of the precision form for the later modes, whose tensors are
+// small: W[a + L (c + l b)] = sum_i T[a + L (i + I b)] Q[i][c] (Q in FP64,
+// staged once per CTA as FP32).  A thread owns one column j = (a, b) of a block
+// of 64 and one block of 8 outputs c, and S threads split the rows i of each
+// (column, output block) for small J; their partial sums meet in shared
+// memory in a fixed order.  Thread tid: column jj = tid % 64, output block
+// cb = (tid / 64) % NCB, row split s = tid / (64 NCB); a warp is 32
+// consecutive columns of one (cb, s), so its loads of T coalesce and its
+// reads of Q are broadcasts.
+template <int NCB>
+__global__ void __launch_bounds__(1024)
+k_col_sweep_cb(const float* __restrict__ T, ModeView v, int l, const double* __restrict__ Q,
+               float* __restrict__ W, int S) {
+  extern __shared__ float4 smq[];
+  constexpr int P = NCB * 8;  // padded row of Q in shared memory
+  float* Qs = (float*)smq;
+  float* red = Qs + (size_t)v.I * P;  // (S - 1) x 64 x P partial sums
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t e = tid; e < v.I * P; e += nt) {
+    const int64_t i = e / P;
+    const int c = (int)(e - i * P);
+    Qs[e] = c < l ? (float)Q[i + v.I * c] : 0.0f;
+  }
+  __syncthreads();
+  const int jj = tid & 63, cb = (tid >> 6) % NCB, sp = (tid >> 6) / NCB;
+  const int64_t rps = (v.I + S - 1) / S;
+  const int64_t i_lo = min(v.I, sp * rps), i_hi = min(v.I, i_lo + rps);
+  for (int64_t jb = blockIdx.x; jb * 64 < v.J; jb += gridDim.x) {
+    const int64_t j = jb * 64 + jj;
+    const bool ok = j < v.J;
+    const int64_t a = ok ? j % v.L : 0, b = ok ? j / v.L : 0;
+    const float* t = T + a + v.L * v.I * b;
+    float acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+    if (ok) {
+      int64_t i = i_lo;
+      for (; i + 8 <= i_hi; i += 8) {
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = __ldg(t + v.L * (i + q));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 q0 = *(const float4*)(Qs + (i + q) * P + cb * 8);
+          const float4 q1 = *(const float4*)(Qs + (i + q) * P + cb * 8 + 4);
+          acc[0] = fmaf(x[q], q0.x, acc[0]);
+          acc[1] = fmaf(x[q], q0.y, acc[1]);
+          acc[2] = fmaf(x[q], q0.z, acc[2]);
+          acc[3] = fmaf(x[q], q0.w, acc[3]);
+          acc[4] = fmaf(x[q], q1.x, acc[4]);
+          acc[5] = fmaf(x[q], q1.y, acc[5]);
+          acc[6] = fmaf(x[q], q1.z, acc[6]);
+          acc[7] = fmaf(x[q], q1.w, acc[7]);
+        }
+      }
+      for (; i < i_hi; ++i) {
+        const float x = __ldg(t + v.L * i);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fmaf(x, Qs[i * P + cb * 8 + u], acc[u]);
+      }
+    }
+    if (S > 1) {
+      __syncthreads();
+      if (sp > 0)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) red[((sp - 1) * 64 + jj) * P + cb * 8 + u] = acc[u];
+      __syncthreads();
+      if (sp == 0)
+        for (int s2 = 1; s2 < S; ++s2)
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] += red[((s2 - 1) * 64 + jj) * P + cb * 8 + u];
+    }
+    if (ok && sp == 0) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = cb * 8 + u;
+        if (c < l) W[a + v.L * (c + (int64_t)l * b)] = acc[u];
+      }
+    }
+  }
+}
+
+template <int NCB>
+cudaError_t col_sweep_cb_typed(const float* T, ModeView v, int l, const double* Q, float* W,
+                               int nsm, cudaStream_t s) {
+  // row splits S until the threads fill the SMs (2048 each), within 1024 per CTA;
+  // at 64 registers a thread, an SM holds 1024 / (64 NCB S) CTAs of this shape
+  const int64_t nb = (v.J + 63) / 64;
+  const int smax = 1024 / (64 * NCB);
+  const int64_t per_s = nb * 64 * NCB;
+  int S = (int)((2048LL * nsm + per_s - 1) / per_s);
+  S = S < 1 ? 1 : (S > smax ? smax : S);
+  const int per_sm = 1024 / (64 * NCB * S) > 0 ? 1024 / (64 * NCB * S) : 1;
+  const int grid = (int)(nb < (int64_t)per_sm * nsm ? nb : (int64_t)per_sm * nsm);
+  const size_t smem = ((size_t)v.I * NCB * 8 + (size_t)(S - 1) * 64 * NCB * 8) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_col_sweep_cb<NCB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  k_col_sweep_cb<NCB><<<grid, 64 * NCB * S, smem, s>>>(T, v, l, Q, W, S);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+// True when the blocked column sweep applies: Q (I x 8 ceil(l / 8) FP32) and
+// the row-split partial sums fit in shared memory.
+bool col_sweep_cb_fits(const ModeView& v, int l) {
+  const int ncb = (l + 7) / 8;
+  return l >= 1 && ncb <= 8 && ((size_t)v.I * ncb * 8 + (size_t)7 * 64 * ncb * 8) * 4 <= 200 * 1024;
+}
 
 int sketch_splits(const ModeView& v, int nsm) {
   const int64_t nib = (v.I + 255) / 256;
@@ -479,6 +589,23 @@ cudaError_t launch_project_f64(const void* T, int in_dtype, ModeView v, int l, c
 
 cudaError_t launch_project_f32(const float* T, ModeView v, int l, const double* Q, float* W,
                                int nblocks, cudaStream_t s) {
+  if (col_sweep_cb_fits(v, l)) {
+    // nblocks counts CTAs of 256 columns; about nblocks / 4 * 4 >= SMs here
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorUnknown;
+    switch ((l + 7) / 8) {
+      case 1: return col_sweep_cb_typed<1>(T, v, l, Q, W, nsm, s);
+      case 2: return col_sweep_cb_typed<2>(T, v, l, Q, W, nsm, s);
+      case 3: return col_sweep_cb_typed<3>(T, v, l, Q, W, nsm, s);
+      case 4: return col_sweep_cb_typed<4>(T, v, l, Q, W, nsm, s);
+      case 5: return col_sweep_cb_typed<5>(T, v, l, Q, W, nsm, s);
+      case 6: return col_sweep_cb_typed<6>(T, v, l, Q, W, nsm, s);
+      case 7: return col_sweep_cb_typed<7>(T, v, l, Q, W, nsm, s);
+      default: return col_sweep_cb_typed<8>(T, v, l, Q, W, nsm, s);
+    }
+  }
   return col_sweep_any(T, v, l, Q, W, (double*)nullptr, nblocks, s);
 }
 
