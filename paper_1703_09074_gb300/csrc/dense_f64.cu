@@ -260,12 +260,17 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
 // normalisations inside the power iterations (any well-conditioned basis of
 // the span serves) and the first round of each final CholeskyQR2 (whose second
 // round, in FP64, restores orthonormality to FP64 rounding; Q is the unique
-// qr+ factor whatever R the first round used).  No shift: a pivot at or below
+// qr+ factor whatever R the first round used).  A pivot at or below
 // 64 l u_32 trace(G), or a non-finite entry, sets chol32_fail and the FP64
-// kernel that follows redoes the round (with its shifted fallback).
+// kernel that follows redoes the round (with its shifted fallback) -- except
+// for a normalisation inside the power iterations (span_only != 0), which
+// instead factors G + s I with s = 64 l u_32 trace(G): every pivot then stays
+// above FP32 rounding, Y R^{-1} spans the same space as Y, and its condition
+// number is at most about sqrt(trace(G) / s), which is all the next product
+// needs (the final CholeskyQR2 of the mode, in FP64, orthonormalises).
 __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, int l,
                                                 double* __restrict__ Rinv, DevState* st,
-                                                int round) {
+                                                int round, int span_only) {
   __shared__ float S[kMaxL][kMaxL + 1];
   __shared__ float tdiag[kMaxL];
   __shared__ float rowb[2][kMaxL];
@@ -292,6 +297,16 @@ __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, i
   __syncthreads();
   const float floor_ = 64.0f * (float)l * 5.9604645e-08f * (float)red[31];
   bool ok = !bad_sh && chol_elim<float>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
+  if (!ok && !bad_sh && span_only) {
+    __syncthreads();
+    for (int p = tid; p < np; p += nt) {
+      int c1 = 0, rem = p;
+      while (rem >= l - c1) { rem -= l - c1; ++c1; }
+      S[c1][c1 + rem] = (float)Gp[p] + (rem == 0 ? floor_ : 0.0f);
+      if (rem > 0) S[c1 + rem][c1] = 0.0f;
+    }
+    ok = chol_elim<float>(S, tdiag, rowb, tb, l, 0.0f, &fail_sh);
+  }
   if (!ok) {
     if (tid == 0) st->chol32_fail = 1;
     return;
@@ -413,7 +428,7 @@ cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv,
     if (e != cudaSuccess) return e;
     if (round == 0 && l <= kMaxL) {
       count_launches(2);
-      k_chol32<<<1, 256, 0, s>>>(Gp, l, Rinv, st, round);
+      k_chol32<<<1, 256, 0, s>>>(Gp, l, Rinv, st, round, final_qr ? 0 : 1);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, (double)I, round, 0, 1);
