@@ -165,8 +165,8 @@ __device__ void als_body(const PersArgs& a, int g) {
         const bool dw = !a.direct64 && R <= 32 && (G > 1 || lmax * R <= 1024);
         for (int e = tid; e < R * R; e += kThreads) {
           const int r = e % R, c = e / R;
-          double v = 1.0;
-          for (int m = 0; m < N; ++m)
+          double v = Gr[(n0 == 0 ? 1 : 0) * R * R + e];
+          for (int m = (n0 == 0 ? 2 : 1); m < N; ++m)
             if (m != n0) v *= Gr[m * R * R + e];
           V[r * (R + 1) + c] = v;
           if (!dw) {
@@ -605,8 +605,10 @@ __device__ void als_body(const PersArgs& a, int g) {
       for (int r = tid; r < R; r += kThreads) {
         double s = 0.0;
         for (int w = 0; w < kWarps; ++w) s += wsum[w * 64 + r];
-        nu[r] = sqrt(s);
-        wsum[kWarps * 64 - 64 + r] = nu[r] > 0.0 ? 1.0 / nu[r] : 0.0;  // last warp's row is free now
+        // the norm and its reciprocal from one reciprocal square root (a zero column stays zero)
+        const double rs = __double_as_longlong(s) > 0 ? rsqrt64(s) : 0.0;
+        nu[r] = s * rs;
+        wsum[kWarps * 64 - 64 + r] = rs;  // last warp's row is free now
       }
       __syncthreads();
       for (int e = tid; e < nout; e += kThreads) {

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "rcp_internal.cuh"
+#include "small_la.cuh"
 
 namespace rcp {
 namespace {
@@ -60,23 +61,6 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
   for (int64_t i = threadIdx.x; i < I; i += blockDim.x) acc = fma(y1[i], y2[i], acc);
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) Gp[p] = s;
-}
-
-// 1 / sqrt(d) for a positive normal d: the FP32 hardware estimate and two
-// Newton steps y <- y + y (1 - d y^2) / 2 in FP64 (each doubles the correct
-// bits; the result is within a few ulp).  Outside the FP32 exponent range the
-// FP64 library square root is used instead.
-__device__ __forceinline__ double rsqrt64(double d) {
-  // range test on the exponent bits (integer compares keep it off the FP64 pipe)
-  const int ex = (__double2hiint(d) >> 20) & 0x7ff;
-  if (ex < 1023 - 99 || ex > 1023 + 99) return 1.0 / sqrt(d);
-  double y = (double)rsqrtf(__double2float_rn(d));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double t = d * y;
-    y = fma(0.5 * y, fma(-t, y, 1.0), y);
-  }
-  return y;
 }
 
 __device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }

@@ -1,8 +1,27 @@
 // Warp-level dense linear algebra on small matrices in shared memory:
-// Cholesky factorisation, triangular solves and an FP32 Gauss-Jordan inverse.
+// Cholesky factorisation and triangular solves; and the FP64 reciprocal
+// square root of the factorisations.
 #pragma once
 
 namespace rcp {
+
+// 1 / sqrt(d) for a positive normal d: the FP32 hardware estimate and two
+// Newton steps y <- y + y (1 - d y^2) / 2 in FP64 (each doubles the correct
+// bits; the result is within a few ulp).  Outside the FP32 exponent range the
+// FP64 library square root is used instead.
+__device__ __forceinline__ double rsqrt64(double d) {
+  // range test on the exponent bits (integer compares keep it off the FP64 pipe)
+  const int ex = (__double2hiint(d) >> 20) & 0x7ff;
+  if (ex < 1023 - 99 || ex > 1023 + 99) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf(__double2float_rn(d));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double t = d * y;
+    y = fma(0.5 * y, fma(-t, y, 1.0), y);
+  }
+  return y;
+}
+
 
 // One warp factors V = U^T U in place (upper triangle, row pitch R + 1),
 // left-looking: row k of U is V[k, :] minus the dot products with the rows
