@@ -94,8 +94,11 @@ template <typename T>
 __device__ bool chol_elim(T (*S)[kMaxL + 1], T* tdiag, T (*rowb)[kMaxL], T (*tb)[kMaxL], int l,
                           T floor_, int* fail_sh) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ut = warp == 0 || warp == 4 ? -1 : (warp < 4 ? tid - 32 : tid - 64);
-  constexpr int nut = 192;
+  // update warps 1-3, 5-7 as uw = 0..5: column lane (l <= 32) or lane + 32 (uw & 1),
+  // rows k+2+r0, k+2+r0+rstep, ...
+  const int uw = warp == 0 || warp == 4 ? -1 : (warp < 4 ? warp - 1 : warp - 2);
+  const int jcol = l <= 32 ? lane : lane + 32 * (uw & 1);
+  const int r0 = l <= 32 ? uw : uw >> 1, rstep = l <= 32 ? 6 : 3;
   if (tid == 0) *fail_sh = 0;
   __syncthreads();
   if (warp == 0) {
@@ -148,11 +151,10 @@ __device__ bool chol_elim(T (*S)[kMaxL + 1], T* tdiag, T (*rowb)[kMaxL], T (*tb)
         tdiag[i] = rs;
         if (!good) *fail_sh = 1;
       }
-    } else if (ut >= 0) {
+    } else if (uw >= 0 && jcol < l) {
       // rows k+2..: S[i][j] -= R[k][i] R[k][j] (j >= i), T[i][j] -= R[k][i] T[k][j] (j <= k)
-      const int rows = l - k - 2;
-      for (int q = ut; q < rows * l; q += nut) {
-        const int i = k + 2 + q / l, j = q - (q / l) * l;
+      const int j = jcol;
+      for (int i = k + 2 + r0; i < l; i += rstep) {
         if (j >= i) S[i][j] = fma(-rk[i], rk[j], S[i][j]);
         else if (j <= k) S[i][j] = fma(-rk[i], tk[j], S[i][j]);
       }
@@ -197,12 +199,10 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
   __syncthreads();
   double tr = 0.0;
   for (int p = tid; p < np; p += nt) {
-    int c1 = 0, rem = p;
-    while (rem >= l - c1) { rem -= l - c1; ++c1; }
     const double g = Gp[p];
     if (!isfinite(g)) bad_sh = 1;
-    if (rem == 0) tr += g;
   }
+  for (int i = tid; i < l; i += nt) tr += Gp[i * l - i * (i - 1) / 2];
   tr = block_sum(tr, red);
   if (tid == 0) red[31] = tr;
   __syncthreads();
@@ -216,11 +216,10 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
 
   bool ok = false;
   for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
-    for (int p = tid; p < np; p += nt) {
-      int c1 = 0, rem = p;
-      while (rem >= l - c1) { rem -= l - c1; ++c1; }
-      S[c1][c1 + rem] = Gp[p] + ((attempt == 1 && rem == 0) ? shift : 0.0);
-      if (rem > 0) S[c1 + rem][c1] = 0.0;
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e / l, j = e - (e / l) * l;  // packed upper triangle: row i starts at i l - i (i - 1) / 2
+      if (j >= i) S[i][j] = Gp[i * l - i * (i - 1) / 2 + (j - i)] + ((attempt == 1 && j == i) ? shift : 0.0);
+      else S[i][j] = 0.0;
     }
     const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
     ok = chol_elim<double>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
@@ -263,18 +262,19 @@ __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, i
   __shared__ int bad_sh, fail_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (round == 0 && tid == 0) st->extra_round = 0;
-  const int np = l * (l + 1) / 2;
   if (tid == 0) bad_sh = 0;
   __syncthreads();
   double tr = 0.0;
-  for (int p = tid; p < np; p += nt) {
-    int c1 = 0, rem = p;
-    while (rem >= l - c1) { rem -= l - c1; ++c1; }
-    const double g = Gp[p];
-    if (!isfinite(g)) bad_sh = 1;
-    if (rem == 0) tr += g;
-    S[c1][c1 + rem] = (float)g;
-    if (rem > 0) S[c1 + rem][c1] = 0.0f;
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e / l, j = e - (e / l) * l;
+    if (j >= i) {
+      const double g = Gp[i * l - i * (i - 1) / 2 + (j - i)];
+      if (!isfinite(g)) bad_sh = 1;
+      if (j == i) tr += g;
+      S[i][j] = (float)g;
+    } else {
+      S[i][j] = 0.0f;
+    }
   }
   tr = block_sum(tr, red);
   if (tid == 0) red[31] = tr;
@@ -283,11 +283,9 @@ __global__ void __launch_bounds__(256) k_chol32(const double* __restrict__ Gp, i
   bool ok = !bad_sh && chol_elim<float>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
   if (!ok && !bad_sh && span_only) {
     __syncthreads();
-    for (int p = tid; p < np; p += nt) {
-      int c1 = 0, rem = p;
-      while (rem >= l - c1) { rem -= l - c1; ++c1; }
-      S[c1][c1 + rem] = (float)Gp[p] + (rem == 0 ? floor_ : 0.0f);
-      if (rem > 0) S[c1 + rem][c1] = 0.0f;
+    for (int e = tid; e < l * l; e += nt) {
+      const int i = e / l, j = e - (e / l) * l;
+      S[i][j] = j >= i ? (float)Gp[i * l - i * (i - 1) / 2 + (j - i)] + (j == i ? floor_ : 0.0f) : 0.0f;
     }
     ok = chol_elim<float>(S, tdiag, rowb, tb, l, 0.0f, &fail_sh);
   }
