@@ -258,43 +258,59 @@ __device__ void als_body(const PersArgs& a, int g) {
       const int gw0 = (G > 1 && G >= 2 * ln) ? ln : 0;
       const int GW = G - gw0, gi = g - gw0;
       // ---- phase A: MTTKRP partial over this CTA's column tiles
-      double acc[KACC];
+      // Each thread owns outputs o = tid + k kThreads, (i, r) = (o % ln, o / ln),
+      // stepped without divisions.  The mixed form sums its FP32 tile sums
+      // across tiles in double-word FP32 (Knuth's TwoSum), the FP64 path in FP64.
+      constexpr bool kMixed = sizeof(TM) == 4;
+      double acc[kMixed ? 1 : KACC];
+      float ahi[kMixed ? KACC : 1], alo[kMixed ? KACC : 1];
 #pragma unroll
-      for (int k = 0; k < KACC; ++k) acc[k] = 0.0;
+      for (int k = 0; k < (kMixed ? 1 : KACC); ++k) acc[k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < (kMixed ? KACC : 1); ++k) ahi[k] = alo[k] = 0.0f;
+      const int o_i0 = tid % ln, o_r0 = tid / ln;
+      const int o_qs = kThreads / ln, o_rs = kThreads - o_qs * ln;
       double nbpart = 0.0;
       // column tiles of tj <= kTileJ columns, narrow enough to keep the GW writers busy
       const int tj = max(1, min(kTileJ, (J + GW - 1) / GW));
       for (int t0 = gi * tj; gi >= 0 && t0 < J; t0 += GW * tj) {
         const int nj = min(tj, J - t0);
-        // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], coalesced along the contiguous index
-        for (int e = tid; e < ln * kTileJ; e += kThreads) {
-          int i, jj;
-          if (L == 1) { i = e % ln; jj = e / ln; }
-          else { jj = e % kTileJ; i = e / kTileJ; }
-          TM v = (TM)0;
-          if (jj < nj) {
-            const int j = t0 + jj;
-            const int b = j / L;
-            v = ((const TM*)a.B)[(int64_t)(j - b * L) + (int64_t)L * (i + (int64_t)ln * b)];
-          }
-          Bs[i * kBP + jj] = v;
+        // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], with lanes along the
+        // contiguous index (i for mode 1, the column otherwise)
+        if (L == 1) {
+          for (int jj = warp; jj < kTileJ; jj += kWarps)
+            for (int i = lane; i < ln; i += 32)
+              Bs[i * kBP + jj] = jj < nj ? ((const TM*)a.B)[i + (int64_t)ln * (t0 + jj)] : (TM)0;
+        } else {
+          const int jj = lane;
+          const int j = t0 + jj;
+          const int b = j / L;
+          const int64_t base = (int64_t)(j - b * L) + (int64_t)L * ln * b;
+          for (int i = warp; i < ln; i += kWarps)
+            Bs[i * kBP + jj] = jj < nj ? ((const TM*)a.B)[base + (int64_t)L * i] : (TM)0;
         }
-        // Khatri-Rao rows of the other factors, mode 1 fastest
-        for (int e = tid; e < kTileJ * R; e += kThreads) {
-          const int jj = e / R, r = e - jj * R;
-          TM prod = (TM)0;
-          if (jj < nj) {
-            int jr = t0 + jj;
-            prod = (TM)1;
-            for (int m = 0; m < N; ++m) {
-              if (m == n0) continue;
-              const int d = a.dims[m];
-              const int q = jr / d;
-              prod *= Fac[foff[m] + (jr - q * d) + d * r];
-              jr = q;
-            }
+        // Khatri-Rao rows of the other factors, mode 1 fastest: thread (jj, rg)
+        // forms column t0 + jj's digits once and the products for r = rg, rg + 8, ...
+        {
+          const int jj = tid >> 3, rg = tid & 7;
+          int dig[kMaxN];
+          int jr = t0 + jj;
+          for (int m = 0; m < N; ++m) {
+            if (m == n0) continue;
+            const int d = a.dims[m];
+            const int q = jr / d;
+            dig[m] = jr - q * d;
+            jr = q;
           }
-          Ks[jj * R + r] = prod;
+          for (int r = rg; r < R; r += 8) {
+            TM prod = (TM)0;
+            if (jj < nj) {
+              prod = (TM)1;
+              for (int m = 0; m < N; ++m)
+                if (m != n0) prod *= Fac[foff[m] + dig[m] + a.dims[m] * r];
+            }
+            Ks[jj * R + r] = prod;
+          }
         }
         __syncthreads();
         if (it == 1 && n0 == 0) {
@@ -303,14 +319,26 @@ __device__ void als_body(const PersArgs& a, int g) {
             nbpart = fma(v, v, nbpart);
           }
         }
+        int oi = o_i0, orr = o_r0;
 #pragma unroll
         for (int k = 0; k < KACC; ++k) {
           const int o = tid + k * kThreads;
           if (o < nout) {
-            const int i = o % ln, r = o / ln;
             TM s = (TM)0;
-            for (int jj = 0; jj < nj; ++jj) s += Bs[i * kBP + jj] * Ks[jj * R + r];
-            acc[k] += (double)s;
+            for (int jj = 0; jj < nj; ++jj) s += Bs[oi * kBP + jj] * Ks[jj * R + orr];
+            if constexpr (kMixed) {
+              const dwf t = dw_two_sum(ahi[k], (float)s);
+              ahi[k] = t.hi;
+              alo[k] += t.lo;
+            } else {
+              acc[k] += (double)s;
+            }
+          }
+          oi += o_rs;
+          orr += o_qs;
+          if (oi >= ln) {
+            oi -= ln;
+            ++orr;
           }
         }
         __syncthreads();
@@ -318,7 +346,10 @@ __device__ void als_body(const PersArgs& a, int g) {
 #pragma unroll
       for (int k = 0; k < KACC; ++k) {
         const int o = tid + k * kThreads;
-        if (o < nout && gi >= 0) a.part[(int64_t)gi * nout + o] = acc[k];
+        if (o < nout && gi >= 0) {
+          if constexpr (kMixed) a.part[(int64_t)gi * nout + o] = (double)ahi[k] + (double)alo[k];
+          else a.part[(int64_t)gi * nout + o] = acc[k];
+        }
       }
       if (it == 1 && n0 == 0 && gi >= 0) {
         for (int o = 16; o > 0; o >>= 1) nbpart += __shfl_down_sync(0xffffffffu, nbpart, o);
