@@ -730,9 +730,10 @@ __device__ void als_body(const PersArgs& a, int g) {
   if (!ok && g == 0 && tid == 0 && !*(volatile int*)&st->status) set_status(st, RCP_ETIMEOUT);
 }
 
-template <typename TM>
+// KACC: MTTKRP outputs per thread (8 covers l_max R <= 2048 with fewer registers)
+template <typename TM, int KACC>
 __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
-  als_body<TM, 16>(a, blockIdx.x);
+  als_body<TM, KACC>(a, blockIdx.x);
 }
 
 // Batched form: CTA b runs the whole ALS of problem b alone (G = 1).
@@ -762,11 +763,15 @@ size_t smem_bytes(const rcp_plan_s* p) {
 template <typename TM>
 cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   const size_t smem = smem_bytes<TM>(p);
-  cudaError_t e = cudaFuncSetAttribute(k_als_persistent<TM>,
+  int lmax0 = 1;
+  for (int m = 0; m < p->N; ++m) lmax0 = lmax0 > p->l[m] ? lmax0 : p->l[m];
+  const bool small = (int64_t)lmax0 * p->R <= 8 * kThreads;
+  const void* kern = small ? (const void*)k_als_persistent<TM, 8> : (const void*)k_als_persistent<TM, 16>;
+  cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_als_persistent<TM>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   PersArgs a{};
@@ -802,7 +807,7 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.direct64 = 0;
   void* args[] = {&a};
   count_launches(1);
-  return cudaLaunchCooperativeKernel((const void*)k_als_persistent<TM>, dim3(a.G), dim3(kThreads),
+  return cudaLaunchCooperativeKernel(kern, dim3(a.G), dim3(kThreads),
                                      args, smem, s);
 }
 
