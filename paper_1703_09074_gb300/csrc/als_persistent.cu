@@ -268,8 +268,17 @@ __device__ void als_body(const PersArgs& a, int g) {
       for (int k = 0; k < (kMixed ? 1 : KACC); ++k) acc[k] = 0.0;
 #pragma unroll
       for (int k = 0; k < (kMixed ? KACC : 1); ++k) ahi[k] = alo[k] = 0.0f;
-      const int o_i0 = tid % ln, o_r0 = tid / ln;
-      const int o_qs = kThreads / ln, o_rs = kThreads - o_qs * ln;
+      // register blocks of kBI rows x kBR columns of the l_n x R output: block
+      // q = tid + kThreads bb (bb < kKB) covers rows ig + nig u and columns rg + nrg v
+      constexpr int kBI = 2, kBR = KACC >= 8 ? 4 : 2, kKB = KACC / (kBI * kBR);
+      const int nig = (ln + kBI - 1) / kBI, nrg = (R + kBR - 1) / kBR;
+      int b_ig[kKB], b_rg[kKB];
+#pragma unroll
+      for (int bb = 0; bb < kKB; ++bb) {
+        const int q = tid + kThreads * bb;
+        b_rg[bb] = q / nig;
+        b_ig[bb] = q - b_rg[bb] * nig;
+      }
       double nbpart = 0.0;
       // column tiles of tj <= kTileJ columns, narrow enough to keep the GW writers busy
       const int tj = max(1, min(kTileJ, (J + GW - 1) / GW));
@@ -319,38 +328,65 @@ __device__ void als_body(const PersArgs& a, int g) {
             nbpart = fma(v, v, nbpart);
           }
         }
-        int oi = o_i0, orr = o_r0;
 #pragma unroll
-        for (int k = 0; k < KACC; ++k) {
-          const int o = tid + k * kThreads;
-          if (o < nout) {
-            TM s = (TM)0;
-            for (int jj = 0; jj < nj; ++jj) s += Bs[oi * kBP + jj] * Ks[jj * R + orr];
-            if constexpr (kMixed) {
-              const dwf t = dw_two_sum(ahi[k], (float)s);
-              ahi[k] = t.hi;
-              alo[k] += t.lo;
-            } else {
-              acc[k] += (double)s;
+        for (int bb = 0; bb < kKB; ++bb) {
+          if (b_rg[bb] < nrg) {
+            // rows and columns past the edge read row / column 0 and are not written
+            int ib[kBI], rb[kBR];
+#pragma unroll
+            for (int u = 0; u < kBI; ++u) {
+              const int i = b_ig[bb] + nig * u;
+              ib[u] = (i < ln ? i : 0) * kBP;
             }
-          }
-          oi += o_rs;
-          orr += o_qs;
-          if (oi >= ln) {
-            oi -= ln;
-            ++orr;
+#pragma unroll
+            for (int v = 0; v < kBR; ++v) {
+              const int r = b_rg[bb] + nrg * v;
+              rb[v] = r < R ? r : 0;
+            }
+            TM sacc[kBI * kBR];
+#pragma unroll
+            for (int q = 0; q < kBI * kBR; ++q) sacc[q] = (TM)0;
+            for (int jj = 0; jj < nj; ++jj) {
+              TM x[kBI], kr[kBR];
+#pragma unroll
+              for (int u = 0; u < kBI; ++u) x[u] = Bs[ib[u] + jj];
+#pragma unroll
+              for (int v = 0; v < kBR; ++v) kr[v] = Ks[jj * R + rb[v]];
+#pragma unroll
+              for (int u = 0; u < kBI; ++u)
+#pragma unroll
+                for (int v = 0; v < kBR; ++v) sacc[u * kBR + v] = fma(x[u], kr[v], sacc[u * kBR + v]);
+            }
+#pragma unroll
+            for (int q = 0; q < kBI * kBR; ++q) {
+              const int k = bb * kBI * kBR + q;
+              if constexpr (kMixed) {
+                const dwf t = dw_two_sum(ahi[k], (float)sacc[q]);
+                ahi[k] = t.hi;
+                alo[k] += t.lo;
+              } else {
+                acc[k] += (double)sacc[q];
+              }
+            }
           }
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int k = 0; k < KACC; ++k) {
-        const int o = tid + k * kThreads;
-        if (o < nout && gi >= 0) {
-          if constexpr (kMixed) a.part[(int64_t)gi * nout + o] = (double)ahi[k] + (double)alo[k];
-          else a.part[(int64_t)gi * nout + o] = acc[k];
-        }
-      }
+      for (int bb = 0; bb < kKB; ++bb)
+#pragma unroll
+        for (int u = 0; u < kBI; ++u)
+#pragma unroll
+          for (int v = 0; v < kBR; ++v) {
+            const int i = b_ig[bb] + nig * u, r = b_rg[bb] + nrg * v;
+            if (gi >= 0 && b_rg[bb] < nrg && i < ln && r < R) {
+              const int k = bb * kBI * kBR + u * kBR + v;
+              double val;
+              if constexpr (kMixed) val = (double)ahi[k] + (double)alo[k];
+              else val = acc[k];
+              a.part[(int64_t)gi * nout + i + ln * r] = val;
+            }
+          }
       if (it == 1 && n0 == 0 && gi >= 0) {
         for (int o = 16; o > 0; o >>= 1) nbpart += __shfl_down_sync(0xffffffffu, nbpart, o);
         if (lane == 0) red[8 + warp] = nbpart;
@@ -730,15 +766,16 @@ __device__ void als_body(const PersArgs& a, int g) {
   if (!ok && g == 0 && tid == 0 && !*(volatile int*)&st->status) set_status(st, RCP_ETIMEOUT);
 }
 
-// KACC: MTTKRP outputs per thread (8 covers l_max R <= 2048 with fewer registers)
+// KACC: MTTKRP outputs per thread, in 2 x 4 register blocks (8: one block per
+// thread, for ceil(l_max / 2) ceil(R / 4) <= 256; 16: two)
 template <typename TM, int KACC>
 __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
   als_body<TM, KACC>(a, blockIdx.x);
 }
 
 // Batched form: CTA b runs the whole ALS of problem b alone (G = 1).
-// Batched problems have l_n <= 32 and R <= 32: at most 4 outputs per thread,
-// which leaves registers for two CTAs per SM.
+// Batched problems have l_n <= 32 and R <= 32: one 2 x 2 block of MTTKRP
+// outputs per thread, which leaves registers for two CTAs per SM.
 template <typename TM>
 __global__ void __launch_bounds__(kThreads, 2) k_als_batched(const PersArgs* __restrict__ args) {
   const PersArgs a = args[blockIdx.x];
@@ -765,7 +802,8 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   const size_t smem = smem_bytes<TM>(p);
   int lmax0 = 1;
   for (int m = 0; m < p->N; ++m) lmax0 = lmax0 > p->l[m] ? lmax0 : p->l[m];
-  const bool small = (int64_t)lmax0 * p->R <= 8 * kThreads;
+  // 8 outputs per thread: 2 x 4 register blocks of the l x R output, one per thread
+  const bool small = (int64_t)((lmax0 + 1) / 2) * ((p->R + 3) / 4) <= kThreads;
   const void* kern = small ? (const void*)k_als_persistent<TM, 8> : (const void*)k_als_persistent<TM, 16>;
   cudaError_t e = cudaFuncSetAttribute(kern,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
