@@ -283,20 +283,20 @@ __device__ void als_body(const PersArgs& a, int g) {
       // column tiles of tj <= kTileJ columns, narrow enough to keep the GW writers busy
       const int tj = max(1, min(kTileJ, (J + GW - 1) / GW));
       // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], with lanes along the
-      // contiguous index (i for mode 1, the column otherwise).  With kPf the next
-      // tile is loaded into registers (8 slots per thread, l_n <= 64) while the
-      // current one is multiplied.
-      constexpr bool kPf = KACC >= 8;
+      // contiguous index (i for mode 1, the column otherwise).  The next tile is
+      // loaded into registers while the current one is multiplied: kPS slots per
+      // thread, 8 for l_n <= 64, 4 for the batched kernel (l_n <= 32).
+      constexpr int kPS = KACC >= 8 ? 8 : 4;
       auto b_slot = [&](int s2, int& i, int& jj) {
         if (L == 1) {
-          jj = warp + kWarps * (s2 >> 1);
-          i = lane + 32 * (s2 & 1);
+          jj = kPS == 8 ? warp + kWarps * (s2 >> 1) : warp + kWarps * s2;
+          i = kPS == 8 ? lane + 32 * (s2 & 1) : lane;
         } else {
           jj = lane;
           i = warp + kWarps * s2;
         }
       };
-      auto b_load = [&](int t0x, TM (&v)[8]) {
+      auto b_load = [&](int t0x, TM (&v)[kPS]) {
         const int njx = min(tj, J - t0x);
         int64_t base = 0;
         if (L != 1) {
@@ -305,7 +305,7 @@ __device__ void als_body(const PersArgs& a, int g) {
           base = (int64_t)(j - b * L) + (int64_t)L * ln * b;
         }
 #pragma unroll
-        for (int s2 = 0; s2 < 8; ++s2) {
+        for (int s2 = 0; s2 < kPS; ++s2) {
           int i, jj;
           b_slot(s2, i, jj);
           TM x = (TM)0;
@@ -315,28 +315,15 @@ __device__ void als_body(const PersArgs& a, int g) {
           v[s2] = x;
         }
       };
-      TM pf[8];
-      if (kPf && gi >= 0 && gi * tj < J) b_load(gi * tj, pf);
+      TM pf[kPS];
+      if (gi >= 0 && gi * tj < J) b_load(gi * tj, pf);
       for (int t0 = gi * tj; gi >= 0 && t0 < J; t0 += GW * tj) {
         const int nj = min(tj, J - t0);
-        if (kPf) {
 #pragma unroll
-          for (int s2 = 0; s2 < 8; ++s2) {
-            int i, jj;
-            b_slot(s2, i, jj);
-            if (i < ln) Bs[i * kBP + jj] = pf[s2];
-          }
-        } else if (L == 1) {
-          for (int jj = warp; jj < kTileJ; jj += kWarps)
-            for (int i = lane; i < ln; i += 32)
-              Bs[i * kBP + jj] = jj < nj ? ((const TM*)a.B)[i + (int64_t)ln * (t0 + jj)] : (TM)0;
-        } else {
-          const int jj = lane;
-          const int j = t0 + jj;
-          const int b = j / L;
-          const int64_t base = (int64_t)(j - b * L) + (int64_t)L * ln * b;
-          for (int i = warp; i < ln; i += kWarps)
-            Bs[i * kBP + jj] = jj < nj ? ((const TM*)a.B)[base + (int64_t)L * i] : (TM)0;
+        for (int s2 = 0; s2 < kPS; ++s2) {
+          int i, jj;
+          b_slot(s2, i, jj);
+          if (i < ln) Bs[i * kBP + jj] = pf[s2];
         }
         // Khatri-Rao rows of the other factors, mode 1 fastest: thread (jj, rg)
         // forms column t0 + jj's digits once and the products for r = rg, rg + 8, ...
@@ -362,7 +349,7 @@ __device__ void als_body(const PersArgs& a, int g) {
           }
         }
         __syncthreads();
-        if (kPf && t0 + GW * tj < J) b_load(t0 + GW * tj, pf);
+        if (t0 + GW * tj < J) b_load(t0 + GW * tj, pf);
         if (it == 1 && n0 == 0) {
           for (int e = tid; e < ln * kTileJ; e += kThreads) {
             const double v = (double)Bs[(e / kTileJ) * kBP + e % kTileJ];
