@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileJ = 32;
+constexpr int kTileJ = 32;  // the tile loads and the Khatri-Rao rows map lanes / tid / 8 onto 32 columns
 constexpr int kBP = kTileJ + 1;                   // padded pitch of the B tile
 constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
 
@@ -258,8 +258,8 @@ __device__ void als_body(const PersArgs& a, int g) {
       const int gw0 = (G > 1 && G >= 2 * ln) ? ln : 0;
       const int GW = G - gw0, gi = g - gw0;
       // ---- phase A: MTTKRP partial over this CTA's column tiles
-      // Each thread owns outputs o = tid + k kThreads, (i, r) = (o % ln, o / ln),
-      // stepped without divisions.  The mixed form sums its FP32 tile sums
+      // Each thread owns register blocks of outputs (below) and forms their tile
+      // sums with independent FMA chains.  The mixed form sums its FP32 tile sums
       // across tiles in double-word FP32 (Knuth's TwoSum), the FP64 path in FP64.
       constexpr bool kMixed = sizeof(TM) == 4;
       double acc[kMixed ? 1 : KACC];
@@ -325,8 +325,9 @@ __device__ void als_body(const PersArgs& a, int g) {
           b_slot(s2, i, jj);
           if (i < ln) Bs[i * kBP + jj] = pf[s2];
         }
-        // Khatri-Rao rows of the other factors, mode 1 fastest: thread (jj, rg)
-        // forms column t0 + jj's digits once and the products for r = rg, rg + 8, ...
+        // Khatri-Rao rows of the other factors, mode 1 fastest: thread (jj, rg),
+        // jj = tid / 8 < 32 = kTileJ, forms column t0 + jj's digits once and the
+        // products for r = rg, rg + 8, ...
         {
           const int jj = tid >> 3, rg = tid & 7;
           int dig[kMaxN];
