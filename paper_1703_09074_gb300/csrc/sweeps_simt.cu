@@ -34,7 +34,8 @@ __device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeVi
                                                double* __restrict__ normpart, int bx, int by,
                                                int gx) {
   __shared__ TA Vs[kRowTile][LMAX];
-  __shared__ int64_t offs[kRowTile];
+  __shared__ int64_t offs[kRowTile];   // column j of the tile: its offset in T
+  __shared__ int64_t offw[kRowTile];   // and in W (SRC == kSrcW)
   const int tid = threadIdx.x;
   const int64_t i = (int64_t)bx * rows_per_cta + tid;
   const bool row_ok = (tid < rows_per_cta) && (i < v.I);
@@ -52,38 +53,45 @@ __device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeVi
   for (int64_t jt = j0; jt < j1; jt += kRowTile) {
     const int nj = (int)min((int64_t)kRowTile, j1 - jt);
     if (tid < nj) {
+      // the only 64-bit divisions of the tile: one per column
       const int64_t j = jt + tid;
-      offs[tid] = (j % v.L) + v.L * v.I * (j / v.L);
+      const int64_t b = v.L == 1 ? j : j / v.L, a = j - b * v.L;
+      offs[tid] = a + v.L * v.I * b;
+      if (SRC == kSrcW) offw[tid] = a + v.L * (int64_t)l * b;
     }
+    // the stream elements of the tile are e = jt l + t, t < nj l local (32-bit)
+    const int nt = nj * l;
     if (SRC == kSrcOmega && sizeof(TA) == 8) {
       // Omega_n[j, c] is element e = j * l + c of the FP64 stream; pairs g = e / 2.
-      const int64_t e0 = jt * l, e1 = (jt + nj) * (int64_t)l;
-      const int64_t g0 = e0 >> 1, g1 = (e1 - 1) >> 1;
-      for (int64_t g = g0 + tid; g <= g1; g += blockDim.x) {
-        const double2 z = normal_pair_f64(seed, sid, kPurposeSketch, (uint64_t)g);
-        int64_t e = 2 * g;
-        if (e >= e0) Vs[e / l - jt][e % l] = (TA)z.x;
-        ++e;
-        if (e < e1) Vs[e / l - jt][e % l] = (TA)z.y;
+      const int64_t e0 = jt * l;
+      const int64_t g0 = e0 >> 1;
+      const int lead = (int)(e0 - 2 * g0);
+      for (int q = tid; 2 * q - lead < nt; q += blockDim.x) {
+        const double2 z = normal_pair_f64(seed, sid, kPurposeSketch, (uint64_t)(g0 + q));
+        int t = 2 * q - lead;
+        if (t >= 0) Vs[t / l][t - (t / l) * l] = (TA)z.x;
+        ++t;
+        if (t < nt) Vs[t / l][t - (t / l) * l] = (TA)z.y;
       }
     } else if (SRC == kSrcOmega) {
       // reduced-precision stream: quads g = e / 4
-      const int64_t e0 = jt * l, e1 = (jt + nj) * (int64_t)l;
-      const int64_t g0 = e0 >> 2, g1 = (e1 - 1) >> 2;
-      for (int64_t g = g0 + tid; g <= g1; g += blockDim.x) {
-        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)g);
+      const int64_t e0 = jt * l;
+      const int64_t g0 = e0 >> 2;
+      const int lead = (int)(e0 - 4 * g0);
+      for (int q = tid; 4 * q - lead < nt; q += blockDim.x) {
+        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)(g0 + q));
         const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t e = 4 * g + q;
-          if (e >= e0 && e < e1) Vs[e / l - jt][e % l] = (TA)zz[q];
+        for (int u = 0; u < 4; ++u) {
+          const int t = 4 * q + u - lead;
+          if (t >= 0 && t < nt) Vs[t / l][t - (t / l) * l] = (TA)zz[u];
         }
       }
     } else if (SRC == kSrcW) {
-      for (int k = tid; k < nj * l; k += blockDim.x) {
+      __syncthreads();  // offw of this tile
+      for (int k = tid; k < nt; k += blockDim.x) {
         const int jj = k / l, c = k - jj * l;
-        const int64_t j = jt + jj;
-        Vs[jj][c] = W[(j % v.L) + v.L * (c + (int64_t)l * (j / v.L))];
+        Vs[jj][c] = W[offw[jj] + v.L * c];
       }
     } else {
       // Khatri-Rao row of the factors of every mode but kr.n, mode 1 fastest.
