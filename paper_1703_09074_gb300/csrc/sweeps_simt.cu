@@ -476,12 +476,129 @@ int project_grid(const ModeView& v, int nsm) {
 
 namespace {
 
+// Row sweep of the batched form (FP32, l <= 32).  A block of few rows would leave
+// most of a 256-thread CTA idle with one thread per row, so the threads form G
+// groups of ceil32(rows) threads: one staging round fills G tiles of kRowTile
+// columns, group g multiplies tile g, and the G partial sums of each row meet
+// in shared memory in a fixed order.  The outputs are those of row_sweep_body.
+template <int LMAX, int SRC>
+__device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__ T, ModeView v,
+                                                       int64_t rows_per_cta, int l,
+                                                       uint64_t seed, uint32_t sid,
+                                                       const float* __restrict__ W,
+                                                       int64_t jchunk, double* __restrict__ part,
+                                                       double* __restrict__ normpart, int bx,
+                                                       int by, int gx) {
+  const bool NORM = normpart != nullptr;  // mode 1 of the sketch also sums X^2
+  constexpr int kMaxG = 8;
+  __shared__ float Vs[kMaxG * kRowTile][LMAX];
+  __shared__ int64_t offs[kMaxG * kRowTile];
+  __shared__ int64_t offw[kMaxG * kRowTile];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int rpc = (int)rows_per_cta;
+  const int rpc32 = (rpc + 31) & ~31;
+  const int G = max(1, min(kMaxG, nthr / rpc32));
+  const int grp = tid / rpc32, r = tid - grp * rpc32;
+  const int64_t i = (int64_t)bx * rows_per_cta + r;
+  const bool row_ok = grp < G && r < rpc && i < v.I;
+  const int64_t j0 = (int64_t)by * jchunk;
+  const int64_t j1 = min(v.J, j0 + jchunk);
+  const int TW = G * kRowTile;  // columns per staging round
+
+  float acc[LMAX];
+#pragma unroll
+  for (int c = 0; c < LMAX; ++c) acc[c] = 0.0f;
+  double nrm = 0.0;
+  for (int k = tid; k < kMaxG * kRowTile * LMAX; k += nthr) (&Vs[0][0])[k] = 0.0f;
+  __syncthreads();
+
+  for (int64_t jt = j0; jt < j1; jt += TW) {
+    const int nj = (int)min((int64_t)TW, j1 - jt);
+    for (int jj = tid; jj < nj; jj += nthr) {
+      const int64_t j = jt + jj;
+      const int64_t b = v.L == 1 ? j : j / v.L, a = j - b * v.L;
+      offs[jj] = a + v.L * v.I * b;
+      if (SRC == kSrcW) offw[jj] = a + v.L * (int64_t)l * b;
+    }
+    const int nt = nj * l;
+    if (SRC == kSrcOmega) {
+      const int64_t e0 = jt * l;
+      const int64_t g0 = e0 >> 2;
+      const int lead = (int)(e0 - 4 * g0);
+      for (int q = tid; 4 * q - lead < nt; q += nthr) {
+        const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)(g0 + q));
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = 4 * q + u - lead;
+          if (t >= 0 && t < nt) Vs[t / l][t - (t / l) * l] = zz[u];
+        }
+      }
+    } else {
+      __syncthreads();  // offw of this round
+      for (int k = tid; k < nt; k += nthr) {
+        const int jj = k / l, c = k - jj * l;
+        Vs[jj][c] = W[offw[jj] + v.L * c];
+      }
+    }
+    __syncthreads();
+    if (row_ok) {
+      // group grp's tile: columns grp kRowTile .. of the round; U loads in flight
+      const int c0 = grp * kRowTile, c1 = min(nj, c0 + kRowTile);
+      constexpr int U = 8;
+      float tn = 0.0f;
+      int jj = c0;
+      for (; jj + U <= c1; jj += U) {
+        float xs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xs[u] = __ldg(T + offs[jj + u] + v.L * i);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (NORM) tn = fmaf(xs[u], xs[u], tn);
+#pragma unroll
+          for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(xs[u], Vs[jj + u][c], acc[c]);
+        }
+      }
+      for (; jj < c1; ++jj) {
+        const float x = __ldg(T + offs[jj] + v.L * i);
+        if (NORM) tn = fmaf(x, x, tn);
+#pragma unroll
+        for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(x, Vs[jj][c], acc[c]);
+      }
+      if (NORM) nrm += (double)tn;
+    }
+    __syncthreads();
+  }
+  // groups 1..G-1 hand their sums to group 0 through Vs (G rpc32 LMAX <= its size)
+  float* red = &Vs[0][0];
+  if (grp > 0 && grp < G)
+#pragma unroll
+    for (int c = 0; c < LMAX; ++c) red[(grp * rpc32 + r) * LMAX + c] = acc[c];
+  __syncthreads();
+  if (grp == 0 && row_ok) {
+    for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+      for (int c = 0; c < LMAX; ++c) acc[c] += red[(g2 * rpc32 + r) * LMAX + c];
+#pragma unroll
+    for (int c = 0; c < LMAX; ++c)
+      if (c < l) part[((int64_t)by * l + c) * v.I + i] = (double)acc[c];
+  }
+  if (NORM) {
+    __shared__ double nred[256];
+    nred[tid] = nrm;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+      if (tid < s2 && tid + s2 < nthr) nred[tid] += nred[tid + s2];
+      __syncthreads();
+    }
+    if (tid == 0) normpart[(int64_t)by * gx + bx] = nred[0];
+  }
+}
 template <int LMAX, int SRC>
 __global__ void __launch_bounds__(256)
 k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
               unsigned* counter, const float* const* __restrict__ xptrs) {
   __shared__ int item_sh;
-  const KrDims kr{};
   for (;;) {
     if (threadIdx.x == 0) item_sh = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -491,14 +608,8 @@ k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, 
     const BItem w = items[it];
     const BRowSweep p = P[w.b];
     const float* T = p.T ? p.T : xptrs[w.b];  // mode 1 reads the caller's tensor
-    if (p.normpart)
-      row_sweep_body<LMAX, float, float, SRC, true>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid,
-                                                    p.W, kr, p.jchunk, p.part, p.normpart, w.bx,
-                                                    w.by, p.gx);
-    else
-      row_sweep_body<LMAX, float, float, SRC, false>(T, p.v, p.rows_per_cta, p.l, p.seed,
-                                                     p.sid, p.W, kr, p.jchunk, p.part, nullptr,
-                                                     w.bx, w.by, p.gx);
+    row_sweep_body_grouped<LMAX, SRC>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid, p.W, p.jchunk,
+                                      p.part, p.normpart, w.bx, w.by, p.gx);
     __syncthreads();
   }
 }
@@ -528,13 +639,17 @@ cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitem
                                int lmax, bool use_w, const float* const* xptrs, int grid,
                                cudaStream_t s) {
   count_launches(1);
-  const int b = lmax_bucket(lmax);
+  // the batch's widths l <= 32 in buckets of 16, 24 and 32 columns (each thread
+  // multiplies every staged column, so padding costs FMAs)
+  const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
   if (use_w) {
     if (b == 16) k_b_row_sweep<16, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else if (b == 24) k_b_row_sweep<24, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
     else if (b == 32) k_b_row_sweep<32, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
     else return cudaErrorInvalidValue;
   } else {
     if (b == 16) k_b_row_sweep<16, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
+    else if (b == 24) k_b_row_sweep<24, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
     else if (b == 32) k_b_row_sweep<32, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
     else return cudaErrorInvalidValue;
   }
@@ -544,10 +659,13 @@ cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitem
 cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitems, unsigned* counter,
                                int lmax, const float* const* xptrs, int grid, cudaStream_t s) {
   count_launches(1);
-  const int b = lmax_bucket(lmax);
+  const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
   if (b == 16) {
     const size_t smem = (size_t)kProjRows * 16 * sizeof(double);
     k_b_col_sweep<16><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+  } else if (b == 24) {
+    const size_t smem = (size_t)kProjRows * 24 * sizeof(double);
+    k_b_col_sweep<24><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
   } else if (b == 32) {
     const size_t smem = (size_t)kProjRows * 32 * sizeof(double);
     k_b_col_sweep<32><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
