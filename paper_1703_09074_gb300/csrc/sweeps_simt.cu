@@ -18,6 +18,7 @@ namespace {
 constexpr int kRowTile = 32;      // columns j staged per step of the row sweep
 constexpr int kProjThreads = 256; // columns j per CTA step of the column sweep
 constexpr int kProjRows = 32;     // rows of Q staged per step of the column sweep
+constexpr int kBatchQRows = 256;  // the same for the batched column sweep (FP32 Q)
 
 enum { kSrcOmega = 0, kSrcW = 1, kSrcKr = 2 };
 
@@ -154,8 +155,10 @@ __device__ __forceinline__ void row_sweep_body(const TIn* __restrict__ T, ModeVi
   }
 }
 
-// Column sweep body for CTA bx of nb persistent CTAs of NT threads (columns j) each.
-template <int LMAX, typename TIn, typename TA, bool GRAM, int NT = kProjThreads>
+// Column sweep body for CTA bx of nb persistent CTAs of NT threads (columns j) each;
+// Q is staged QR rows at a time.
+template <int LMAX, typename TIn, typename TA, bool GRAM, int NT = kProjThreads,
+          int QR = kProjRows>
 __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
                                                const double* __restrict__ Q, TA* __restrict__ W,
                                                double* __restrict__ gpart, int bx, int nb);
@@ -173,13 +176,13 @@ k_row_sweep(const TIn* __restrict__ T, ModeView v, int64_t rows_per_cta, int l, 
 
 }  // namespace
 
-template <int LMAX, typename TIn, typename TA, bool GRAM, int NT>
+template <int LMAX, typename TIn, typename TA, bool GRAM, int NT, int QR>
 __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeView v, int l,
                                                const double* __restrict__ Q, TA* __restrict__ W,
                                                double* __restrict__ gpart, int bx, int nb) {
   extern __shared__ double sm[];
-  TA* Qs = (TA*)sm;                                 // kProjRows x LMAX
-  double* Ws = sm + kProjRows * LMAX;               // NT x (LMAX + 1), GRAM only
+  TA* Qs = (TA*)sm;                                 // QR x LMAX
+  double* Ws = sm + QR * LMAX;                      // NT x (LMAX + 1), GRAM only
   __shared__ unsigned short pairs[kMaxL * (kMaxL + 1) / 2];
   constexpr int kSlots = (LMAX * (LMAX + 1) / 2 + NT - 1) / NT;
   const int tid = threadIdx.x;
@@ -200,10 +203,10 @@ __device__ __forceinline__ void col_sweep_body(const TIn* __restrict__ T, ModeVi
     TA acc[LMAX];
 #pragma unroll
     for (int c = 0; c < LMAX; ++c) acc[c] = (TA)0;
-    for (int64_t i0 = 0; i0 < v.I; i0 += kProjRows) {
-      const int ni = (int)min((int64_t)kProjRows, v.I - i0);
+    for (int64_t i0 = 0; i0 < v.I; i0 += QR) {
+      const int ni = (int)min((int64_t)QR, v.I - i0);
       __syncthreads();
-      for (int k = tid; k < kProjRows * LMAX; k += NT) {
+      for (int k = tid; k < QR * LMAX; k += NT) {
         const int ii = k / LMAX, c = k - ii * LMAX;
         Qs[k] = (ii < ni && c < l) ? (TA)Q[(i0 + ii) + v.I * c] : (TA)0;
       }
@@ -627,8 +630,9 @@ k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, 
     if (it >= nitems) break;
     const BItem w = items[it];
     const BColSweep p = P[w.b];
-    col_sweep_body<LMAX, float, float, false>(p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr,
-                                              w.bx, p.nb);
+    // Q staged 256 rows at a time: once per column block for I <= 256
+    col_sweep_body<LMAX, float, float, false, kProjThreads, kBatchQRows>(
+        p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr, w.bx, p.nb);
     __syncthreads();
   }
 }
@@ -661,13 +665,13 @@ cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitem
   count_launches(1);
   const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
   if (b == 16) {
-    const size_t smem = (size_t)kProjRows * 16 * sizeof(double);
+    const size_t smem = (size_t)kBatchQRows * 16 * sizeof(float);
     k_b_col_sweep<16><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
   } else if (b == 24) {
-    const size_t smem = (size_t)kProjRows * 24 * sizeof(double);
+    const size_t smem = (size_t)kBatchQRows * 24 * sizeof(float);
     k_b_col_sweep<24><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
   } else if (b == 32) {
-    const size_t smem = (size_t)kProjRows * 32 * sizeof(double);
+    const size_t smem = (size_t)kBatchQRows * 32 * sizeof(float);
     k_b_col_sweep<32><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
   } else {
     return cudaErrorInvalidValue;
