@@ -61,15 +61,20 @@ constexpr int kQrThreads = 256;
 
 // CTA per tensor: reduce partials, then CholeskyQR2 (+ a third round after a
 // shifted first round), all in FP64.  Y is I x l column-major in global memory.
+// The factorisation of each round is chol_elim: the elimination on [G | I]
+// that yields R^{-1} with the pivot chain on warp 0 (no serial back
+// substitution).
 __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) {
-  __shared__ double Gs[kMaxL * (kMaxL + 1)];
-  __shared__ double Ri[kMaxL * kMaxL];
+  __shared__ double S[kMaxL][kMaxL + 1];  // Gram / Schur complement; then R^{-1} (upper)
+  __shared__ double tdiag[kMaxL];
+  __shared__ double rowb[2][kMaxL];
+  __shared__ double tb[2][kMaxL];
   __shared__ double red[32];
-  __shared__ int flag[2];
+  __shared__ int flag[2], fail_sh;
   const BQr p = P[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t I = p.I;
-  const int l = p.l, Pp = l + 1;
+  const int l = p.l;
   const int64_t n = I * l;
   for (int64_t e = tid; e < n; e += kQrThreads) {
     double s = 0.0;
@@ -89,11 +94,8 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
     }
   }
   __syncthreads();
-  if (tid == 0) flag[0] = 0;
-  for (int round = 0; round < 3; ++round) {
-    __syncthreads();
-    if (round == 2 && !flag[0]) break;
-    // Gram G = Y^T Y (upper triangle, pitch l + 1)
+  // S = Y^T Y in the upper triangle (plus shift on the diagonal), zero below
+  auto gram = [&](double shift) {
     for (int q = tid; q < l * (l + 1) / 2; q += kQrThreads) {
       int c = 0, rem = q;
       while (rem > c) {
@@ -110,78 +112,54 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
         s1 = fma(y1[i + 1], y2[i + 1], s1);
       }
       if (i < I) s0 = fma(y1[i], y2[i], s0);
-      Gs[r * Pp + c] = s0 + s1;
+      S[r][c] = (s0 + s1) + (r == c ? shift : 0.0);
+      if (r != c) S[c][r] = 0.0;
     }
     __syncthreads();
-    // Cholesky (warp 0): round 0 may fall back to the shifted Gram G + s I
-    // (shifted CholeskyQR3, then one more plain round); a failure after that
-    // is reported as singular
+  };
+  if (tid == 0) flag[0] = 0;
+  for (int round = 0; round < 3; ++round) {
+    __syncthreads();
+    if (round == 2 && !flag[0]) break;
+    gram(0.0);
+    // trace and finiteness of the diagonal (warp 0), the shifted-CholeskyQR3 shift
     if (warp == 0) {
-      double tr = 0.0;
-      bool bad = false;
-      for (int c = 0; c < l; ++c) {
-        tr += Gs[c * Pp + c];
-        bad = bad || !isfinite(Gs[c * Pp + c]);
+      const double d = lane < l ? S[lane][lane] : 0.0;
+      int bad = lane < l && !isfinite(d);
+      double tr = d;
+      for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
       }
-      const double shift = 11.0 * ((double)I * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
-      int res = 0;  // 0 ok, 1 shifted retry needed, 2 fatal
-      if (bad) {
-        res = 2;
-        if (lane == 0) set_status(p.st, RCP_ENAN);
-      } else if (!warp_chol(Gs, l, round == 0 ? shift : 0.0)) {
-        res = round == 0 ? 1 : 2;
-        if (res == 2 && lane == 0) set_status(p.st, RCP_ESINGULAR);
+      if (lane == 0) {
+        red[0] = 11.0 * ((double)I * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
+        flag[1] = bad;
+        if (bad) set_status(p.st, RCP_ENAN);
       }
-      if (lane == 0) flag[1] = res;
     }
     __syncthreads();
-    if (flag[1] == 2) return;
-    if (flag[1] == 1) {
-      for (int q = tid; q < l * (l + 1) / 2; q += kQrThreads) {
-        int c = 0, rem = q;
-        while (rem > c) {
-          rem -= c + 1;
-          ++c;
-        }
-        const int r = rem;
-        const double* y1 = p.Y + I * r;
-        const double* y2 = p.Y + I * c;
-        double s = 0.0;
-        for (int64_t i = 0; i < I; ++i) s = fma(y1[i], y2[i], s);
-        Gs[r * Pp + c] = s;
-      }
+    if (flag[1]) return;
+    const double shift = red[0];
+    bool ok = chol_elim<double>(S, tdiag, rowb, tb, l, round == 0 ? shift : 0.0, &fail_sh);
+    if (!ok && round == 0) {
+      // shifted CholeskyQR3: factor G + s I, then one more plain round
       __syncthreads();
-      if (warp == 0) {
-        double tr = 0.0;
-        for (int c = 0; c < l; ++c) tr += Gs[c * Pp + c];
-        const double shift = 11.0 * ((double)I * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
-        __syncwarp();
-        for (int c = lane; c < l; c += 32) Gs[c * Pp + c] += shift;
-        __syncwarp();
-        const bool ok = warp_chol(Gs, l, 0.0);
-        if (lane == 0) {
-          flag[1] = ok ? 0 : 2;
-          flag[0] = 1;
-          atomicOr(&p.st->info, RCP_INFO_SHIFTED_QR);
-          if (!ok) set_status(p.st, RCP_ESINGULAR);
-        }
+      gram(shift);
+      ok = chol_elim<double>(S, tdiag, rowb, tb, l, 0.0, &fail_sh);
+      if (tid == 0) {
+        flag[0] = 1;
+        atomicOr(&p.st->info, RCP_INFO_SHIFTED_QR);
       }
-      __syncthreads();
-      if (flag[1] == 2) return;
     }
-    // R^{-1} by back substitution, lanes of warp 0 own columns
-    if (warp == 0) {
-      for (int c = lane; c < l; c += 32) {
-        for (int i = l - 1; i >= 0; --i) {
-          double v = 0.0;
-          if (i <= c) {
-            v = (i == c) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= c; ++k) v -= Gs[i * Pp + k] * Ri[k * kMaxL + c];
-            v /= Gs[i * Pp + i];
-          }
-          Ri[i * kMaxL + c] = v;
-        }
-      }
+    if (!ok) {
+      if (tid == 0) set_status(p.st, RCP_ESINGULAR);
+      return;
+    }
+    // R^{-1}[k][c] = (R^{-T})[c][k] into the upper triangle (the lower one is only read)
+    for (int q = tid; q < l * l; q += kQrThreads) {
+      const int k = q / l, c = q - k * l;
+      if (k < c) S[k][c] = S[c][k];
+      else if (k == c) S[k][k] = tdiag[k];
     }
     __syncthreads();
     // Y <- Y R^{-1}, one thread per row, in place
@@ -190,7 +168,7 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
       for (int k = 0; k < l; ++k) y[k] = p.Y[i + I * k];
       for (int c = l - 1; c >= 0; --c) {
         double s = 0.0;
-        for (int k = 0; k <= c; ++k) s = fma(y[k], Ri[k * kMaxL + c], s);
+        for (int k = 0; k <= c; ++k) s = fma(y[k], S[k][c], s);
         y[c] = s;  // y[k] for k < c still holds the input row
       }
       for (int c = 0; c < l; ++c) p.Y[i + I * c] = y[c];

@@ -63,117 +63,6 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
   if (threadIdx.x == 0) Gp[p] = s;
 }
 
-__device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
-__device__ __forceinline__ double rsqrt_t(double d) { return rsqrt64(d); }
-
-// d > floor_ >= 0 and finite, as integer compares (positive IEEE numbers order
-// like their bit patterns), which keeps the test off the FP64 pipe
-__device__ __forceinline__ bool pivot_ok(double d, double floor_) {
-  const long long db = __double_as_longlong(d);
-  return db > __double_as_longlong(floor_) && db > 0 && db < 0x7ff0000000000000LL;
-}
-__device__ __forceinline__ bool pivot_ok(float d, float floor_) {
-  const int db = __float_as_int(d);
-  return db > __float_as_int(floor_) && db > 0 && db < 0x7f800000;
-}
-
-// Cholesky G = R^T R of the SPD matrix in the upper triangle of S (l x l, with
-// the strict lower triangle zero) by one CTA, together with R^{-1}.
-// Elimination on [G | I] by rows: step k scales row k by 1 / sqrt(pivot)
-// (giving row k of R, and of R^{-T} on the right) and subtracts R[k][i] times
-// it from every later row i, so the left part ends as R and the right part as
-// R^{-T} (the row operations E satisfy E G = R, hence E = R^{-T}).  S keeps
-// the Schur complement in its upper triangle and receives R^{-T} in its strict
-// lower triangle (diagonal in tdiag).  The pivot chain (update of row k+1, its
-// reciprocal square root, the scaling) runs on warp 0 one step ahead, while
-// warps 1-3 and 5-7 (warp 4 shares warp 0's sub-partition, whose FP64 unit
-// issues one warp instruction per 64 cycles) update rows k+2.. of step k: one
-// barrier per step.  Returns false, uniformly, when a pivot is not above
-// floor_ (>= 0); 256 threads.
-template <typename T>
-__device__ bool chol_elim(T (*S)[kMaxL + 1], T* tdiag, T (*rowb)[kMaxL], T (*tb)[kMaxL], int l,
-                          T floor_, int* fail_sh) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // update warps 1-3, 5-7 as uw = 0..5: column lane (l <= 32) or lane + 32 (uw & 1),
-  // rows k+2+r0, k+2+r0+rstep, ...
-  const int uw = warp == 0 || warp == 4 ? -1 : (warp < 4 ? warp - 1 : warp - 2);
-  const int jcol = l <= 32 ? lane : lane + 32 * (uw & 1);
-  const int r0 = l <= 32 ? uw : uw >> 1, rstep = l <= 32 ? 6 : 3;
-  if (tid == 0) *fail_sh = 0;
-  __syncthreads();
-  if (warp == 0) {
-    const T d = S[0][0];
-    const bool good = pivot_ok(d, floor_);
-    const T rs = good ? rsqrt_t(d) : T(0);
-    for (int j = lane; j < l; j += 32) rowb[0][j] = S[0][j] * rs;
-    if (lane == 0) {
-      tb[0][0] = rs;
-      tdiag[0] = rs;
-      if (!good) *fail_sh = 1;
-    }
-  }
-  __syncthreads();
-  bool ok = *fail_sh == 0;
-  for (int k = 0; ok && k + 1 < l; ++k) {
-    const T* rk = rowb[k & 1];
-    const T* tk = tb[k & 1];
-    if (warp == 0) {
-      // row k+1: its update by row k, the pivot, the scaling
-      const int i = k + 1;
-      const T f = rk[i];
-      T v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
-        v[h] = T(0);
-        if (j < l) v[h] = fma(-f, j >= i ? rk[j] : tk[j], S[i][j]);
-      }
-      const T d = __shfl_sync(0xffffffffu, (i >> 5) ? v[1] : v[0], i & 31);
-      const bool good = pivot_ok(d, floor_);
-      const T rs = good ? rsqrt_t(d) : T(0);
-      T* rn = rowb[(k + 1) & 1];
-      T* tn = tb[(k + 1) & 1];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
-        if (j < l) {
-          const T w = v[h] * rs;
-          if (j > i) {
-            rn[j] = w;
-          } else if (j < i) {
-            tn[j] = w;
-            S[i][j] = w;
-          }
-        }
-      }
-      if (lane == 0) {
-        tn[i] = rs;
-        tdiag[i] = rs;
-        if (!good) *fail_sh = 1;
-      }
-    } else if (uw >= 0 && jcol < l) {
-      // rows k+2..: S[i][j] -= R[k][i] R[k][j] (j >= i), T[i][j] -= R[k][i] T[k][j] (j <= k)
-      const int j = jcol;
-      for (int i = k + 2 + r0; i < l; i += rstep) {
-        if (j >= i) S[i][j] = fma(-rk[i], rk[j], S[i][j]);
-        else if (j <= k) S[i][j] = fma(-rk[i], tk[j], S[i][j]);
-      }
-    }
-    __syncthreads();
-    ok = *fail_sh == 0;
-  }
-  return ok;
-}
-
-// R^{-1} = (R^{-T})^T to Rinv (l x l column-major): (R^{-1})[i][c] = T[c][i], i <= c
-template <typename T>
-__device__ void write_rinv(const T (*S)[kMaxL + 1], const T* tdiag, int l, double* Rinv) {
-  for (int q = threadIdx.x; q < l * l; q += blockDim.x) {
-    const int i = q % l, c = q / l;
-    Rinv[q] = i < c ? (double)S[c][i] : (i == c ? (double)tdiag[c] : 0.0);
-  }
-}
-
 // The FP64 factorisation of one CholeskyQR round (chol_elim in FP64).
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
