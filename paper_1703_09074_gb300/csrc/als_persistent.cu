@@ -375,6 +375,9 @@ __device__ void als_body(const PersArgs& a, int g) {
             TM sacc[kBI * kBR];
 #pragma unroll
             for (int q = 0; q < kBI * kBR; ++q) sacc[q] = (TM)0;
+            // unrolled so that the shared-memory loads of later columns are in
+            // flight while earlier FMAs run
+#pragma unroll 8
             for (int jj = 0; jj < nj; ++jj) {
               TM x[kBI], kr[kBR];
 #pragma unroll
