@@ -196,6 +196,13 @@ __device__ void als_body(const PersArgs& a, int g) {
         if (dw) {
           double* zd = nullptr;
           gj = cta_gj_inverse_dw<kThreads>(R, A0, A1, &zd);
+          // FP32 copy of V^{-1} (the double-word high parts, row pitch 32) in U32,
+          // unused by path 3: the one-CTA solve forms its refinement correction in FP32
+          if (gj && G == 1)
+            for (int e = tid; e < R * R; e += kThreads) {
+              const int i = e / R, c = e - i * R;
+              U32[i * 32 + c] = ((const float2*)Sx)[i * 64 + R + c].x;
+            }
         }
         if (warp == 0) {
           int path = 0;
@@ -471,18 +478,22 @@ __device__ void als_body(const PersArgs& a, int g) {
             X0[e] = d;
           }
           __syncthreads();
+          // the residual m - x0 V in FP64, kept in FP32: the correction it feeds is
+          // about kappa 2^-46 of x, so its FP32 rounding stays far below FP64 rounding
+          // of x, and the FP64 unit is this loop's bound
+          float* Rf = (float*)Xs;
           for (int e = tid; e < nout; e += kThreads) {
             const int c = e / ln, i = e - c * ln;
             double d = 0.0;
             for (int k = 0; k < R; ++k) d = fma(X0[i + ln * k], V[k * (R + 1) + c], d);
-            Xs[e] = Mm[e] - d;
+            Rf[e] = (float)(Mm[e] - d);
           }
           __syncthreads();
           for (int e = tid; e < nout; e += kThreads) {
             const int c = e / ln, i = e - c * ln;
-            double d = 0.0;
-            for (int k = 0; k < R; ++k) d = fma(Xs[i + ln * k], Zd[k * 32 + c], d);
-            const double x = X0[e] + d;
+            float d = 0.0f;
+            for (int k = 0; k < R; ++k) d = fmaf(Rf[i + ln * k], U32[k * 32 + c], d);
+            const double x = X0[e] + (double)d;
             a.rows[e] = x;
             X0[e] = Mm[e] * x;
           }
