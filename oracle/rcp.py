@@ -151,6 +151,87 @@ def cp_als(B, R, tol, max_iters, seed, init=None):
     return lam, A, rho, it, hist
 
 
+def eig_init(B, R):
+    """Algorithm 2 step 2 / Algorithm 3 step 2: initial factors of modes 2..N.
+
+    For each mode n >= 2, the eigenvectors of B_(n) B_(n)^T belonging to its R
+    largest eigenvalues (in descending order), each with its largest-magnitude
+    entry positive (the first such entry on a tie).  Mode 1 is computed first
+    and needs none (entry None).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    out = [None]
+    for n in range(2, B.ndim + 1):
+        Bn = unfold(B, n)
+        w, V = np.linalg.eigh(Bn @ Bn.T)
+        V = V[:, np.argsort(-w, kind="stable")[:R]]
+        piv = np.argmax(np.abs(V), axis=0)
+        s = np.sign(V[piv, np.arange(V.shape[1])])
+        s[s == 0] = 1.0
+        out.append(V * s[None, :])
+    return out
+
+
+def initial_factors(B, R, seed, init="randn"):
+    """Initial factors of the stage-2 solvers: seeded N(0,1) or eigenvectors."""
+    if init == "eig":
+        return eig_init(B, R)
+    return als_init(np.asarray(B).shape, R, seed)
+
+
+def cp_bcd(B, R, tol, max_iters, seed, init=None):
+    """Algorithm 3 steps 3-15: CP by successive rank-one deflation (block
+    coordinate descent, Section 3.2.2) on the compressed tensor B.
+
+    The residual starts as Y = B.  Component r = 1..R starts from column r of
+    the initial factors (modes 2..N) and repeats, for n = 1..N,
+        a_n = Y_(n) (KR of the other a_m) / prod_{m != n} a_m^T a_m
+    (the rank-one case of Definition 2's pseudo-inverse), normalising a_n for
+    n < N and taking lambda_r = |a_N| with a_N normalised at n = N.  After each
+    such sweep the fit of the rank-r model, rho = 1 - |Y - lambda_r a_1 o ...
+    o a_N|^2 / |B|^2, is compared with the previous sweep's (before the first
+    sweep: the fit of the rank-(r-1) model, 1 - |Y|^2 / |B|^2); the component
+    is done when the change is below tol or after max_iters sweeps.  Then
+    Y = B - [[lambda_{1..r}; A_{:,1..r}, ...]] (step 14).
+    Returns (lam, factors, rho, total sweeps over all components, rho history).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    N = B.ndim
+    A0 = list(init) if init is not None else als_init(B.shape, R, seed)
+    F = [np.zeros((B.shape[n], R)) for n in range(N)]
+    lam = np.zeros(R)
+    nB = fro2(B)
+    Y = B.copy()
+    total = 0
+    hist = []
+    rho = 1.0 - fro2(Y) / nB
+    for r in range(R):
+        a = [None] + [np.array(A0[n][:, r], dtype=np.float64) for n in range(1, N)]
+        lam_r = 0.0
+        rho_prev = 1.0 - fro2(Y) / nB
+        for _ in range(max_iters):
+            for n in range(1, N + 1):
+                cols = [None if v is None else v[:, None] for v in a]
+                kr = kr_except(cols, n)[:, 0]
+                denom = float(np.prod([a[m - 1] @ a[m - 1] for m in range(1, N + 1) if m != n]))
+                an = unfold(Y, n) @ kr / denom
+                nu = float(np.sqrt(an @ an))
+                a[n - 1] = an / nu if nu > 0 else np.zeros_like(an)
+                if n == N:
+                    lam_r = nu
+            total += 1
+            rho = 1.0 - fro2(Y - kruskal(np.array([lam_r]), [v[:, None] for v in a])) / nB
+            hist.append(rho)
+            if abs(rho - rho_prev) < tol:
+                break
+            rho_prev = rho
+        for n in range(N):
+            F[n][:, r] = a[n]
+        lam[r] = lam_r
+        Y = B - kruskal(lam[:r + 1], [Fn[:, :r + 1] for Fn in F])
+    return lam, F, rho, total, hist
+
+
 def back_project(Qs, lam, factors):
     """Algorithm 2 steps 12-13: A_n = Q_n Atilde_n, then re-normalise and update lambda."""
     lam = np.array(lam, dtype=np.float64)
@@ -163,11 +244,16 @@ def back_project(Qs, lam, factors):
     return lam, out
 
 
-def rcp_als(X, R, p, q, tol, max_iters, seed, init=None, omega="f64"):
-    """The whole method: compress, ALS on B, recover.  Returns a dict of every intermediate."""
+def rcp_als(X, R, p, q, tol, max_iters, seed, init=None, omega="f64", solver="als"):
+    """The whole method: compress, ALS (Algorithm 2) or BCD (Algorithm 3) on B,
+    recover.  ``init`` is a list of initial factors, "randn" (the default) or
+    "eig" (eigenvectors of B_(n) B_(n)^T).  Returns a dict of every intermediate."""
     X = np.asarray(X, dtype=np.float64)
     B, Qs = compress(X, R, p, q, seed, omega)
-    lam_t, At, rho, iters, hist = cp_als(B, R, tol, max_iters, seed, init=init)
+    if isinstance(init, str):
+        init = initial_factors(B, R, seed, init)
+    stage2 = cp_bcd if solver == "bcd" else cp_als
+    lam_t, At, rho, iters, hist = stage2(B, R, tol, max_iters, seed, init=init)
     lam, A = back_project(Qs, lam_t, At)
     nX2 = fro2(X)
     nB2 = fro2(B)
