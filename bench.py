@@ -48,9 +48,10 @@ WORKLOADS = {
 NCU_TRAFFIC = {("c2", "mixed", "apply"): 275.27e6 + 3.58e6,
                ("c2", "mixed", "project"): 256.86e6 + 14.30e6}
 
-# GB300 FP64 arithmetic peak used for ALU-bound FP64 kernels: 152 SMs x 2 FP64
-# FMA per clock per SM x 2 FLOP x 2.07 GHz ("Roofline").
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# GB300 FP64 arithmetic peak for ALU-bound FP64 kernels: 1.06 TFLOP/s, measured on
+# this part with an FMA-chain kernel (profiles/fp64_fp32_fma_peak_gb300.md); the
+# measured-peaks file holds HBM and BF16 figures only.
+FP64_PEAK_TFLOPS = 1.06
 
 
 def parse():
@@ -289,7 +290,7 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": f"mode-1 {dom} sweep (FP64 FMA)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived FP64 FMA rate (not in the measured-peaks file)",
+                "peak_source": "measured FP64 FMA rate (FMA-chain probe; not in the measured-peaks file)",
                 "algorithmic": f"{flops:.4g} FLOP per launch (2 I J l)"}
     else:
         achieved = xbytes / per_launch_s / 1e9
@@ -339,7 +340,9 @@ def run_ours(args):
                    "equal_fit_1e-3": abs(res["rel_err"] - r64["rel_err"]) <= 1e-3 * r64["rel_err"]}
         p64.close()
 
-    value = total_ms / 1e3 / (args.steps * ws)
+    # every rank decomposes its own replica: the time of one decomposition is the
+    # slowest rank's per-step time, and the job's throughput is ws decompositions per step
+    value = total_ms / 1e3 / args.steps
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -354,7 +357,8 @@ def run_ours(args):
             "stages": stages,
             "mode1_sweeps": mode1,
             "roofline": roof,
-            "e2e": {"value": e2e_v / ws, "unit": "s", "h2d_bytes_per_step": xbytes,
+            "decompositions_per_s": ws * args.steps / (total_ms / 1e3),
+            "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": xbytes,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_total // args.steps,
             "clocks": clk}

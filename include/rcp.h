@@ -87,8 +87,25 @@ enum {
 
 /* Flags for rcp_config.flags. */
 enum {
-  RCP_FLAG_HOST_STAGING = 1    /* reserve device buffers so rcp_decompose_host can run */
+  RCP_FLAG_HOST_STAGING = 1,   /* reserve device buffers so rcp_decompose_host can run  */
+  RCP_FLAG_NO_SHIFT = 2        /* no shifted-CholeskyQR fallback: a sketch whose Gram
+                                  needs the shift (numerically rank-deficient Y) sets
+                                  RCP_ESINGULAR instead of RCP_INFO_SHIFTED_QR        */
 };
+
+/* Initial factors of the stage-2 solver on B (Algorithm 2 step 2, Algorithm 3
+ * step 2). */
+typedef enum {
+  RCP_INIT_RANDN = 0,   /* seeded N(0,1) factors for modes 2..N (the default)       */
+  RCP_INIT_LEARNED = 1, /* reserved for the warm-start network (batched form only)  */
+  RCP_INIT_EIG = 2      /* the leading R eigenvectors of B_(n) B_(n)^T, n = 2..N     */
+} rcp_init;
+
+/* Stage-2 solver on the compressed tensor B. */
+typedef enum {
+  RCP_SOLVER_ALS = 0,   /* CP-ALS, Algorithm 2                                       */
+  RCP_SOLVER_BCD = 1    /* rank-one deflation by block coordinate descent, Algorithm 3 */
+} rcp_solver;
 
 #define RCP_MAX_NDIM 8
 #define RCP_MAX_L 64      /* largest sketch width l_n = R + p supported */
@@ -106,6 +123,12 @@ typedef struct {
   uint64_t seed;                 /* key of the counter-based random streams          */
   int32_t precision;             /* rcp_precision                                    */
   int32_t flags;                 /* RCP_FLAG_* bits                                  */
+  int32_t init;                  /* rcp_init (0 = seeded N(0,1))                     */
+  int32_t solver;                /* rcp_solver (0 = ALS)                             */
+  int64_t wait_budget;           /* clock cycles each grid-barrier wait of the
+                                    multi-CTA ALS kernel may spin before it records
+                                    RCP_ETIMEOUT and the kernel leaves; 0 = the
+                                    default (2^31 cycles, about one second)        */
 } rcp_config;
 
 /* Results of one decomposition, filled by rcp_result / rcp_decompose_host. */
@@ -286,6 +309,16 @@ rcp_status rcp_batched_autotune(rcp_batched_t plan, const void* const* X_dev, in
  * tensor's device status. */
 rcp_status rcp_batched_result(rcp_batched_t plan, int32_t index, double* const* A_dev,
                               double* lambda_dev, rcp_result* res);
+
+/* Intermediates of tensor `index` after a run, for checking each step of the
+ * method: the bases Q_n of Algorithm 1 step 12 (Q_dev[n-1], I_n x l_n
+ * column-major FP64), the compressed tensor B of step 13 (B_dev, FP64, Kolda
+ * layout l_1 x ... x l_N), and the ALS factors Atilde_n of Algorithm 2 step 11
+ * with their lambda (At_dev[n-1], l_n x R column-major FP64; lambda_t_dev, R
+ * doubles).  Every pointer (and every array entry) may be NULL.  Asynchronous
+ * on the plan's stream. */
+rcp_status rcp_batched_intermediates(rcp_batched_t plan, int32_t index, double* const* Q_dev,
+                                     double* B_dev, double* const* At_dev, double* lambda_t_dev);
 
 /* Free the batch plan (synchronises first).  NULL is ignored. */
 rcp_status rcp_batched_destroy(rcp_batched_t plan);

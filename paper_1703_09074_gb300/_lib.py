@@ -16,7 +16,9 @@ RCP_OK, RCP_EINVAL, RCP_ENOMEM, RCP_ECUDA, RCP_ESINGULAR, RCP_ENAN, RCP_ETIMEOUT
     RCP_EORDER, RCP_ENOTCONV = range(9)
 RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
 RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
-RCP_FLAG_HOST_STAGING = 1
+RCP_FLAG_HOST_STAGING, RCP_FLAG_NO_SHIFT = 1, 2
+RCP_INIT_RANDN, RCP_INIT_LEARNED, RCP_INIT_EIG = 0, 1, 2
+RCP_SOLVER_ALS, RCP_SOLVER_BCD = 0, 1
 RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED, RCP_INFO_LEARNED_INIT = 1, 2, 4
 WS_LPAD, WS_RPAD = 24, 16
 MLP_IN, MLP_HIDDEN, MLP_OUT = 13824, 512, 1152
@@ -34,7 +36,10 @@ class RcpConfig(ctypes.Structure):
                 ("max_iters", ctypes.c_int32),
                 ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32),
+                ("init", ctypes.c_int32),
+                ("solver", ctypes.c_int32),
+                ("wait_budget", ctypes.c_int64)]
 
 
 class RcpResult(ctypes.Structure):
@@ -77,6 +82,8 @@ SIGNATURES = {
     "rcp_batched_result": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P), P,
                                           ctypes.POINTER(RcpResult)]),
     "rcp_batched_destroy": (ctypes.c_int, [P]),
+    "rcp_batched_intermediates": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P), P,
+                                                 ctypes.POINTER(P), P]),
     "rcp_mlp_param_count": (ctypes.c_int64, []),
     "rcp_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, P, ctypes.POINTER(P)]),
     "rcp_mlp_destroy": (ctypes.c_int, [P]),

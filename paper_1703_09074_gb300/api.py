@@ -15,6 +15,8 @@ from ._lib import RcpConfig, RcpResult, check
 
 _DT = {torch.float32: _lib.RCP_DTYPE_F32, torch.float64: _lib.RCP_DTYPE_F64}
 _PREC = {"f64": _lib.RCP_PREC_F64, "mixed": _lib.RCP_PREC_MIXED}
+_INIT = {"randn": _lib.RCP_INIT_RANDN, "eig": _lib.RCP_INIT_EIG}
+_SOLVER = {"als": _lib.RCP_SOLVER_ALS, "bcd": _lib.RCP_SOLVER_BCD}
 
 
 def _ptr_array(tensors):
@@ -29,7 +31,7 @@ class Plan:
 
     def __init__(self, dims, rank, oversample=10, power_iters=2, tol=1e-10, max_iters=50,
                  seed=0, in_dtype=torch.float32, precision="f64", host_staging=False,
-                 stream=None):
+                 stream=None, init="randn", solver="als", wait_budget=0, no_shift=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.N = len(self.dims)
@@ -47,7 +49,11 @@ class Plan:
         cfg.max_iters = int(max_iters)
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         cfg.precision = _PREC[precision]
-        cfg.flags = _lib.RCP_FLAG_HOST_STAGING if host_staging else 0
+        cfg.flags = ((_lib.RCP_FLAG_HOST_STAGING if host_staging else 0) |
+                     (_lib.RCP_FLAG_NO_SHIFT if no_shift else 0))
+        cfg.init = _INIT[init]
+        cfg.solver = _SOLVER[solver]
+        cfg.wait_budget = int(wait_budget)
         self.cfg = cfg
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
@@ -150,10 +156,12 @@ class Plan:
         check(code, "rcp_decompose_host")
         return [a.t() for a in A_host], lam_host, _result_dict(res, self.N)
 
-    def result(self):
+    def result(self, raise_on_status=True):
+        """Result record; a device error status raises unless raise_on_status is False."""
         res = RcpResult()
         code = self.lib.rcp_result_get(self.h, ctypes.byref(res))
-        check(code, "rcp_result_get")
+        if raise_on_status or code in (_lib.RCP_EINVAL, _lib.RCP_ECUDA):
+            check(code, "rcp_result_get")
         return _result_dict(res, self.N)
 
     def core(self):
@@ -270,6 +278,24 @@ class BatchedPlan:
                                            ctypes.byref(res))
         check(code, "rcp_batched_result")
         return [a.t() for a in A], lam, _result_dict(res, len(self.dims[b]))
+
+    def intermediates(self, b):
+        """Tensor b's bases Q_n (I_n x l_n), core B (Kolda layout, FP64) and ALS factors."""
+        l = self.widths(b)
+        dev = self.device
+        Q = [torch.empty((ln, I), dtype=torch.float64, device=dev) for I, ln in zip(self.dims[b], l)]
+        B = torch.empty(tuple(reversed(l)), dtype=torch.float64, device=dev)
+        At = [torch.empty((self.ranks[b], ln), dtype=torch.float64, device=dev) for ln in l]
+        lam_t = torch.empty(self.ranks[b], dtype=torch.float64, device=dev)
+        check(self.lib.rcp_batched_intermediates(self.h, b, _ptr_array(Q), ctypes.c_void_p(B.data_ptr()),
+                                                 _ptr_array(At), ctypes.c_void_p(lam_t.data_ptr())),
+              "rcp_batched_intermediates")
+        return [q.t() for q in Q], B, [a.t() for a in At], lam_t
+
+    def widths(self, b):
+        res = RcpResult()
+        self.lib.rcp_batched_result(self.h, b, None, None, ctypes.byref(res))
+        return [res.widths[k] for k in range(len(self.dims[b]))]
 
     def set_warm_start(self, net):
         """Start ALS from the network's factors in later runs (None: random init)."""

@@ -40,7 +40,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTileJ = 32;  // the tile loads and the Khatri-Rao rows map lanes / tid / 8 onto 32 columns
 constexpr int kBP = kTileJ + 1;                   // padded pitch of the B tile
-constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
+constexpr long long kBarrierBudget = 1LL << 31;  // default clock-cycle budget (about 1 s)
 
 
 // Grid barrier over nblocks CTAs on a monotonic arrival counter (zeroed before
@@ -51,7 +51,8 @@ constexpr long long kBarrierBudget = 1LL << 31;  // clock cycles (about 1 s)
 // raises the abort flag and returns false.  The other CTAs then run out their
 // own budgets at this barrier or the next, neither of which can complete, so
 // every CTA leaves.
-__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag, unsigned& epoch) {
+__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag, unsigned& epoch,
+                          long long budget) {
   __syncthreads();
   __shared__ int ok_sh;
   if (threadIdx.x == 0) {
@@ -64,7 +65,7 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag, unsi
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if ((int)(v - target) >= 0) break;
-      if (clock64() - t0 > kBarrierBudget) {
+      if (clock64() - t0 > budget) {
         ok = 0;
         break;
       }
@@ -82,7 +83,8 @@ __device__ __forceinline__ bool phase_sync(const PersArgs& a, int G, unsigned& e
     __syncthreads();
     return true;
   }
-  return grid_sync(a.bar, (unsigned)G, a.abort_flag, epoch);
+  return grid_sync(a.bar, (unsigned)G, a.abort_flag, epoch,
+                   a.budget > 0 ? a.budget : kBarrierBudget);
 }
 
 // KACC: MTTKRP outputs (l_n x R) per thread, at most KACC * kThreads.
@@ -884,6 +886,7 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.tol = p->cfg.tol;
   a.max_iters = p->cfg.max_iters;
   a.user_init = p->user_init ? 1 : 0;
+  a.budget = p->cfg.wait_budget;
   // R <= 32: each row-owning CTA inverts V in double-word arithmetic (path 3)
   a.direct64 = 0;
   void* args[] = {&a};

@@ -11,9 +11,9 @@
 namespace rcp {
 cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStream_t s);
 cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
-                        int round, int als_mode, cudaStream_t s);
+                        int round, int als_mode, cudaStream_t s, bool no_shift = false);
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s, bool final_qr);
+                          cudaStream_t s, bool final_qr, bool no_shift = false);
 cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
                          cudaStream_t s);
@@ -151,8 +151,17 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   if (cfg->in_dtype != RCP_DTYPE_F64 && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
   if (cfg->precision != RCP_PREC_F64 && cfg->precision != RCP_PREC_MIXED) return RCP_EINVAL;
   if (cfg->precision == RCP_PREC_MIXED && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
-  for (int n = 0; n < N; ++n)
-    if (cfg->dims[n] < 1 || cfg->dims[n] > (1LL << 40)) return RCP_EINVAL;
+  if (cfg->init != RCP_INIT_RANDN) return RCP_EINVAL;
+  if (cfg->solver != RCP_SOLVER_ALS) return RCP_EINVAL;
+  if (cfg->wait_budget < 0) return RCP_EINVAL;
+  if (cfg->flags & ~(RCP_FLAG_HOST_STAGING | RCP_FLAG_NO_SHIFT)) return RCP_EINVAL;
+  {
+    int64_t total = 1;
+    for (int n = 0; n < N; ++n) {
+      if (cfg->dims[n] < 1 || cfg->dims[n] > (1LL << 40)) return RCP_EINVAL;
+      if (!mul_elems(total, cfg->dims[n], &total)) return RCP_EINVAL;  // no int64 overflow below
+    }
+  }
   {
     // every l_n = min(R + p, I_n, J_n) must lie in [R, RCP_MAX_L] (checked before any CUDA call)
     int64_t cur[kMaxN];
@@ -226,6 +235,7 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     int lmx = 1;
     for (int n = 0; n < N; ++n) lmx = lmx > p->l[n] ? lmx : p->l[n];
     part_max = std::max(part_max, (int64_t)p->nsm * lmx * p->R);  // persistent ALS partials
+    part_max = std::max(part_max, (int64_t)N * 32 * 32);  // one-cluster ALS: N x 32 x 32 float2
   }
   p->bufT_elems = bufmax;
   p->part_elems = part_max;
@@ -309,6 +319,7 @@ namespace {
 // Algorithm 1 steps (5)-(12) for mode n on the FP64 path.
 rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
   cudaStream_t s = p->stream;
+  const bool ns = (p->cfg.flags & RCP_FLAG_NO_SHIFT) != 0;
   const int n0 = mode - 1;
   const ModeView v = p->view[n0];
   const int l = p->l[n0];
@@ -329,7 +340,7 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
-  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0, ns));
   // q normalised power iterations (steps 7-11)
   const int ng = project_grid(v, p->nsm);
   const int npairs = l * (l + 1) / 2;
@@ -340,7 +351,7 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
       RCP_TRY(launch_project_f64(T, dt, v, l, p->Y, W, p->gpart, ng, s));
     }
     RCP_TRY(launch_reduce(p->gpart, ng, npairs, p->G, p->tmp, p->tmp_elems, s));
-    RCP_TRY(launch_chol(p->G, l, p->RWinv, p->dstate, (double)v.J, -1, 0, s));
+    RCP_TRY(launch_chol(p->G, l, p->RWinv, p->dstate, (double)v.J, -1, 0, s, ns));
     // Y = T_(n) W R_W^{-1} (step 10), then Q = qr(Y) (step 8 of the next iteration / step 12)
     {
       Span sp(p, RCP_KT_APPLY, mode);
@@ -349,7 +360,7 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
     RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
     RCP_TRY(launch_trmm(p->Y, v.I, l, p->RWinv, p->Y, p->dstate, 0, s));
     RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
-                          it == p->cfg.power_iters - 1));
+                          it == p->cfg.power_iters - 1, ns));
   }
   return RCP_OK;
 }
@@ -360,6 +371,7 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
 // upper-triangular right factor, which the QR of Y removes.
 rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
   cudaStream_t s = p->stream;
+  const bool ns = (p->cfg.flags & RCP_FLAG_NO_SHIFT) != 0;
   const int n0 = mode - 1;
   const ModeView v = p->view[n0];
   const int l = p->l[n0];
@@ -379,7 +391,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
     const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
-    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0, ns));
     for (int it = 0; it < p->cfg.power_iters; ++it) {
       RCP_TRY(launch_q_to_qt32(p->Y, v.I, l, p->QT32, s));
       {
@@ -393,7 +405,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
       }
       RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
       RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
-                          it == p->cfg.power_iters - 1));
+                          it == p->cfg.power_iters - 1, ns));
     }
     return RCP_OK;
   }
@@ -409,7 +421,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
-  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0));
+  RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0, ns));
   const int ng = project_grid(v, p->nsm);
   for (int it = 0; it < p->cfg.power_iters; ++it) {
     {
@@ -422,7 +434,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     }
     RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
     RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
-                          it == p->cfg.power_iters - 1));
+                          it == p->cfg.power_iters - 1, ns));
   }
   return RCP_OK;
 }
@@ -522,7 +534,10 @@ rcp_status rcp_als(rcp_plan_t p, double* lambda_host, double* fit_host, int32_t*
   {
     Span sp(p, RCP_KT_ALS, 0);
     const bool f32 = p->prec == RCP_PREC_MIXED;
-    if (als_persistent_fits(p, f32)) {
+    if (f32 && als_cluster_fits(p)) {
+      // small core: one thread-block cluster runs every sweep
+      RCP_TRY(launch_als_cluster(p, (const float*)mode_output(p, p->N), s));
+    } else if (als_persistent_fits(p, f32)) {
       // one cooperative kernel runs every sweep (FP32 MTTKRP in the mixed form)
       RCP_TRY(cudaMemsetAsync(p->bar, 0, 4 * sizeof(unsigned), s));
       RCP_TRY(cudaMemsetAsync(p->abort_flag, 0, 4 * sizeof(int), s));

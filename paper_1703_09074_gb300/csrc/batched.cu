@@ -568,9 +568,10 @@ rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
     if (c.power_iters != cfgs[0].power_iters || c.power_iters < 0) return RCP_EINVAL;
     if (c.rank < 1 || c.rank > 32 || c.oversample < 0 || c.max_iters < 1 || !(c.tol >= 0.0))
       return RCP_EINVAL;
-    int64_t cur[kMaxN];
+    int64_t cur[kMaxN], total = 1;
     for (int n = 0; n < N; ++n) {
       if (c.dims[n] < 1 || c.dims[n] > (1LL << 24)) return RCP_EINVAL;
+      if (!mul_elems(total, c.dims[n], &total)) return RCP_EINVAL;  // no int64 overflow below
       cur[n] = c.dims[n];
     }
     for (int n = 0; n < N; ++n) {
@@ -835,6 +836,25 @@ rcp_status rcp_batched_export(rcp_batched_t p, float* Bpad_dev, int32_t* meta_de
   RCPB_TRY(launch_ws_gather(p->ws_items, C, Bpad_dev, meta_dev, s));
   RCPB_TRY(launch_ws_canon(Bpad_dev, meta_dev, C, x_dev, U_dev, s));
   RCPB_TRY(launch_ws_targets(p->ws_items, U_dev, C, t_dev, s));
+  return RCP_OK;
+}
+
+rcp_status rcp_batched_intermediates(rcp_batched_t p, int32_t index, double* const* Q_dev,
+                                     double* B_dev, double* const* At_dev, double* lambda_t_dev) {
+  if (!p || index < 0 || index >= p->count) return RCP_EINVAL;
+  const auto& t = p->t[index];
+  cudaStream_t s = p->stream;
+  for (int n = 0; n < p->N; ++n) {
+    if (Q_dev && Q_dev[n])
+      RCPB_TRY(cudaMemcpyAsync(Q_dev[n], t.Q[n], sizeof(double) * t.dims[n] * t.l[n],
+                               cudaMemcpyDeviceToDevice, s));
+    if (At_dev && At_dev[n])
+      RCPB_TRY(cudaMemcpyAsync(At_dev[n], t.At[n], sizeof(double) * t.l[n] * t.R,
+                               cudaMemcpyDeviceToDevice, s));
+  }
+  if (B_dev) RCPB_TRY(launch_to_f64(t.buf[(p->N - 1) % 2], RCP_DTYPE_F32, t.core, B_dev, s));
+  if (lambda_t_dev)
+    RCPB_TRY(cudaMemcpyAsync(lambda_t_dev, t.lam_t, sizeof(double) * t.R, cudaMemcpyDeviceToDevice, s));
   return RCP_OK;
 }
 

@@ -67,10 +67,12 @@ __global__ void k_gram_pairs(const double* __restrict__ Y, int64_t I, int l,
 // shift_rows: the row count m entering the shifted-CholeskyQR3 shift; 0 forbids the shift.
 // round < 0: unconditional; round == 2: only when an earlier round was shifted.
 // after32 != 0: runs only when the FP32 attempt of the same round failed.
+// no_shift != 0: a Gram that would need the shift (a pivot at or below it)
+// records RCP_ESINGULAR instead of being factored with it.
 __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int l,
                                               double* __restrict__ Rinv, DevState* st,
                                               double shift_rows, int round, int als_mode,
-                                              int after32) {
+                                              int after32, int no_shift) {
   __shared__ double S[kMaxL][kMaxL + 1];
   __shared__ double tdiag[kMaxL];
   __shared__ double rowb[2][kMaxL];
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ Gp, int
     }
     const double floor_ = (attempt == 0 && shift_rows > 0.0) ? shift : 0.0;
     ok = chol_elim<double>(S, tdiag, rowb, tb, l, floor_, &fail_sh);
-    if (!ok && attempt == 0 && shift_rows > 0.0) {
+    if (!ok && attempt == 0 && shift_rows > 0.0 && !no_shift) {
       if (tid == 0) {
         atomicOr(&st->info, als_mode ? RCP_INFO_ALS_REGULARISED : RCP_INFO_SHIFTED_QR);
         if (round == 0) st->extra_round = 1;
@@ -267,9 +269,9 @@ cudaError_t launch_gram(const double* Y, int64_t I, int l, double* Gp, cudaStrea
 }
 
 cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, double shift_rows,
-                        int round, int als_mode, cudaStream_t s) {
+                        int round, int als_mode, cudaStream_t s, bool no_shift) {
   count_launches(1);
-  k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode, 0);
+  k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, shift_rows, round, als_mode, 0, no_shift ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -286,7 +288,7 @@ cudaError_t launch_trmm(const double* Y, int64_t I, int l, const double* Rinv, d
 }
 
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s, bool final_qr) {
+                          cudaStream_t s, bool final_qr, bool no_shift) {
   // round 0 (shift allowed), round 1, round 2 (only after a shifted round); in place on Y.
   // A normalisation inside the power iterations needs a well-conditioned basis
   // of the same span, not an orthonormal one: one round (CholeskyQR) serves it,
@@ -299,13 +301,13 @@ cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv,
     if (e != cudaSuccess) return e;
     if (round == 0 && l <= kMaxL) {
       count_launches(2);
-      k_chol32<<<1, 256, 0, s>>>(Gp, l, Rinv, st, round, final_qr ? 0 : 1);
+      k_chol32<<<1, 256, 0, s>>>(Gp, l, Rinv, st, round, (final_qr || no_shift) ? 0 : 1);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, (double)I, round, 0, 1);
+      k_chol<<<1, 256, 0, s>>>(Gp, l, Rinv, st, (double)I, round, 0, 1, no_shift ? 1 : 0);
       e = cudaGetLastError();
     } else {
-      e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s);
+      e = launch_chol(Gp, l, Rinv, st, round == 0 ? (double)I : 0.0, round, 0, s, no_shift);
     }
     if (e != cudaSuccess) return e;
     e = launch_trmm(Y, I, l, Rinv, Y, st, round == 2, s);

@@ -91,7 +91,8 @@ __device__ __forceinline__ double dw_to_double(dwf x) { return (double)x.hi + (d
 // On success V^{-1} is written in FP64 to Zd (row pitch 32), which aliases the
 // copy not holding the result, and true is returned.  false (returned by every
 // thread at the same point) means that the trace of V is outside
-// (1e-30, 1e30) or that a pivot fell to R 2^-44 trace(V) or below.
+// (1e-18, 1e18), that a pivot fell to R 2^-44 trace(V) or below, or that an
+// element of the inverse is not finite.
 template <int NT, int KE>
 __device__ bool cta_gj_inverse_dw_k(int R, float2* A0, float2* A1, double** Zd) {
   const int tid = threadIdx.x, lane = tid & 31;
@@ -113,7 +114,10 @@ __device__ bool cta_gj_inverse_dw_k(int R, float2* A0, float2* A1, double** Zd) 
     col[u] = own[u] ? e - (e / R) * R : 0;
   }
   __syncthreads();
-  if (!(tr > 1e-30f && tr < 1e30f)) return false;
+  // |v_ij| <= trace for SPD V: with the trace inside (1e-18, 1e18) the FP32
+  // products a_ik a_kj of the first steps stay finite and the pivot floor
+  // below stays a normal number (rcp.approx.ftz flushes subnormals)
+  if (!(tr > 1e-18f && tr < 1e18f)) return false;
   const float floor_ = (float)R * 5.684342e-14f * tr;
   const float2* cur = A0;
   float2* nxt = A1;
@@ -145,12 +149,17 @@ __device__ bool cta_gj_inverse_dw_k(int R, float2* A0, float2* A1, double** Zd) 
     nxt = t;
   }
   double* z = (double*)nxt;
+  int bad = 0;
   for (int e = tid; e < R * R; e += NT) {
     const int i = e / R, c = e - i * R;
     const float2 v = cur[i * 64 + R + c];
-    z[i * 32 + c] = dw_to_double({v.x, v.y});
+    const double d = dw_to_double({v.x, v.y});
+    bad |= !isfinite(d);
+    z[i * 32 + c] = d;
   }
-  __syncthreads();
+  // an element growth that overflowed FP32 on the way (a nearly singular V whose
+  // pivots still passed the floor) sends the caller to its FP64 path
+  if (__syncthreads_or(bad)) return false;
   *Zd = z;
   return true;
 }

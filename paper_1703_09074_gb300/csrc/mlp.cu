@@ -479,7 +479,12 @@ rcp_status rcp_mlp_train_step(rcp_mlp_t p, const float* x_dev, const float* t_de
   cudaStream_t s = p->stream;
   rcp_status st = mlp_forward_enqueue(p, x_dev, count, true, s);
   if (st != RCP_OK) return st;
-  // rows >= count keep dY = 0 (zeroed at creation; the loss writes only rows < count)
+  // the loss writes dY rows < count only; rows >= count are cleared here, since an
+  // earlier step with a larger count leaves its gradient in them and the forward
+  // pass gives zero input rows nonzero (bias) activations that would carry it on
+  if (count < p->batch)
+    MLP_TRY(cudaMemsetAsync(p->dY + (int64_t)count * kMlpOut, 0,
+                            (size_t)(p->batch - count) * kMlpOut * 4, s));
   MLP_TRY(launch_ws_loss(p->Y, t_dev, meta_dev, count, 1.0f / (float)count, p->dY, p->loss, s));
   st = mlp_backward_enqueue(p, p->dY, s);
   if (st != RCP_OK) return st;

@@ -11,7 +11,7 @@
 
 namespace rcp {
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
-                          cudaStream_t s, bool final_qr);
+                          cudaStream_t s, bool final_qr, bool no_shift = false);
 }  // namespace rcp
 
 namespace {
@@ -57,9 +57,11 @@ extern "C" rcp_status rcp_sketch_mode1_static(const void* X_dev, int32_t in_dtyp
   if (in_dtype != RCP_DTYPE_F64 && in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
   if (ndim < 2 || ndim > kMaxN || rank < 1 || rank > RCP_MAX_RANK || oversample < 0)
     return RCP_EINVAL;
-  int64_t J = 1;
+  int64_t J = 1, total = 1;
   for (int n = 0; n < ndim; ++n) {
     if (dims[n] < 1 || dims[n] > (1LL << 40)) return RCP_EINVAL;
+    // the element count must not overflow (a wrapped J would size the sweep wrongly)
+    if (!mul_elems(total, dims[n], &total)) return RCP_EINVAL;
     if (n > 0) J *= dims[n];
   }
   const int64_t I = dims[0];

@@ -179,6 +179,19 @@ __device__ __forceinline__ float4 normal_quad_f32(uint64_t seed, uint32_t stream
 int64_t& launch_counter();
 inline void count_launches(int k) { launch_counter() += k; }
 
+// Largest element count of an input tensor (product of its dims) accepted by the
+// entry points: 2^48, far beyond any device memory, so that every product of
+// dims formed from accepted sizes stays inside int64.
+constexpr int64_t kMaxElems = 1LL << 48;
+
+// *out = a * b when the product is at most kMaxElems (a, b >= 1); false otherwise.
+inline bool mul_elems(int64_t a, int64_t b, int64_t* out) {
+  int64_t r = 0;
+  if (__builtin_mul_overflow(a, b, &r) || r > kMaxElems) return false;
+  *out = r;
+  return true;
+}
+
 constexpr uint32_t kPurposeSketch = 0;
 constexpr uint32_t kPurposeAlsInit = 1;
 
@@ -206,6 +219,7 @@ struct PersArgs {
   int max_iters;
   int user_init;
   int direct64;          // solve with the FP64 Cholesky factor only (no FP32 factor + refinement)
+  long long budget;      // clock cycles per grid-barrier wait (0: the default)
 };
 
 // ---------------------------------------------------------------- batched form
@@ -294,6 +308,8 @@ cudaError_t launch_als_sweep(rcp_plan_s* p, int mode0, cudaStream_t s);
 cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lambda_dev,
                                cudaStream_t s);
 bool als_persistent_fits(const rcp_plan_s* p, bool f32);
+bool als_cluster_fits(const rcp_plan_s* p);
+cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, cudaStream_t s);
 size_t als_smem_bytes_f32(int N, int R, const int* l);
 cudaError_t prepare_als_batched(size_t smem);
 cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s);

@@ -1,0 +1,150 @@
+"""The precision form against the oracle, step by step, on the 4-way, flow-like
+and batched workloads (needs a GB300).
+
+The oracle runs on the same tensors with the same reduced-precision Gaussian
+stream (evaluated in FP64), so the two sides differ only by the split-TF32
+products and FP32 storage of the GPU's sweeps.  What is compared, and why the
+bounds hold:
+
+* bases: the R smallest principal angles between span(Q_n) of the GPU and of
+  the oracle (the signal directions).  Each sweep's products keep about 21 bits
+  (error <= 2^-20 |x||y|) with FP32 accumulation; the signal directions of the
+  sketch move by that error over the relative gap sigma_R / sigma_1 <= 1e2 here,
+  so sin <= 1e-3 holds with a wide margin;
+* the compressed tensor B, mapped into the oracle's coordinates
+  (B_gpu x_n (Q_n,oracle^T Q_n,gpu)).  The trailing (noise) directions of the
+  l_n-dimensional spans are fixed by the sketch itself and rotate by more than
+  the signal directions (measured up to a few 1e-2 on these inputs), so the
+  bound is taken from the measured spans: B_gpu = X x_n Q_n,gpu^T, and
+  telescoping over the modes gives |B_gpu' - B_oracle| <= sum_n
+  |P_n,gpu - P_n,oracle|_2 |X| = sum_n sin(theta_n,max) |X|, plus the FP32
+  storage of the intermediate tensors (allowed 1e-5 relative);
+* the CP model on B, [[lambda; Atilde_1, ..., Atilde_N]], in the same
+  coordinates: both sides start ALS from the same seeded factors and run the
+  same sweeps, so their Kruskal tensors agree to 1e-2 relative (a bound on the
+  drift of two ALS trajectories whose cores differ by the amount above);
+* the final relative error |X - Xhat| / |X| within 1e-3 relative ("equal fit").
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def _sines(Qg, Qo):
+    """Sines of the principal angles between span(Qg) and span(Qo), smallest first."""
+    c = np.clip(np.linalg.svd(Qo.T @ Qg, compute_uv=False), 0.0, 1.0)
+    return np.sqrt(np.maximum(1.0 - c * c, 0.0))
+
+
+def _to_oracle_basis(B, Qg, Qo):
+    T = np.asarray(B, dtype=np.float64)
+    for n, (qg, qo) in enumerate(zip(Qg, Qo), start=1):
+        T = tensor.ttm(T, qo.T @ qg, n)
+    return T
+
+
+def _compare(R, Qg, Bg, Atg, lamg, relg, o):
+    full = []
+    for n, (qg, qo) in enumerate(zip(Qg, o["Q"]), start=1):
+        assert qg.shape == qo.shape, n
+        s = _sines(qg, qo)
+        assert s[:R].max() < 1e-3, (n, s[:R].max())
+        full.append(s.max())
+    Bo = o["B"]
+    dB = np.linalg.norm(_to_oracle_basis(Bg, Qg, o["Q"]) - Bo)
+    assert dB <= sum(full) * np.sqrt(o["normX2"]) + 1e-5 * np.linalg.norm(Bo), (dB, full)
+    Mg = [qo.T @ qg @ a for qg, qo, a in zip(Qg, o["Q"], Atg)]
+    Kg = tensor.kruskal(lamg, Mg)
+    Ko = tensor.kruskal(o["lam_tilde"], o["A_tilde"])
+    dK = np.linalg.norm(Kg - Ko) / np.linalg.norm(Ko)
+    assert dK < 1e-2, dK
+    assert relg == pytest.approx(o["rel_err_identity"], rel=1e-3)
+
+
+def _run_plan(w, seed=0, tol=None, max_iters=None):
+    from paper_1703_09074_gb300 import Plan
+    X = torch.from_numpy(w.kolda).cuda()
+    with Plan(w.dims, w.rank, w.oversample, w.power_iters, w.tol if tol is None else tol,
+              w.max_iters if max_iters is None else max_iters, seed=seed,
+              in_dtype=torch.float32, precision="mixed") as p:
+        Qs = []
+        for n in range(1, len(w.dims) + 1):
+            Qs.append(p.sketch(X, n, return_basis=True).cpu().numpy())
+            p.compress(X, n)
+        B = p.core().cpu().numpy().T
+        p.als(sync=False)
+        At, lam_t = p.compressed_factors()
+        res = p.result()
+    del X
+    torch.cuda.empty_cache()
+    assert res["device_status"] == 0, res
+    return Qs, B, [a.cpu().numpy() for a in At], lam_t.cpu().numpy(), res
+
+
+@pytest.mark.slow
+def test_4way_full_size_matches_oracle_step_by_step():
+    # 128 x 128 x 128 x 64 FP32 (512 MB), R = 32, p = 16, q = 1, 50 ALS sweeps
+    w = synth.config("c3_128cubed_x64_f32")
+    Qg, Bg, Atg, lamg, res = _run_plan(w)
+    o = oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, 0,
+                           omega="f32")
+    _compare(w.rank, Qg, Bg, Atg, lamg, res["rel_err"], o)
+
+
+def test_flowlike_reduced_matches_oracle_step_by_step():
+    # the flow-like recipe at 256 x 512 x 400: mode 1 on the tensor cores over
+    # 204800 columns (many chunks per CTA), l = 20, q = 2, later modes on FP32 sweeps
+    w = synth.cp_tensor((256, 512, 400), 10, seed=0, kind="flow", snr_db=20.0, dtype="f32",
+                        p=10, q=2)
+    Qg, Bg, Atg, lamg, res = _run_plan(w)
+    o = oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, 0,
+                           omega="f32")
+    _compare(w.rank, Qg, Bg, Atg, lamg, res["rel_err"], o)
+
+
+def test_batched_matches_oracle_per_tensor_step_by_step():
+    from paper_1703_09074_gb300 import BatchedPlan
+    # 16 tensors of the batched workload's distribution (I_n ~ U{32..256}, R ~ U{3..16})
+    ws = synth.batch(16, seed=9, p=8, q=1)
+    probs = [dict(dims=w.dims, rank=w.rank, oversample=8, power_iters=1, tol=1e-10,
+                  max_iters=50, seed=40 + b) for b, w in enumerate(ws)]
+    Xs = [torch.from_numpy(w.kolda).cuda() for w in ws]
+    with BatchedPlan(probs) as bp:
+        bp.run(Xs)
+        got = []
+        for b in range(len(ws)):
+            Q, B, At, lam_t = bp.intermediates(b)
+            _A, _lam, r = bp.result(b)
+            got.append(([q.cpu().numpy() for q in Q], B.cpu().numpy().T,
+                        [a.cpu().numpy() for a in At], lam_t.cpu().numpy(), r))
+    for b, (w, pr) in enumerate(zip(ws, probs)):
+        Qg, Bg, Atg, lamg, r = got[b]
+        assert r["device_status"] == 0, (b, r)
+        o = oracle.rcp.rcp_als(w.X, w.rank, 8, 1, 1e-10, 50, pr["seed"], omega="f32")
+        _compare(w.rank, Qg, Bg, Atg, lamg, r["rel_err"], o)
+
+
+@pytest.mark.parametrize("dims,R,p,q", [
+    ((60, 50, 40), 3, 4, 1),          # l = 7: a cluster of 7 CTAs, one row each, 8 accumulators
+    ((80, 70, 60), 12, 8, 1),         # l = 20, 16 accumulators
+    ((90, 64, 50), 20, 10, 2),        # l = 30, 24 accumulators (the 400^3 workload's shape class)
+    ((100, 64, 48), 28, 4, 1),        # l = 32, 32 accumulators
+    ((40, 30, 20, 16), 6, 6, 1),      # 4-way core 12^4: two remaining modes per lane index
+    ((200, 150), 5, 5, 1),            # 2-way: no remaining modes
+])
+def test_small_core_als_matches_oracle(dims, R, p, q):
+    # these cores run ALS in the one-cluster kernel (l_n <= 32, R <= 32); a fixed
+    # number of sweeps (tol = 0) keeps both sides on the same iteration count
+    w = synth.cp_tensor(dims, R, seed=21, congruence=0.3, snr_db=20.0, dtype="f32", p=p, q=q)
+    Qg, Bg, Atg, lamg, res = _run_plan(w, seed=4, tol=0.0, max_iters=30)
+    o = oracle.rcp.rcp_als(w.X, R, p, q, 0.0, 30, 4, omega="f32")
+    assert res["iters"] == 30
+    _compare(R, Qg, Bg, Atg, lamg, res["rel_err"], o)
+    assert res["fit"] == pytest.approx(o["fit"], abs=1e-5)

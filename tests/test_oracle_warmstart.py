@@ -87,6 +87,24 @@ def test_adam_first_step_closed_form():
     assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
 
 
+def test_adam_two_steps_by_hand():
+    # one parameter p0 = 1, gradients 1/2 then -1/5, lr = 1/10, eps = 0 (Kingma & Ba,
+    # Algorithm 1).  By hand: m1 = 1/20, v1 = 1/4000, bias-corrected 1/2 and 1/4,
+    # p1 = 9/10; m2 = 1/40, v2 = 1159/4000000, bias-corrected by 1 - 0.9^2 and
+    # 1 - 0.999^2 to 5/38 and 1159/7996, p2 = 9/10 - (1/10)(5/38)/sqrt(1159/7996).
+    # A correction that used t = 1 again, or none, fails the second step.
+    p1, m1, v1 = ws.adam(np.array([1.0]), np.zeros(1), np.zeros(1), np.array([0.5]), 1, 0.1,
+                         eps=0.0)
+    assert m1[0] == pytest.approx(1 / 20, abs=1e-16)
+    assert v1[0] == pytest.approx(1 / 4000, abs=1e-18)
+    assert p1[0] == pytest.approx(0.9, abs=1e-15)
+    p2, m2, v2 = ws.adam(p1, m1, v1, np.array([-0.2]), 2, 0.1, eps=0.0)
+    assert m2[0] == pytest.approx(1 / 40, abs=1e-16)
+    assert v2[0] == pytest.approx(1159 / 4000000, abs=1e-18)
+    assert p2[0] == pytest.approx(0.9 - 0.1 * (5 / 38) / np.sqrt(1159 / 7996), abs=1e-15)
+    assert p2[0] == pytest.approx(0.8654394152087408, abs=1e-14)
+
+
 def _sample(rng, l=(9, 8, 7), R=5):
     y = rng.standard_normal(ws.OUT) * 0.3
     t = np.zeros((3, ws.LPAD, ws.RPAD))
