@@ -88,16 +88,23 @@ enum {
 /* Flags for rcp_config.flags. */
 enum {
   RCP_FLAG_HOST_STAGING = 1,   /* reserve device buffers so rcp_decompose_host can run  */
-  RCP_FLAG_NO_SHIFT = 2        /* no shifted-CholeskyQR fallback: a sketch whose Gram
+  RCP_FLAG_NO_SHIFT = 2,       /* no shifted-CholeskyQR fallback: a sketch whose Gram
                                   needs the shift (numerically rank-deficient Y) sets
                                   RCP_ESINGULAR instead of RCP_INFO_SHIFTED_QR        */
+  RCP_FLAG_MODE_OVERSAMPLE = 4, /* use rcp_config.mode_oversample[n-1] as p for mode n
+                                  (the remark after Algorithm 1)                       */
+  RCP_FLAG_LU_NORM = 8         /* normalise the power iterations with the pivoted LU
+                                  factor of Algorithm 1 steps 8-9 (P L of Y = P L U)
+                                  instead of CholeskyQR: the same spans, a different
+                                  basis until the final QR of step 12                  */
 };
 
 /* Initial factors of the stage-2 solver on B (Algorithm 2 step 2, Algorithm 3
  * step 2). */
 typedef enum {
   RCP_INIT_RANDN = 0,   /* seeded N(0,1) factors for modes 2..N (the default)       */
-  RCP_INIT_LEARNED = 1, /* reserved for the warm-start network (batched form only)  */
+  RCP_INIT_LEARNED = 1, /* the warm-start network's factors (rcp_set_warm_start; the
+                           precision form, 3-way, l_n <= 24, R <= 16), else seeded   */
   RCP_INIT_EIG = 2      /* the leading R eigenvectors of B_(n) B_(n)^T, n = 2..N     */
 } rcp_init;
 
@@ -125,6 +132,10 @@ typedef struct {
   int32_t flags;                 /* RCP_FLAG_* bits                                  */
   int32_t init;                  /* rcp_init (0 = seeded N(0,1))                     */
   int32_t solver;                /* rcp_solver (0 = ALS)                             */
+  int32_t skip_modes;            /* bit n-1 set: mode n is not compressed (Q_n = I,
+                                    l_n = I_n <= RCP_MAX_L); the remark after
+                                    Algorithm 1 lets the user choose the modes     */
+  int32_t mode_oversample[RCP_MAX_NDIM]; /* p_n per mode with RCP_FLAG_MODE_OVERSAMPLE */
   int64_t wait_budget;           /* clock cycles each grid-barrier wait of the
                                     multi-CTA ALS kernel may spin before it records
                                     RCP_ETIMEOUT and the kernel leaves; 0 = the
@@ -183,10 +194,18 @@ rcp_status rcp_compress(rcp_plan_t plan, const void* X, int32_t mode);
  * once that copy completes.  Applies to the next rcp_als call only. */
 rcp_status rcp_als_init(rcp_plan_t plan, const double* const* At_dev);
 
-/* Algorithm 2 steps (3)-(11) on the compressed tensor B: ALS sweeps over
- * modes 1..N, each solving A_n = B_(n) (KR of the others) (Hadamard product of
- * their Grams)^-1 and normalising columns (lambda from mode N), until the fit
- * change falls below tol or max_iters sweeps have run.
+/* The stage-2 solver on the compressed tensor B, from the initial factors that
+ * rcp_config.init selects (seeded N(0,1), or Algorithm 2 step 2's eigenvectors
+ * of B_(n) B_(n)^T; rcp_als_init overrides both for one call).
+ * RCP_SOLVER_ALS -- Algorithm 2 steps (3)-(11): ALS sweeps over modes 1..N,
+ *   each solving A_n = B_(n) (KR of the others) (Hadamard product of their
+ *   Grams)^-1 and normalising columns (lambda from mode N), until the fit
+ *   change falls below tol or max_iters sweeps have run.
+ * RCP_SOLVER_BCD -- Algorithm 3 steps (3)-(15): for r = 1..R, rank-one sweeps
+ *   a_n = Y_(n) (KR of the other a_m) / prod (a_m^T a_m) on the residual Y of
+ *   the components already found (never formed: Section 3.2.2's residual-free
+ *   MTTKRP), each component until its fit changes by less than tol or after
+ *   max_iters sweeps; iters_host then counts the sweeps of all components.
  * Requires rcp_compress(N) (else RCP_EORDER).
  * lambda_host (R doubles), fit_host, iters_host: optional host outputs; when
  * any is non-NULL the call synchronises the stream and returns the device
@@ -463,6 +482,17 @@ rcp_status rcp_batched_export(rcp_batched_t plan, float* Bpad_dev, int32_t* meta
  * RCP_INFO_LEARNED_INIT.  The network's batch must be >= the plan's count and
  * its stream is not used by the plan.  Synchronises. */
 rcp_status rcp_batched_set_warm_start(rcp_batched_t plan, rcp_mlp_t net);
+
+/* Start the stage-2 solver of a plan whose rcp_config.init is RCP_INIT_LEARNED
+ * from the warm-start network's factors (the batched form's data path for the
+ * plan's one compressed tensor: canonical basis, a forward pass of `net`,
+ * A_n = U_n (E + Y_n)); a prediction with a non-finite or zero column falls back
+ * to the seeded start.  The plan must be of the precision form, 3-way, with
+ * l_n <= 24 and R <= 16 (else RCP_EINVAL); net = NULL detaches the network
+ * (seeded start).  The network runs on the plan's stream and must stay alive
+ * while the plan uses it.  The first call allocates the plan's warm-start
+ * buffers and synchronises. */
+rcp_status rcp_set_warm_start(rcp_plan_t plan, rcp_mlp_t net);
 
 /* Synthetic CP tensor for training and benchmarking (no counterpart in the
  * method): X[i_1..i_N] = sum_r lambda_r prod_n A_n[i_n, r] + sigma z, z ~ N(0, 1)

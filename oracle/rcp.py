@@ -60,31 +60,53 @@ def gaussian_test_matrix(seed, n, J, l, omega="f64"):
     return philox.gaussian_matrix(seed, n, philox.PURPOSE_SKETCH, J, l)
 
 
-def range_finder(T, n, l, q, seed, omega="f64"):
+def lu_psych(Y):
+    """[L, ~] = lu(Y) of Algorithm 1 steps 8-9: the permuted unit lower-trapezoidal
+    factor P L of the partial-pivoting LU Y = P L U (LAPACK getrf via scipy), whose
+    columns span the same space as Y's."""
+    from scipy.linalg import lu
+    PL, _U = lu(np.asarray(Y, dtype=np.float64), permute_l=True)
+    return PL
+
+
+def range_finder(T, n, l, q, seed, omega="f64", normalize="qr"):
     """Basis Q_n for mode n of the current tensor T (Algorithm 1 steps 4-12).
 
-    Y = T_(n) Omega; q times: Q = qr+(Y), Z = qr+(T_(n)^T Q), Y = T_(n) Z;
-    then Q_n = qr+(Y).
+    Y = T_(n) Omega; q times: Q = norm(Y), Z = norm(T_(n)^T Q), Y = T_(n) Z;
+    then Q_n = qr+(Y).  norm is qr+ (the default reading) or, with
+    normalize="lu", the pivoted-LU factor of steps 8-9 as the paper prints them.
     """
     Tn = unfold(T, n)
     J = Tn.shape[1]
     Omega = gaussian_test_matrix(seed, n, J, l, omega)
     Y = Tn @ Omega
     for _ in range(q):
-        Q, _r = qr_pos(Y)
-        Z, _r = qr_pos(Tn.T @ Q)
+        if normalize == "lu":
+            Q = lu_psych(Y)
+            Z = lu_psych(Tn.T @ Q)
+        else:
+            Q, _r = qr_pos(Y)
+            Z, _r = qr_pos(Tn.T @ Q)
         Y = Tn @ Z
     Qn, _r = qr_pos(Y)
     return Qn
 
 
-def compress(X, R, p, q, seed, omega="f64"):
-    """Algorithm 1: returns the compressed tensor B and the bases [Q_1, ..., Q_N]."""
+def compress(X, R, p, q, seed, omega="f64", normalize="qr", p_modes=None, skip=()):
+    """Algorithm 1: returns the compressed tensor B and the bases [Q_1, ..., Q_N].
+
+    Options of the remark after Algorithm 1: p_modes[n - 1] replaces p for
+    mode n, and modes listed in ``skip`` (1-based) are not compressed
+    (Q_n = I, the tensor keeps I_n in that mode)."""
     T = np.asarray(X, dtype=np.float64)
     Qs = []
     for n in range(1, T.ndim + 1):
-        l = sketch_width(R, p, T.shape, n)
-        Qn = range_finder(T, n, l, q, seed, omega)
+        if n in skip:
+            Qs.append(np.eye(T.shape[n - 1]))
+            continue
+        pn = p if p_modes is None else p_modes[n - 1]
+        l = sketch_width(R, pn, T.shape, n)
+        Qn = range_finder(T, n, l, q, seed, omega, normalize)
         Qs.append(Qn)
         T = ttm(T, Qn.T, n)
     return T, Qs
@@ -244,12 +266,14 @@ def back_project(Qs, lam, factors):
     return lam, out
 
 
-def rcp_als(X, R, p, q, tol, max_iters, seed, init=None, omega="f64", solver="als"):
+def rcp_als(X, R, p, q, tol, max_iters, seed, init=None, omega="f64", solver="als",
+            **compress_options):
     """The whole method: compress, ALS (Algorithm 2) or BCD (Algorithm 3) on B,
     recover.  ``init`` is a list of initial factors, "randn" (the default) or
-    "eig" (eigenvectors of B_(n) B_(n)^T).  Returns a dict of every intermediate."""
+    "eig" (eigenvectors of B_(n) B_(n)^T); ``compress_options`` go to compress
+    (normalize, p_modes, skip).  Returns a dict of every intermediate."""
     X = np.asarray(X, dtype=np.float64)
-    B, Qs = compress(X, R, p, q, seed, omega)
+    B, Qs = compress(X, R, p, q, seed, omega, **compress_options)
     if isinstance(init, str):
         init = initial_factors(B, R, seed, init)
     stage2 = cp_bcd if solver == "bcd" else cp_als

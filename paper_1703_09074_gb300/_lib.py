@@ -16,7 +16,7 @@ RCP_OK, RCP_EINVAL, RCP_ENOMEM, RCP_ECUDA, RCP_ESINGULAR, RCP_ENAN, RCP_ETIMEOUT
     RCP_EORDER, RCP_ENOTCONV = range(9)
 RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
 RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
-RCP_FLAG_HOST_STAGING, RCP_FLAG_NO_SHIFT = 1, 2
+RCP_FLAG_HOST_STAGING, RCP_FLAG_NO_SHIFT, RCP_FLAG_MODE_OVERSAMPLE, RCP_FLAG_LU_NORM = 1, 2, 4, 8
 RCP_INIT_RANDN, RCP_INIT_LEARNED, RCP_INIT_EIG = 0, 1, 2
 RCP_SOLVER_ALS, RCP_SOLVER_BCD = 0, 1
 RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED, RCP_INFO_LEARNED_INIT = 1, 2, 4
@@ -39,6 +39,8 @@ class RcpConfig(ctypes.Structure):
                 ("flags", ctypes.c_int32),
                 ("init", ctypes.c_int32),
                 ("solver", ctypes.c_int32),
+                ("skip_modes", ctypes.c_int32),
+                ("mode_oversample", ctypes.c_int32 * MAX_NDIM),
                 ("wait_budget", ctypes.c_int64)]
 
 
@@ -99,6 +101,7 @@ SIGNATURES = {
     "rcp_mlp_train_step": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_float, P]),
     "rcp_batched_export": (ctypes.c_int, [P, P, P, P, P, P]),
     "rcp_batched_set_warm_start": (ctypes.c_int, [P, P]),
+    "rcp_set_warm_start": (ctypes.c_int, [P, P]),
     "rcp_synth_cp": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                     ctypes.POINTER(P), P, ctypes.c_float, ctypes.c_uint64, P, P]),
     "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,

@@ -15,7 +15,7 @@ from ._lib import RcpConfig, RcpResult, check
 
 _DT = {torch.float32: _lib.RCP_DTYPE_F32, torch.float64: _lib.RCP_DTYPE_F64}
 _PREC = {"f64": _lib.RCP_PREC_F64, "mixed": _lib.RCP_PREC_MIXED}
-_INIT = {"randn": _lib.RCP_INIT_RANDN, "eig": _lib.RCP_INIT_EIG}
+_INIT = {"randn": _lib.RCP_INIT_RANDN, "eig": _lib.RCP_INIT_EIG, "learned": _lib.RCP_INIT_LEARNED}
 _SOLVER = {"als": _lib.RCP_SOLVER_ALS, "bcd": _lib.RCP_SOLVER_BCD}
 
 
@@ -31,7 +31,8 @@ class Plan:
 
     def __init__(self, dims, rank, oversample=10, power_iters=2, tol=1e-10, max_iters=50,
                  seed=0, in_dtype=torch.float32, precision="f64", host_staging=False,
-                 stream=None, init="randn", solver="als", wait_budget=0, no_shift=False):
+                 stream=None, init="randn", solver="als", wait_budget=0, no_shift=False,
+                 skip_modes=(), mode_oversample=None, lu_norm=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.N = len(self.dims)
@@ -50,7 +51,14 @@ class Plan:
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         cfg.precision = _PREC[precision]
         cfg.flags = ((_lib.RCP_FLAG_HOST_STAGING if host_staging else 0) |
-                     (_lib.RCP_FLAG_NO_SHIFT if no_shift else 0))
+                     (_lib.RCP_FLAG_NO_SHIFT if no_shift else 0) |
+                     (_lib.RCP_FLAG_LU_NORM if lu_norm else 0) |
+                     (_lib.RCP_FLAG_MODE_OVERSAMPLE if mode_oversample is not None else 0))
+        for n in skip_modes:   # 1-based modes left uncompressed
+            cfg.skip_modes |= 1 << (int(n) - 1)
+        if mode_oversample is not None:
+            for k, pn in enumerate(mode_oversample):
+                cfg.mode_oversample[k] = int(pn)
         cfg.init = _INIT[init]
         cfg.solver = _SOLVER[solver]
         cfg.wait_budget = int(wait_budget)
@@ -177,6 +185,12 @@ class Plan:
                                                   ctypes.c_void_p(lam.data_ptr())),
               "rcp_get_compressed_factors")
         return [a.t() for a in At], lam
+
+    def set_warm_start(self, net):
+        """Stage-2 start from the warm-start network (a plan made with init="learned")."""
+        self._net = net
+        check(self.lib.rcp_set_warm_start(self.h, None if net is None else net.h),
+              "rcp_set_warm_start")
 
     def last_error(self):
         st = ctypes.c_int32()

@@ -72,6 +72,7 @@ struct ClusterArgs {
   double tol;
   int max_iters;
   int user_init;
+  const int* user_init_dev;  // when set, a device word that replaces user_init
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -169,7 +170,7 @@ __host__ __device__ inline Layout make_layout(int core_smem, int N, int KR) {
   L.G32 = o;  o += N * 32 * kGP;                // FP32 Grams
   L.Z = o;    o += 32 * kGP;                    // FP32 V^{-1}
   o = (o + 3) & ~3;
-  L.Vdw = o;  o += 2 * 32 * 32;                 // V, double word
+  L.Vdw = o;  o += 2 * 32 * kFP;                // V, double word (row pitch kFP)
   L.Fdw = o;  o += 2 * 2 * 32 * kFP;            // two receive buffers of the new factor rows
   L.Macc = o; o += 2 * kMW * kRowsMax * 32;     // per-warp MTTKRP accumulators
   L.ipb = o;  o += 2 * 2 * 16;                  // <M, x> partial of each CTA, two buffers
@@ -262,74 +263,68 @@ __device__ void mttkrp_rows(const ClusterArgs& a, int n, int nrows, int crank, c
   }
 }
 
-// One Gauss-Jordan step k on the SPD matrix held one row per lane (a[c];
-// lanes and columns >= R hold the identity), FP32, no pivoting; z holds the
-// rows of the inverse.  The pivot row is broadcast by shuffles.  The steps are
-// instantiated recursively so that every register index is a constant.
-template <int KR, int K>
-__device__ __forceinline__ void gj_steps(float (&a)[KR], float (&z)[KR], int R, float floor_,
-                                         int lane, bool& ok) {
-  if constexpr (K < KR) {
-    if (K < R) {
-      const float piv = __shfl_sync(kFull, a[K], K);
-      ok = ok && piv > floor_;
-      const float rp = fast_rcp(piv);
-      const bool me = lane == K;
-      const float f = me ? 0.0f : a[K] * rp;
-#pragma unroll
-      for (int c = K + 1; c < KR; ++c) {
-        const float pc = __shfl_sync(kFull, a[c], K);
-        a[c] = me ? a[c] * rp : fmaf(-f, pc, a[c]);
-      }
-#pragma unroll
-      for (int c = 0; c <= K; ++c) {
-        const float pc = __shfl_sync(kFull, z[c], K);
-        z[c] = me ? z[c] * rp : fmaf(-f, pc, z[c]);
-      }
-      a[K] = me ? 1.0f : 0.0f;
-      gj_steps<KR, K + 1>(a, z, R, floor_, lane, ok);
-    }
-  }
-}
-
-// Gauss-Jordan inverse (rows of V^{-1} into z); false if a pivot is at or
-// below floor_ or not finite (the same answer in every lane).
+// Gauss-Jordan inverse of the SPD matrix V held one row per lane (a[c]; lanes
+// and columns >= R hold the identity), FP32, no pivoting (every pivot of an SPD
+// matrix is a positive Schur-complement diagonal).  z receives the rows of
+// V^{-1}.  Step k broadcasts the pivot row (lane k) by shuffles and updates
+// every row at once: row_i -= f_i row_k with f_k = 1 - 1/a_kk, which scales the
+// pivot row itself.  The left part is shifted down one column per step, so the
+// pivot column is always a[0] and the loop body does not depend on k: one
+// small body runs R times instead of R unrolled copies (the straight-line form
+// was bound by instruction fetch).  Returns false if a pivot is at or below
+// floor_ or not finite (the same answer in every lane).
 template <int KR>
 __device__ bool gj_warp(float (&a)[KR], float (&z)[KR], int R, float floor_, int lane) {
 #pragma unroll
   for (int c = 0; c < KR; ++c) z[c] = c == lane ? 1.0f : 0.0f;
   bool ok = true;
-  gj_steps<KR, 0>(a, z, R, floor_, lane, ok);
+#pragma unroll 1
+  for (int k = 0; k < R; ++k) {
+    const float piv = __shfl_sync(kFull, a[0], k);
+    ok = ok && piv > floor_;
+    const float rp = fast_rcp(piv);
+    const float f = lane == k ? 1.0f - rp : a[0] * rp;
+#pragma unroll
+    for (int c = 1; c < KR; ++c) a[c - 1] = fmaf(-f, __shfl_sync(kFull, a[c], k), a[c]);
+    a[KR - 1] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < KR; ++c) z[c] = fmaf(-f, __shfl_sync(kFull, z[c], k), z[c]);
+  }
   return ok;
 }
 
-// Phase 1, solver warp: V for mode n in double word (Vdw) and its FP32
-// inverse (Z).  Returns the RCP_INFO bits to add (regularised) or -1 when V
+// V for mode n, the Hadamard product of the other modes' FP32 Grams
+// (Definition 2), in double word (exact for N = 3) into Vdw (row pitch kFP).
+// Run by the whole CTA as soon as the last of those Grams is known, so the
+// solver warp of the next phase 1 starts from it.
+__device__ __forceinline__ void build_V(int N, int R, int n, const float* G32, float2* Vdw,
+                                        int tid) {
+  for (int e = tid; e < R * R; e += kCThreads) {
+    const int r = e / R, c = e - r * R;
+    dwf w = {1.0f, 0.0f};
+    bool first = true;
+    for (int m = 0; m < N; ++m) {
+      if (m == n) continue;
+      const float g = G32[m * 32 * kGP + r * kGP + c];
+      w = first ? dwf{g, 0.0f} : dw_mul(w, {g, 0.0f});
+      first = false;
+    }
+    st_dw(&Vdw[r * kFP + c], w);
+  }
+}
+
+// Phase 1, solver warp: the FP32 inverse Z of V (Vdw, built beforehand).  Returns the RCP_INFO bits to add (regularised) or -1 when V
 // is not finite.
 template <int KR>
 __device__ int build_and_invert(const ClusterArgs& a, int n, const float* G32, float* Z,
                                 float2* Vdw, int lane) {
-  const int N = a.N, R = a.R;
-  // row `lane` of V in double word into Vdw, then its FP32 rounding into registers
-  if (lane < R)
-    for (int c = 0; c < R; ++c) {
-      dwf w = {1.0f, 0.0f};
-      bool first = true;
-      for (int m = 0; m < N; ++m) {
-        if (m == n) continue;
-        const float g = G32[m * 32 * kGP + lane * kGP + c];
-        w = first ? dwf{g, 0.0f} : dw_mul(w, {g, 0.0f});
-        first = false;
-      }
-      st_dw(&Vdw[lane * 32 + c], w);
-    }
-  __syncwarp();
+  const int R = a.R;
   float v[KR];
   float diag = 0.0f;
 #pragma unroll
   for (int c = 0; c < KR; ++c) {
-    v[c] = (lane < R && c < R) ? Vdw[lane * 32 + c].x : (c == lane ? 1.0f : 0.0f);
-    if (c == lane) diag = v[c];
+    v[c] = (lane < R && c < R) ? Vdw[lane * kFP + c].x : (c == lane ? 1.0f : 0.0f);
+    if (c == lane && lane < R) diag = v[c];
   }
   float tr = diag;
 #pragma unroll
@@ -370,45 +365,38 @@ template <int KR>
 __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vdw, int R,
                                          int lane) {
   const bool on = lane < R;
+  const int cz = on ? lane : 0;  // lanes >= R read a valid column and are zeroed below
   float xa = 0.0f, xb = 0.0f;
-#pragma unroll
-  for (int k = 0; k < KR; ++k) {
+#pragma unroll 2
+  for (int k = 0; k < R; ++k) {
     const float mk = __shfl_sync(kFull, m.hi, k);
-    if (k < R) {
-      const float z = on ? Z[k * kGP + lane] : 0.0f;
-      if (k & 1) xb = fmaf(mk, z, xb);
-      else xa = fmaf(mk, z, xa);
-    }
+    if (k & 1) xb = fmaf(mk, Z[k * kGP + cz], xb);
+    else xa = fmaf(mk, Z[k * kGP + cz], xa);
   }
   dwf x = on ? dw_fast_two_sum(xa, xb) : dwf{0.0f, 0.0f};
 #pragma unroll 1
   for (int step = 0; step < 2; ++step) {
     float s = m.hi, c0 = m.lo, c1 = 0.0f;
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
+#pragma unroll 2
+    for (int k = 0; k < R; ++k) {
       const float xh = __shfl_sync(kFull, x.hi, k);
       const float xl = __shfl_sync(kFull, x.lo, k);
-      if (k < R) {
-        const float2 v = on ? Vdw[k * 32 + lane] : make_float2(0.0f, 0.0f);
-        const float ph = __fmul_rn(xh, v.x);
-        const float pl = __fmaf_rn(xh, v.x, -ph);
-        const dwf t = dw_two_sum(s, -ph);
-        s = t.hi;
-        const float e = __fsub_rn(t.lo, __fadd_rn(pl, __fmaf_rn(xh, v.y, __fmul_rn(xl, v.x))));
-        if (k & 1) c1 = __fadd_rn(c1, e);
-        else c0 = __fadd_rn(c0, e);
-      }
+      const float2 v = Vdw[k * kFP + cz];
+      const float ph = __fmul_rn(xh, v.x);
+      const float pl = __fmaf_rn(xh, v.x, -ph);
+      const dwf t = dw_two_sum(s, -ph);
+      s = t.hi;
+      const float e = __fsub_rn(t.lo, __fadd_rn(pl, __fmaf_rn(xh, v.y, __fmul_rn(xl, v.x))));
+      if (k & 1) c1 = __fadd_rn(c1, e);
+      else c0 = __fadd_rn(c0, e);
     }
-    const dwf r = dw_two_sum(s, __fadd_rn(c0, c1));  // s may have cancelled below c
+    const dwf r = on ? dw_two_sum(s, __fadd_rn(c0, c1)) : dwf{0.0f, 0.0f};  // s may have cancelled below c
     float da = 0.0f, db = 0.0f;
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
+#pragma unroll 2
+    for (int k = 0; k < R; ++k) {
       const float rk = __shfl_sync(kFull, r.hi, k);
-      if (k < R) {
-        const float z = on ? Z[k * kGP + lane] : 0.0f;
-        if (k & 1) db = fmaf(rk, z, db);
-        else da = fmaf(rk, z, da);
-      }
+      if (k & 1) db = fmaf(rk, Z[k * kGP + cz], db);
+      else da = fmaf(rk, Z[k * kGP + cz], da);
     }
     x = on ? dw_add(x, {__fadd_rn(da, db), 0.0f}) : dwf{0.0f, 0.0f};
   }
@@ -483,6 +471,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
   // stream drawn row-major (l_m x R), as FP32 copies (entries r >= R zero;
   // mode 1 starts at zero and is computed first)
   for (int e = tid; e < 32 * KR; e += kCThreads) F32[e] = 0.0f;
+  const int user_init = a.user_init_dev ? *a.user_init_dev : a.user_init;
   for (int m = 1; m < N; ++m) {
     const int lm = a.l[m];
     for (int e = tid; e < lm * KR; e += kCThreads) {
@@ -490,7 +479,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
       float v = 0.0f;
       if (r < R) {
         double d;
-        if (a.user_init) {
+        if (user_init) {
           d = a.At[m][i + lm * r];
         } else {
           const int g = i * R + r;
@@ -518,6 +507,8 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
   double nb2 = 0.0;
   for (int w = 0; w < kWarps; ++w) nb2 += red[2 * w] + red[2 * w + 1];
   const double inv_nb2 = 1.0 / nb2;
+  __syncthreads();
+  build_V(N, R, 0, G32, Vdw, tid);
   __syncthreads();
 
   double rho_prev = 0.0;
@@ -599,6 +590,9 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
       }
       __syncthreads();
       gram_f32<KR>(F32, G32, n, ln, R, warp, lane);
+      __syncthreads();
+      // V of the next mode update: every Gram it needs is final now
+      build_V(N, R, n + 1 < N ? n + 1 : 0, G32, Vdw, tid);
       __syncthreads();
       if (n == N - 1) {
         // ---- fit of Section 3.3 on B: |Bhat|^2 = lambda^T (Hadamard product of
@@ -717,8 +711,10 @@ bool als_cluster_fits(const rcp_plan_s* p) {
   return cluster_smem(p, nullptr) <= 220 * 1024;
 }
 
-cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, cudaStream_t s) {
+cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_init_dev,
+                               cudaStream_t s) {
   ClusterArgs a{};
+  a.user_init_dev = user_init_dev;
   a.N = p->N;
   a.R = p->R;
   int lmax = 1;

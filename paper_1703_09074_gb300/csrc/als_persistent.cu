@@ -124,12 +124,13 @@ __device__ void als_body(const PersArgs& a, int g) {
   DevState* st = a.st;
 
   // ---- initial factors (modes 2..N) and their Grams, identical in every CTA
+  const int user_init = a.user_init_dev ? *a.user_init_dev : a.user_init;
   for (int m = 1; m < N; ++m) {
     const int lm = a.dims[m];
     for (int e = tid; e < lm * R; e += kThreads) {
       const int i = e / R, r = e - i * R;
       double v;
-      if (a.user_init) {
+      if (user_init) {
         v = a.At[m][i + lm * r];
       } else {
         const double2 z = normal_pair_f64(a.seed, (uint32_t)(m + 1), kPurposeAlsInit, (uint64_t)(e >> 1));
@@ -843,7 +844,7 @@ size_t smem_bytes(const rcp_plan_s* p) {
 }
 
 template <typename TM>
-cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
+cudaError_t launch_typed(rcp_plan_s* p, const void* B, const int* user_init_dev, cudaStream_t s) {
   const size_t smem = smem_bytes<TM>(p);
   int lmax0 = 1;
   for (int m = 0; m < p->N; ++m) lmax0 = lmax0 > p->l[m] ? lmax0 : p->l[m];
@@ -887,6 +888,7 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, cudaStream_t s) {
   a.max_iters = p->cfg.max_iters;
   a.user_init = p->user_init ? 1 : 0;
   a.budget = p->cfg.wait_budget;
+  a.user_init_dev = user_init_dev;
   // R <= 32: each row-owning CTA inverts V in double-word arithmetic (path 3)
   a.direct64 = 0;
   void* args[] = {&a};
@@ -933,8 +935,10 @@ cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem,
   return cudaGetLastError();
 }
 
-cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s) {
-  return f32 ? launch_typed<float>(p, B, s) : launch_typed<double>(p, B, s);
+cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, const int* user_init_dev,
+                                  cudaStream_t s) {
+  return f32 ? launch_typed<float>(p, B, user_init_dev, s)
+             : launch_typed<double>(p, B, user_init_dev, s);
 }
 
 }  // namespace rcp

@@ -15,6 +15,8 @@ cudaError_t launch_chol(const double* Gp, int l, double* Rinv, DevState* st, dou
 cudaError_t launch_cholqr(double* Y, int64_t I, int l, double* Gp, double* Rinv, DevState* st,
                           cudaStream_t s, bool final_qr, bool no_shift = false);
 cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream_t s);
+cudaError_t launch_lu_norm(double* Y, int64_t M, int l, int64_t L, uint8_t* used, double* cval,
+                           int64_t* cidx, double* prow, DevState* st, int nsm, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
                          cudaStream_t s);
 }  // namespace rcp
@@ -54,6 +56,18 @@ struct Span {
 
 bool valid_plan(rcp_plan_t p) { return p != nullptr && p->N >= 2; }
 
+bool mode_skipped(const rcp_config* cfg, int n0) { return (cfg->skip_modes >> n0) & 1; }
+
+// l_n of Algorithm 1 step 3 for 0-based mode n0 of the current shape (I_n, J_n):
+// min(R + p_n, I_n, J_n), p_n the mode's own oversampling when the plan sets
+// one (the remark after Algorithm 1); an uncompressed mode keeps l_n = I_n.
+int64_t mode_width(const rcp_config* cfg, int n0, int64_t In, int64_t J) {
+  if (mode_skipped(cfg, n0)) return In;
+  const int64_t pn = (cfg->flags & RCP_FLAG_MODE_OVERSAMPLE) ? cfg->mode_oversample[n0]
+                                                             : cfg->oversample;
+  return std::min<int64_t>((int64_t)cfg->rank + pn, std::min(In, J));
+}
+
 template <typename T>
 rcp_status dalloc(T** ptr, int64_t elems) {
   *ptr = nullptr;
@@ -91,7 +105,12 @@ void free_plan(rcp_plan_t p) {
   cudaFree(p->dstate);
   cudaFree(p->bar);
   cudaFree(p->abort_flag);
+  plan_ws_free(p);
   cudaFree(p->X_stage);
+  cudaFree(p->lu_used);
+  cudaFree(p->lu_cval);
+  cudaFree(p->lu_cidx);
+  cudaFree(p->lu_prow);
   cudaFree(p->lam_stage);
   if (p->prof) {
     for (int k = 0; k < p->prof_cap; ++k) {
@@ -151,10 +170,16 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   if (cfg->in_dtype != RCP_DTYPE_F64 && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
   if (cfg->precision != RCP_PREC_F64 && cfg->precision != RCP_PREC_MIXED) return RCP_EINVAL;
   if (cfg->precision == RCP_PREC_MIXED && cfg->in_dtype != RCP_DTYPE_F32) return RCP_EINVAL;
-  if (cfg->init != RCP_INIT_RANDN) return RCP_EINVAL;
-  if (cfg->solver != RCP_SOLVER_ALS) return RCP_EINVAL;
+  if (cfg->init != RCP_INIT_RANDN && cfg->init != RCP_INIT_EIG && cfg->init != RCP_INIT_LEARNED)
+    return RCP_EINVAL;
+  if (cfg->init == RCP_INIT_LEARNED && cfg->precision != RCP_PREC_MIXED) return RCP_EINVAL;
+  if (cfg->solver != RCP_SOLVER_ALS && cfg->solver != RCP_SOLVER_BCD) return RCP_EINVAL;
   if (cfg->wait_budget < 0) return RCP_EINVAL;
-  if (cfg->flags & ~(RCP_FLAG_HOST_STAGING | RCP_FLAG_NO_SHIFT)) return RCP_EINVAL;
+  if (cfg->flags & ~(RCP_FLAG_HOST_STAGING | RCP_FLAG_NO_SHIFT | RCP_FLAG_MODE_OVERSAMPLE |
+                     RCP_FLAG_LU_NORM))
+    return RCP_EINVAL;
+  if (cfg->skip_modes & ~((1 << N) - 1)) return RCP_EINVAL;
+  if ((cfg->flags & RCP_FLAG_LU_NORM) && cfg->precision != RCP_PREC_F64) return RCP_EINVAL;
   {
     int64_t total = 1;
     for (int n = 0; n < N; ++n) {
@@ -170,7 +195,8 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
       int64_t J = 1;
       for (int m = 0; m < N; ++m)
         if (m != n) J *= cur[m];
-      const int64_t l = std::min<int64_t>((int64_t)cfg->rank + cfg->oversample, std::min(cur[n], J));
+      if ((cfg->flags & RCP_FLAG_MODE_OVERSAMPLE) && cfg->mode_oversample[n] < 0) return RCP_EINVAL;
+      const int64_t l = mode_width(cfg, n, cur[n], J);
       if (l < cfg->rank || l > RCP_MAX_L) return RCP_EINVAL;
       cur[n] = l;
     }
@@ -204,7 +230,7 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
       if (m != n) J *= cur[m];
     for (int m = 0; m < n; ++m) L *= cur[m];
     for (int m = n + 1; m < N; ++m) Rt *= cur[m];
-    const int64_t l = std::min<int64_t>((int64_t)cfg->rank + cfg->oversample, std::min(cur[n], J));
+    const int64_t l = mode_width(cfg, n, cur[n], J);
     if (l < cfg->rank || l > RCP_MAX_L) {
       delete p;
       return RCP_EINVAL;
@@ -237,10 +263,12 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     part_max = std::max(part_max, (int64_t)p->nsm * lmx * p->R);  // persistent ALS partials
     part_max = std::max(part_max, (int64_t)N * 32 * 32);  // one-cluster ALS: N x 32 x 32 float2
   }
+  part_max = std::max(part_max, bcd_scratch_elems(p));  // rCP-BCD contraction buffers
   p->bufT_elems = bufmax;
   p->part_elems = part_max;
   p->tmp_elems = std::max<int64_t>(16 * std::max(red_max, (int64_t)kMaxL * (kMaxL + 1) / 2),
                                    (int64_t)kMaxN * RCP_MAX_RANK);
+  p->tmp_elems = std::max<int64_t>(p->tmp_elems, (int64_t)kMaxN * kMaxL * kMaxL);  // eig-init Grams
   p->gpart_elems = gpart_max;
   p->normpart_elems = std::max<int64_t>(norm_max, 4096);
 
@@ -269,7 +297,7 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   A(dalloc(&p->bar, 4));
   A(dalloc(&p->abort_flag, 4));
   if (p->prec == RCP_PREC_MIXED) {
-    p->tc1 = tc_mode1_supported(p->dims[0], p->l[0]);
+    p->tc1 = !mode_skipped(cfg, 0) && tc_mode1_supported(p->dims[0], p->l[0]);
     int64_t p32 = 1;
     if (p->tc1) {
       int ns = 0;
@@ -281,6 +309,14 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     A(dalloc(&p->part32, p32));
     A(dalloc(&p->QT32, (int64_t)2 * 64 * tc_ipad(Imax)));
     A(dalloc(&p->Bcore_own, p->core_elems));
+  }
+  if (cfg->flags & RCP_FLAG_LU_NORM) {
+    int64_t mrows = 1;
+    for (int n = 0; n < N; ++n) mrows = std::max(mrows, std::max(p->view[n].I, p->view[n].J));
+    A(dalloc((uint8_t**)&p->lu_used, mrows));
+    A(dalloc(&p->lu_cval, 2 * (int64_t)p->nsm));
+    A(dalloc((int64_t**)&p->lu_cidx, 2 * (int64_t)p->nsm));
+    A(dalloc(&p->lu_prow, kMaxL + 1));
   }
   if (cfg->flags & RCP_FLAG_HOST_STAGING) {
     int64_t nx = 1;
@@ -340,9 +376,30 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
     const int64_t nn = (int64_t)nsplit * ((v.I + 255) / 256);
     RCP_TRY(launch_sum_to(p->normpart, nn, &p->dstate->norm_x2, s));
   }
+  const int ng = project_grid(v, p->nsm);
+  if ((p->cfg.flags & RCP_FLAG_LU_NORM) && p->cfg.power_iters > 0) {
+    // steps 7-11 as printed: Q = lu(Y), Z = lu(T_(n)^T Q), Y = T_(n) Z; then
+    // the QR of step 12 (CholeskyQR2)
+    for (int it = 0; it < p->cfg.power_iters; ++it) {
+      RCP_TRY(launch_lu_norm(p->Y, v.I, l, v.I, p->lu_used, p->lu_cval, p->lu_cidx, p->lu_prow,
+                             p->dstate, p->nsm, s));
+      {
+        Span sp(p, RCP_KT_PROJECT, mode);
+        RCP_TRY(launch_project_f64(T, dt, v, l, p->Y, W, p->gpart, ng, s));
+      }
+      RCP_TRY(launch_lu_norm(W, v.J, l, v.L, p->lu_used, p->lu_cval, p->lu_cidx, p->lu_prow,
+                             p->dstate, p->nsm, s));
+      {
+        Span sp(p, RCP_KT_APPLY, mode);
+        RCP_TRY(launch_sketch_f64(T, dt, v, l, 0, 0, W, nsplit, p->part, nullptr, s));
+      }
+      RCP_TRY(launch_reduce(p->part, nsplit, ny, p->Y, p->tmp, p->tmp_elems, s));
+    }
+    RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, true, ns));
+    return RCP_OK;
+  }
   RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s, p->cfg.power_iters == 0, ns));
   // q normalised power iterations (steps 7-11)
-  const int ng = project_grid(v, p->nsm);
   const int npairs = l * (l + 1) / 2;
   for (int it = 0; it < p->cfg.power_iters; ++it) {
     // W = T_(n)^T Q and its Gram (step 9)
@@ -459,8 +516,19 @@ rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) 
     RCP_TRY(cudaMemsetAsync(p->dstate, 0, sizeof(DevState), s));
     p->als_done = false;
   }
-  const rcp_status st = p->prec == RCP_PREC_MIXED ? sketch_mixed(p, X, mode) : sketch_f64(p, X, mode);
-  if (st != RCP_OK) return st;
+  if (mode_skipped(&p->cfg, n0)) {
+    // an uncompressed mode (the remark after Algorithm 1): Q_n = I, and |X|^2,
+    // which the mode-1 sketch otherwise accumulates, from its own pass
+    RCP_TRY(launch_identity(p->Y, p->view[n0].I, s));
+    if (mode == 1) {
+      const int64_t nx = p->view[0].I * p->view[0].J;
+      RCP_TRY(launch_sumsq_any(X, p->cfg.in_dtype, nx, p->normpart, 64, &p->dstate->norm_x2, s));
+    }
+  } else {
+    const rcp_status st =
+        p->prec == RCP_PREC_MIXED ? sketch_mixed(p, X, mode) : sketch_f64(p, X, mode);
+    if (st != RCP_OK) return st;
+  }
   RCP_TRY(cudaMemcpyAsync(p->Q[n0], p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
   if (Q_out)
     RCP_TRY(cudaMemcpyAsync(Q_out, p->Y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, s));
@@ -475,7 +543,20 @@ rcp_status rcp_compress(rcp_plan_t p, const void* X, int32_t mode) {
   if (check_device(p) != RCP_OK) return RCP_ECUDA;
   const int n0 = mode - 1;
   const ModeView& v = p->view[n0];
-  if (p->prec == RCP_PREC_MIXED) {
+  if (mode_skipped(&p->cfg, n0)) {
+    // T_{n+1} = T_n: the working tensor moves to the next buffer unchanged
+    int dt = 0;
+    const void* T = p->prec == RCP_PREC_MIXED ? (mode == 1 ? X : p->bufT[(mode - 2) % 2])
+                                              : mode_input(p, X, mode, &dt);
+    const int64_t ne = v.I * v.J;
+    void* out = mode_output(p, mode);
+    if (p->prec != RCP_PREC_MIXED && dt == RCP_DTYPE_F32) {
+      RCP_TRY(launch_to_f64(T, RCP_DTYPE_F32, ne, (double*)out, p->stream));
+    } else {
+      RCP_TRY(cudaMemcpyAsync(out, T, (size_t)ne * p->work_elem, cudaMemcpyDeviceToDevice,
+                              p->stream));
+    }
+  } else if (p->prec == RCP_PREC_MIXED) {
     const float* T = (const float*)(mode == 1 ? X : p->bufT[(mode - 2) % 2]);
     float* out = (float*)mode_output(p, mode);
     Span sp(p, RCP_KT_TTM, mode);
@@ -534,15 +615,29 @@ rcp_status rcp_als(rcp_plan_t p, double* lambda_host, double* fit_host, int32_t*
   {
     Span sp(p, RCP_KT_ALS, 0);
     const bool f32 = p->prec == RCP_PREC_MIXED;
-    if (f32 && als_cluster_fits(p)) {
+    const int* init_dev = nullptr;  // device word chosen by the learned warm start
+    if (p->cfg.init == RCP_INIT_EIG && !p->user_init) {
+      // Algorithm 2 step 2: eigenvectors of B_(n) B_(n)^T as the initial factors
+      RCP_TRY(launch_eig_init(p, p->Bcore64, p->tmp, s));
+      p->user_init = true;
+    } else if (p->cfg.init == RCP_INIT_LEARNED && !p->user_init) {
+      // the warm-start network's factors, or the seeded start where it has none
+      const rcp_status ws = plan_ws_enqueue(p, &init_dev);
+      if (ws != RCP_OK) return ws;
+    }
+    if (p->cfg.solver == RCP_SOLVER_BCD) {
+      // Algorithm 3: successive rank-one deflation (one CTA, every component in one launch)
+      const void* B = f32 ? (const void*)mode_output(p, p->N) : (const void*)p->Bcore64;
+      RCP_TRY(launch_bcd(p, B, f32, p->part, init_dev, s));
+    } else if (f32 && als_cluster_fits(p)) {
       // small core: one thread-block cluster runs every sweep
-      RCP_TRY(launch_als_cluster(p, (const float*)mode_output(p, p->N), s));
+      RCP_TRY(launch_als_cluster(p, (const float*)mode_output(p, p->N), init_dev, s));
     } else if (als_persistent_fits(p, f32)) {
       // one cooperative kernel runs every sweep (FP32 MTTKRP in the mixed form)
       RCP_TRY(cudaMemsetAsync(p->bar, 0, 4 * sizeof(unsigned), s));
       RCP_TRY(cudaMemsetAsync(p->abort_flag, 0, 4 * sizeof(int), s));
       const void* B = f32 ? (const void*)mode_output(p, p->N) : (const void*)p->Bcore64;
-      RCP_TRY(launch_als_persistent(p, B, f32, s));
+      RCP_TRY(launch_als_persistent(p, B, f32, init_dev, s));
     } else {
       RCP_TRY(launch_sumsq(p->Bcore64, p->core_elems, p->normpart, 64, &p->dstate->norm_b2, s));
       RCP_TRY(launch_als_init(p, s));

@@ -227,14 +227,24 @@ __global__ void k_sum_to(const double* __restrict__ x, int64_t n, double* dst) {
   if (threadIdx.x == 0) *dst = s;
 }
 
-__global__ void k_sumsq_part(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+template <typename T>
+__global__ void k_sumsq_part(const T* __restrict__ x, int64_t n, double* __restrict__ part) {
   __shared__ double red[32];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    acc = fma(x[i], x[i], acc);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[i];
+    acc = fma(v, v, acc);
+  }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Q = the I x I identity (column-major): the basis of a mode left uncompressed.
+__global__ void k_identity(double* __restrict__ Q, int64_t I) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < I * I;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Q[e] = (e % (I + 1)) == 0 ? 1.0 : 0.0;
 }
 
 template <typename T>
@@ -325,8 +335,24 @@ cudaError_t launch_sum_to(const double* part, int64_t n, double* dst, cudaStream
 cudaError_t launch_sumsq(const double* x, int64_t n, double* part, int nblocks, double* dst,
                          cudaStream_t s) {
   count_launches(2);
-  k_sumsq_part<<<nblocks, 256, 0, s>>>(x, n, part);
+  k_sumsq_part<double><<<nblocks, 256, 0, s>>>(x, n, part);
   k_sum_to<<<1, 256, 0, s>>>(part, nblocks, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq_any(const void* x, int dtype, int64_t n, double* part, int nblocks,
+                             double* dst, cudaStream_t s) {
+  count_launches(2);
+  if (dtype == RCP_DTYPE_F32) k_sumsq_part<float><<<nblocks, 256, 0, s>>>((const float*)x, n, part);
+  else k_sumsq_part<double><<<nblocks, 256, 0, s>>>((const double*)x, n, part);
+  k_sum_to<<<1, 256, 0, s>>>(part, nblocks, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_identity(double* Q, int64_t I, cudaStream_t s) {
+  count_launches(1);
+  const unsigned grid = (unsigned)std::min<int64_t>((I * I + 255) / 256, 1024);
+  k_identity<<<grid, 256, 0, s>>>(Q, I);
   return cudaGetLastError();
 }
 

@@ -50,6 +50,8 @@ struct Workspace;
 
 }  // namespace rcp
 
+struct rcp_plan_ws_s;
+
 struct rcp_plan_s {
   rcp_config cfg;
   cudaStream_t stream;
@@ -107,6 +109,15 @@ struct rcp_plan_s {
   float* part32;             // FP32 split partials of the tensor-core row sweep
   int64_t part32_elems;
   float* QT32;               // Q^T in FP32, padded to NP x Ipad
+
+  // pivoted-LU normalisation (RCP_FLAG_LU_NORM): row flags, per-CTA candidates, pivot row
+  uint8_t* lu_used;
+  double* lu_cval;
+  int64_t* lu_cidx;
+  double* lu_prow;
+
+  // learned warm start of the single-tensor path (rcp_set_warm_start)
+  rcp_plan_ws_s* ws;
 
   // host staging (rcp_decompose_host)
   void* X_stage;
@@ -220,6 +231,7 @@ struct PersArgs {
   int user_init;
   int direct64;          // solve with the FP64 Cholesky factor only (no FP32 factor + refinement)
   long long budget;      // clock cycles per grid-barrier wait (0: the default)
+  const int* user_init_dev;  // when set, a device word that replaces user_init
 };
 
 // ---------------------------------------------------------------- batched form
@@ -309,12 +321,23 @@ cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lamb
                                cudaStream_t s);
 bool als_persistent_fits(const rcp_plan_s* p, bool f32);
 bool als_cluster_fits(const rcp_plan_s* p);
-cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, cudaStream_t s);
+cudaError_t launch_eig_init(rcp_plan_s* p, const double* B, double* gram, cudaStream_t s);
+void plan_ws_free(rcp_plan_s* p);
+rcp_status plan_ws_enqueue(rcp_plan_s* p, const int** flag_dev);
+int64_t bcd_scratch_elems(const rcp_plan_s* p);
+cudaError_t launch_bcd(rcp_plan_s* p, const void* B, bool f32, double* scratch,
+                       const int* user_init_dev, cudaStream_t s);
+cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_init_dev,
+                               cudaStream_t s);
 size_t als_smem_bytes_f32(int N, int R, const int* l);
 cudaError_t prepare_als_batched(size_t smem);
 cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s);
-cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, cudaStream_t s);
+cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, const int* user_init_dev,
+                                  cudaStream_t s);
 cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s);
+cudaError_t launch_sumsq_any(const void* x, int dtype, int64_t n, double* part, int nblocks,
+                             double* dst, cudaStream_t s);
+cudaError_t launch_identity(double* Q, int64_t I, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, int64_t n, double* dst, cudaStream_t s);
 
 }  // namespace rcp

@@ -65,16 +65,35 @@ def plan_configs(problems, p=8, q=1, tol=1e-10, max_iters=50):
                  max_iters=max_iters, seed=pr["seed"]) for pr in problems]
 
 
-def generate(count, seed, device, chunk=256):
-    """Training rows (x, t, meta) of ``count`` method-generated tensors (eligible rows only)."""
+def generate(count, seed, device, chunk=256, target_sweeps=None):
+    """Training rows (x, t, meta) of ``count`` method-generated tensors (eligible rows only).
+
+    target_sweeps=None: the targets are the factors ALS converges to from random
+    initial factors (at most 50 sweeps).  target_sweeps=k: the targets are the
+    factors ALS reaches after exactly k sweeps from the eigenvector start (the
+    untrained network), i.e. points further along the trajectory that the warm
+    start itself begins; a network that predicts them lets ALS start k sweeps
+    ahead on that trajectory.
+    """
+    from .api import WarmStartNet
     xs, ts, ms = [], [], []
     done = 0
     k = 0
+    eig_net = None
+    if target_sweeps is not None:
+        eig_net = WarmStartNet(batch=((chunk + 127) // 128) * 128, seed=0,
+                               stream=torch.cuda.current_stream(device))
     while done < count:
         n = min(chunk, count - done)
         probs = draw_problems(n, seed * 7919 + k)
         Xs = make_tensors(probs, device)
-        bp = BatchedPlan(plan_configs(probs), stream=torch.cuda.current_stream(device))
+        if target_sweeps is None:
+            cfgs = plan_configs(probs)
+        else:
+            cfgs = plan_configs(probs, tol=0.0, max_iters=int(target_sweeps))
+        bp = BatchedPlan(cfgs, stream=torch.cuda.current_stream(device))
+        if eig_net is not None:
+            bp.set_warm_start(eig_net)
         bp.run(Xs)
         ex = bp.export()
         keep = ex["meta"][:, 3] > 0
@@ -86,6 +105,8 @@ def generate(count, seed, device, chunk=256):
         del Xs, ex
         done += n
         k += 1
+    if eig_net is not None:
+        eig_net.close()
     return dict(x=torch.cat(xs), t=torch.cat(ts), meta=torch.cat(ms))
 
 

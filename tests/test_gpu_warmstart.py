@@ -215,3 +215,42 @@ def test_learned_warm_start_gain(rcp_lib):
     test.close()
     print("\n" + "\n".join(lines))
     net.close()
+
+
+@pytest.mark.slow
+def test_trained_network_beats_its_untrained_start(rcp_lib):
+    """Held-out batch: the trained network against the untrained one (epoch 0, whose
+    zero last layer gives the eigenvector initialisation of Algorithm 2 step 2).
+
+    Training targets are the factors ALS reaches after 10 sweeps from that very
+    start, so a network that learns them lets ALS begin further along its own
+    trajectory.  The yardstick is the mean fit within 5 and within 10 sweeps
+    (the precision form's fit carries FP32 rounding of about 1e-7, far below the
+    margin asserted)."""
+    from paper_1703_09074_gb300 import WarmStartNet
+    from paper_1703_09074_gb300 import warmstart as W
+    dev = torch.device("cuda")
+    data = W.generate(8192, seed=41, device=dev, target_sweeps=10)
+    net = WarmStartNet(batch=256, seed=5)
+    val = W.Evaluator(256, seed=42, device=dev, budgets=(5,))
+    hist, best_epoch = W.train(net, data, epochs=8, lr=3e-4, evaluator=val)
+    val.close()
+    untrained = WarmStartNet(batch=256, seed=5)
+    test = W.Evaluator(256, seed=43, device=dev, budgets=(5, 10))
+    lines = [f"trained vs untrained network (best epoch {best_epoch}, "
+             f"validation fit by epoch {[round(h.get('val_fit', 0.0), 6) for h in hist]}):"]
+    gains = {}
+    for k in (5, 10):
+        e0 = test.run(untrained, k)
+        tr = test.run(net, k)
+        gains[k] = tr["fit"].mean() - e0["fit"].mean()
+        lines.append(f"  {k:2d} sweeps: mean fit untrained {e0['fit'].mean():.6f} trained "
+                     f"{tr['fit'].mean():.6f} (gain {gains[k]:+.6f})")
+        assert tr["learned"].mean() > 0.95 and e0["learned"].mean() > 0.95
+    test.close()
+    print("\n" + "\n".join(lines))
+    untrained.close()
+    net.close()
+    assert best_epoch > 0
+    for k in (5, 10):
+        assert gains[k] > 1e-4, (k, gains[k])
