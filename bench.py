@@ -300,6 +300,13 @@ def run_ours(args):
                 "peak_source": src,
                 "algorithmic": f"{xbytes} B per launch (one read of X)"}
     sketch_gbs = xbytes / (sk_ms / sk_n / 1e3) / 1e9 if sk_n else None
+    # ALS (one launch per decomposition): time per mode update and share of the step
+    als_ms = stages["als"]["ms_per_step"]
+    updates = max(res["iters"], 1) * len(w.dims)
+    als_line = {"ms_per_step": als_ms, "us_per_mode_update": 1e3 * als_ms / updates,
+                "mode_updates": updates, "share_of_step": als_ms / (total_ms / args.steps),
+                "bound": "latency (dependent small solves on one cluster, no HBM traffic: "
+                         "the core stays in shared memory)"}
 
     # end to end through the host-buffer entry point (H2D of X and D2H of factors inside)
     e2e = []
@@ -357,6 +364,7 @@ def run_ours(args):
             "stages": stages,
             "mode1_sweeps": mode1,
             "roofline": roof,
+            "als": als_line,
             "decompositions_per_s": ws * args.steps / (total_ms / 1e3),
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": xbytes,
                     "d2h_bytes_per_step": d2h},

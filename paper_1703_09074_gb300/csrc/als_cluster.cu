@@ -6,33 +6,34 @@
 // factor, so the mode-n update needs no cross-CTA reduction: CTA c owns the
 // rows i = c, c + C, c + 2C, ... of the factor being updated.  Per mode update:
 //
-//   phase 1  warps 0..7: MTTKRP rows M[i, :] = B_(n)[i, :] (KR of the other
-//            factors) for the owned rows, in two stages (Section 3.2.1): the
-//            inner sum over the first other mode a,
+//   phase 1  nine warps (sub-partitions 1-3): MTTKRP rows M[i, :] = B_(n)[i, :]
+//            (KR of the other factors) for the owned rows, in two stages
+//            (Section 3.2.1): the inner sum over the first other mode a,
 //              s[i, p, r] = sum_{i_a} B[.., i, .., i_a, .., p] A_a[i_a, r],
 //            with one lane per multi-index p of the remaining modes, times the
 //            remaining factors' Khatri-Rao row KR_p[r]; the 32 lanes' vectors
 //            are then summed by a reduce-scatter so that lane r ends with
 //            M[i, r].  FP32 products and sums (at most 32 terms per stage),
 //            double-word accumulation across work items.
-//            warp 8 (concurrently): V = Hadamard product of the other modes'
-//            Grams (Definition 2), in double-word form (exact for N = 3) and
-//            rounded to FP32; Z = V^{-1} by Gauss-Jordan in FP32 registers, one
-//            row per lane (V is symmetric positive definite: no pivoting).  A
-//            pivot at or below 64 R u_32 trace(V) repeats it on V + s I with
-//            that shift s (RCP_INFO_ALS_REGULARISED).
-//   phase 2  the solve x V = M of Definition 2 for the owned rows: x0 = M Z,
+//            warp 0 (concurrently, alone on sub-partition 0): Z = V^{-1} by
+//            Gauss-Jordan in FP32 registers, one row per lane, V the Hadamard
+//            product of the other modes' Grams (Definition 2), built in double
+//            word by the whole CTA at the end of the previous update.  V is
+//            symmetric positive definite: no pivoting.  A pivot at or below
+//            64 R u_32 trace(V) repeats it on V + s I with that shift s
+//            (RCP_INFO_ALS_REGULARISED).
+//   phase 2  warp j solves owned row j of x V = M (Definition 2): x0 = M Z,
 //            then two steps of iterative refinement x <- x + (M - x V) Z whose
-//            residual is formed as a compensated dot product (Ogita, Rump &
-//            Oishi 2005) from double-word x, V and M: each step multiplies the
-//            error by about kappa(V) u_32, so the solve ends within about
+//            residual is a compensated dot product (Ogita, Rump & Oishi 2005)
+//            over double-word x, V and M: each step multiplies the error by
+//            about kappa(V) u_32, so the solve ends within about
 //            (kappa u_32)^3 + kappa 2^-44 of the exact solution.
-//   phase 3  the owned rows (double word) are stored into every CTA's shared
-//            memory through distributed shared memory; one cluster barrier.
+//   phase 3  each row (double word) goes to every CTA's shared memory through
+//            distributed shared memory; one cluster barrier.
 //   phase 4  every CTA, identically: column norms in double word, the column
 //            normalisation of Algorithm 2 (lambda = the norms at n = N), the
-//            FP32 copy for the next MTTKRPs and its Gram; after mode N the fit
-//            of Section 3.3 and the stop rule.
+//            FP32 copy for the next MTTKRPs, its Gram, V of the next update;
+//            after mode N the fit of Section 3.3 and the stop rule.
 //
 // The receive buffers alternate between updates, so one cluster barrier per
 // update orders every remote store after the readers of the buffer's previous
@@ -268,28 +269,33 @@ __device__ void mttkrp_rows(const ClusterArgs& a, int n, int nrows, int crank, c
 // matrix is a positive Schur-complement diagonal).  z receives the rows of
 // V^{-1}.  Step k broadcasts the pivot row (lane k) by shuffles and updates
 // every row at once: row_i -= f_i row_k with f_k = 1 - 1/a_kk, which scales the
-// pivot row itself.  The left part is shifted down one column per step, so the
-// pivot column is always a[0] and the loop body does not depend on k: one
-// small body runs R times instead of R unrolled copies (the straight-line form
-// was bound by instruction fetch).  Returns false if a pivot is at or below
-// floor_ or not finite (the same answer in every lane).
+// pivot row itself (no select).  The steps are instantiated recursively so
+// that every register index is a constant; gj_warp returns false if a pivot is
+// at or below floor_ or not finite (the same answer in every lane).
+template <int KR, int K>
+__device__ __forceinline__ void gj_steps(float (&a)[KR], float (&z)[KR], int R, float floor_,
+                                         int lane, bool& ok) {
+  if constexpr (K < KR) {
+    if (K < R) {
+      const float piv = __shfl_sync(kFull, a[K], K);
+      ok = ok && piv > floor_;
+      const float rp = fast_rcp(piv);
+      const float f = lane == K ? 1.0f - rp : a[K] * rp;
+#pragma unroll
+      for (int c = K + 1; c < KR; ++c) a[c] = fmaf(-f, __shfl_sync(kFull, a[c], K), a[c]);
+#pragma unroll
+      for (int c = 0; c <= K; ++c) z[c] = fmaf(-f, __shfl_sync(kFull, z[c], K), z[c]);
+      gj_steps<KR, K + 1>(a, z, R, floor_, lane, ok);
+    }
+  }
+}
+
 template <int KR>
 __device__ bool gj_warp(float (&a)[KR], float (&z)[KR], int R, float floor_, int lane) {
 #pragma unroll
   for (int c = 0; c < KR; ++c) z[c] = c == lane ? 1.0f : 0.0f;
   bool ok = true;
-#pragma unroll 1
-  for (int k = 0; k < R; ++k) {
-    const float piv = __shfl_sync(kFull, a[0], k);
-    ok = ok && piv > floor_;
-    const float rp = fast_rcp(piv);
-    const float f = lane == k ? 1.0f - rp : a[0] * rp;
-#pragma unroll
-    for (int c = 1; c < KR; ++c) a[c - 1] = fmaf(-f, __shfl_sync(kFull, a[c], k), a[c]);
-    a[KR - 1] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < KR; ++c) z[c] = fmaf(-f, __shfl_sync(kFull, z[c], k), z[c]);
-  }
+  gj_steps<KR, 0>(a, z, R, floor_, lane, ok);
   return ok;
 }
 
@@ -367,7 +373,7 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
   const bool on = lane < R;
   const int cz = on ? lane : 0;  // lanes >= R read a valid column and are zeroed below
   float xa = 0.0f, xb = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
   for (int k = 0; k < R; ++k) {
     const float mk = __shfl_sync(kFull, m.hi, k);
     if (k & 1) xb = fmaf(mk, Z[k * kGP + cz], xb);
@@ -377,7 +383,7 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
 #pragma unroll 1
   for (int step = 0; step < 2; ++step) {
     float s = m.hi, c0 = m.lo, c1 = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < R; ++k) {
       const float xh = __shfl_sync(kFull, x.hi, k);
       const float xl = __shfl_sync(kFull, x.lo, k);
@@ -392,7 +398,7 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
     }
     const dwf r = on ? dw_two_sum(s, __fadd_rn(c0, c1)) : dwf{0.0f, 0.0f};  // s may have cancelled below c
     float da = 0.0f, db = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < R; ++k) {
       const float rk = __shfl_sync(kFull, r.hi, k);
       if (k & 1) db = fmaf(rk, Z[k * kGP + cz], db);
@@ -403,24 +409,34 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
   return x;
 }
 
-// Gram of mode m's FP32 factor copy: warp w forms rows r = w, w + 12, ... with
-// lane c holding column c (each entry summed over i in the same order, so the
-// matrix is exactly symmetric).
+// Gram of mode m's FP32 factor copy: thread t forms the 2 x 2 block (rows 2 br,
+// 2 br + 1; columns 2 bc, 2 bc + 1) from two 8-byte loads per row of the factor
+// (columns >= R of the copy are zero).  Both halves are formed with the same
+// products in the same order, so the matrix is exactly symmetric.
 template <int KR>
 __device__ __forceinline__ void gram_f32(const float* F32, float* G32, int m, int lm, int R,
-                                         int warp, int lane) {
+                                         int tid) {
   const float* F = F32 + m * 32 * KR;
   float* G = G32 + m * 32 * kGP;
-  for (int r = warp; r < R; r += kWarps) {
-    float s0 = 0.0f, s1 = 0.0f;
-    if (lane < R) {
-      int i = 0;
-      for (; i + 1 < lm; i += 2) {
-        s0 = fmaf(F[i * KR + r], F[i * KR + lane], s0);
-        s1 = fmaf(F[(i + 1) * KR + r], F[(i + 1) * KR + lane], s1);
-      }
-      if (i < lm) s0 = fmaf(F[i * KR + r], F[i * KR + lane], s0);
-      G[r * kGP + lane] = __fadd_rn(s0, s1);
+  const int nb = (R + 1) >> 1;
+  for (int e = tid; e < nb * nb; e += kCThreads) {
+    const int br = e / nb, bc = e - br * nb;
+    float s00 = 0.0f, s01 = 0.0f, s10 = 0.0f, s11 = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < lm; ++i) {
+      const float2 u = *(const float2*)(F + i * KR + 2 * br);
+      const float2 v = *(const float2*)(F + i * KR + 2 * bc);
+      s00 = fmaf(u.x, v.x, s00);
+      s01 = fmaf(u.x, v.y, s01);
+      s10 = fmaf(u.y, v.x, s10);
+      s11 = fmaf(u.y, v.y, s11);
+    }
+    const int r = 2 * br, c = 2 * bc;
+    G[r * kGP + c] = s00;
+    if (c + 1 < R) G[r * kGP + c + 1] = s01;
+    if (r + 1 < R) {
+      G[(r + 1) * kGP + c] = s10;
+      if (c + 1 < R) G[(r + 1) * kGP + c + 1] = s11;
     }
   }
 }
@@ -503,7 +519,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
     sh_done = 0;
   }
   __syncthreads();
-  for (int m = 1; m < N; ++m) gram_f32<KR>(F32, G32, m, a.l[m], R, warp, lane);
+  for (int m = 1; m < N; ++m) gram_f32<KR>(F32, G32, m, a.l[m], R, tid);
   double nb2 = 0.0;
   for (int w = 0; w < kWarps; ++w) nb2 += red[2 * w] + red[2 * w + 1];
   const double inv_nb2 = 1.0 / nb2;
@@ -589,7 +605,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
         }
       }
       __syncthreads();
-      gram_f32<KR>(F32, G32, n, ln, R, warp, lane);
+      gram_f32<KR>(F32, G32, n, ln, R, tid);
       __syncthreads();
       // V of the next mode update: every Gram it needs is final now
       build_V(N, R, n + 1 < N ? n + 1 : 0, G32, Vdw, tid);

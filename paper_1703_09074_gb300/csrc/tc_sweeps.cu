@@ -256,17 +256,25 @@ k_tc_rows(const float* __restrict__ X, int64_t I, int64_t J, int l, uint64_t see
   tc::tc_fence_after_sync();
   if (!ok && tid == 0) set_status(st, RCP_ETIMEOUT);
 
+  // a wait that gave up may leave MMAs in flight: then tensor memory is not read
+  // (the partials are zeroed) and the launch only records RCP_ETIMEOUT
+  const bool ok_all = __syncthreads_and(ok) != 0;
   if (warp < 4) {  // warp w reads tensor-memory lanes 32 w .. 32 w + 31
     const int64_t r = i0 + warp * 32 + lane;
 #pragma unroll
     for (int cg = 0; cg < NP / 32; ++cg) {
       float v[32];
-      tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), v);
+      if (ok_all && nk > 0) {
+        tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), v);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 0.0f;
+      }
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
         const int col = cg * 32 + k;
         if (col < l && r < I)
-          part[((int64_t)blockIdx.y * l + col) * I + r] = (ok && nk > 0) ? v[k] : 0.0f;
+          part[((int64_t)blockIdx.y * l + col) * I + r] = v[k];
       }
     }
   }
