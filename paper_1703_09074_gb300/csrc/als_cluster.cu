@@ -41,6 +41,7 @@
 // so the stop decision is identical in all of them and every CTA reaches every
 // cluster barrier: there is no spin-wait and no early exit.
 #include <math.h>
+#include <string.h>
 
 #include "dw_arith.cuh"
 #include "rcp_internal.cuh"
@@ -54,7 +55,6 @@ namespace {
 constexpr int kWarps = 12;
 constexpr int kCThreads = kWarps * 32;
 constexpr int kMW = 9;                       // MTTKRP warps
-constexpr int kRowsMax = 4;                  // owned rows per mode: ceil(32 / 8)
 constexpr int kGP = 33;                      // row pitch of the FP32 Grams and of Z
 constexpr int kFP = 33;                      // row pitch (float2) of the receive buffers
 constexpr unsigned kFull = 0xffffffffu;
@@ -74,6 +74,7 @@ struct ClusterArgs {
   int max_iters;
   int user_init;
   const int* user_init_dev;  // when set, a device word that replaces user_init
+  int max_items;         // MTTKRP work items of the busiest mode (partial-result slots)
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -164,7 +165,7 @@ struct Layout {
   int F32, G32, Z, Vdw, Fdw, Macc, ipb, lamd, red, total;  // offsets in floats
 };
 
-__host__ __device__ inline Layout make_layout(int core_smem, int N, int KR) {
+__host__ __device__ inline Layout make_layout(int core_smem, int N, int KR, int max_items) {
   Layout L;
   int o = (core_smem + 3) & ~3;
   L.F32 = o;  o += N * 32 * KR;                 // FP32 factor copies, [i][r], pitch KR
@@ -173,7 +174,7 @@ __host__ __device__ inline Layout make_layout(int core_smem, int N, int KR) {
   o = (o + 3) & ~3;
   L.Vdw = o;  o += 2 * 32 * kFP;                // V, double word (row pitch kFP)
   L.Fdw = o;  o += 2 * 2 * 32 * kFP;            // two receive buffers of the new factor rows
-  L.Macc = o; o += 2 * kMW * kRowsMax * 32;     // per-warp MTTKRP accumulators
+  L.Macc = o; o += max_items * 32;              // one FP32 partial row per MTTKRP work item
   L.ipb = o;  o += 2 * 2 * 16;                  // <M, x> partial of each CTA, two buffers
   L.lamd = o; o += 2 * 32;                      // lambda, double word
   L.red = o;  o += 2 * 64;                      // 64 doubles of scratch
@@ -181,28 +182,43 @@ __host__ __device__ inline Layout make_layout(int core_smem, int N, int KR) {
   return L;
 }
 
+// Work items of the MTTKRP of mode n for a CTA owning nrows rows: per row, PC
+// chunks of 32 multi-indices p times S segments of the inner mode's range (S > 1
+// only while there are fewer items than MTTKRP warps).
+__host__ __device__ inline void mttkrp_items(const int* l, int N, int n, int nrows, int* PC,
+                                             int* S) {
+  const int am = n == 0 ? 1 : 0;
+  int P = 1;
+  for (int m = 0; m < N; ++m)
+    if (m != n && m != am) P *= l[m];
+  *PC = (P + 31) >> 5;
+  const int base = nrows * *PC;
+  const int la = l[am];
+  *S = 1;
+  if (base > 0 && base < kMW) {
+    const int s1 = kMW / base, s2 = la >> 2;
+    *S = s1 < (s2 > 1 ? s2 : 1) ? s1 : (s2 > 1 ? s2 : 1);
+  }
+}
+
 // Phase 1, MTTKRP warps: rows crank + j C (j < nrows) of M = B_(n) KR.  Work
 // items (row slot j, chunk of 32 multi-indices p, segment of the inner mode's
-// range) are spread over the kMW MTTKRP warps; MTTKRP warp w (0..kMW-1) adds its
-// items' results into its own double-word accumulators Macc[w][j][r].
+// range) are spread over the kMW MTTKRP warps; item t leaves its partial row
+// (lane r: its part of M[i, r]) in slot t of Mpart; the items of row j are the
+// PC S consecutive slots from j PC S.
 template <int KR>
 __device__ void mttkrp_rows(const ClusterArgs& a, int n, int nrows, int crank, const float* Bs,
-                            const float* F32, float2* Macc, int warp, int lane) {
+                            const float* F32, float* Mpart, int warp, int lane) {
   const int N = a.N, C = a.C;
   const int am = n == 0 ? 1 : 0;  // the inner (first other) mode
   const int la = a.l[am];
   int P = 1;
   for (int m = 0; m < N; ++m)
     if (m != n && m != am) P *= a.l[m];
-  const int PC = (P + 31) >> 5;
-  const int base = nrows * PC;
-  int S = 1;
-  if (base > 0 && base < kMW) S = min(kMW / base, max(1, la >> 2));
-  const int nitems = base * S;
+  int PC, S;
+  mttkrp_items(a.l, N, n, nrows, &PC, &S);
+  const int nitems = nrows * PC * S;
   const int seglen = (la + S - 1) / S;
-  float2* macc = Macc + warp * kRowsMax * 32;
-#pragma unroll
-  for (int j = 0; j < kRowsMax; ++j) macc[j * 32 + lane] = make_float2(0.0f, 0.0f);
   const int sa = a.S[am];
   for (int item = warp; item < nitems; item += kMW) {
     const int j = item / (PC * S);
@@ -257,10 +273,7 @@ __device__ void mttkrp_rows(const ClusterArgs& a, int n, int nrows, int crank, c
         acc[4 * q + 3] *= v.w;
       }
     }
-    const float v = reduce_scatter32<KR>(acc, lane);
-    const float2 m2 = macc[j * 32 + lane];
-    const dwf t = dw_two_sum(m2.x, v);
-    macc[j * 32 + lane] = make_float2(t.hi, __fadd_rn(m2.y, t.lo));
+    Mpart[item * 32 + lane] = reduce_scatter32<KR>(acc, lane);
   }
 }
 
@@ -442,21 +455,21 @@ __device__ __forceinline__ void gram_f32(const float* F32, float* G32, int m, in
 }
 
 template <int KR>
-__global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
+__device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int sh_info, sh_bad, sh_done;
-  __shared__ float2 ipr[kRowsMax];
+  __shared__ float2 ipr[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.N, R = a.R, C = a.C;
   const int crank = (int)cluster_rank();
-  const Layout Ly = make_layout(a.core_smem, N, KR);
+  const Layout Ly = make_layout(a.core_smem, N, KR, a.max_items);
   float* Bs = smem;
   float* F32 = smem + Ly.F32;
   float* G32 = smem + Ly.G32;
   float* Z = smem + Ly.Z;
   float2* Vdw = (float2*)(smem + Ly.Vdw);
   float2* Fdw = (float2*)(smem + Ly.Fdw);
-  float2* Macc = (float2*)(smem + Ly.Macc);
+  float* Mpart = smem + Ly.Macc;
   float2* ipb = (float2*)(smem + Ly.ipb);
   float2* lamd = (float2*)(smem + Ly.lamd);
   double* red = (double*)(smem + Ly.red);
@@ -535,7 +548,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
       const int nrows = ln > crank ? (ln - crank + C - 1) / C : 0;
       // ---- phase 1: MTTKRP of the owned rows || V and its inverse
       if (mw >= 0) {
-        mttkrp_rows<KR>(a, n, nrows, crank, Bs, F32, Macc, mw, lane);
+        mttkrp_rows<KR>(a, n, nrows, crank, Bs, F32, Mpart, mw, lane);
       } else if (warp == 0) {
         const int inf = build_and_invert<KR>(a, n, G32, Z, Vdw, lane);
         if (lane == 0) {
@@ -544,18 +557,19 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
         }
       }
       __syncthreads();
-      // ---- phase 2 + 3: warp j solves owned row j and stores it into every CTA
+      // ---- phase 2 + 3: warp w solves owned rows w, w + 12, ... and stores them into every CTA
       float2* fd = Fdw + buf * 32 * kFP;
-      if (warp < nrows) {
-        const int j = warp, i = crank + j * C;
+      int PCn, Sn;
+      mttkrp_items(a.l, N, n, nrows, &PCn, &Sn);
+      const int per_row = PCn * Sn;
+      for (int j = warp; j < nrows; j += kWarps) {
+        const int i = crank + j * C;
         dwf m = {0.0f, 0.0f};
-        if (lane < R) {
-          dwf t[kMW];
-#pragma unroll
-          for (int w = 0; w < kMW; ++w) t[w] = ld_dw(&Macc[(w * kRowsMax + j) * 32 + lane]);
-          m = dw_add(dw_add(dw_add(t[0], t[1]), dw_add(t[2], t[3])),
-                     dw_add(dw_add(dw_add(t[4], t[5]), dw_add(t[6], t[7])), t[8]));
-        }
+        if (lane < R)  // the row's partials in slot order, summed in double word
+          for (int q = 0; q < per_row; ++q) {
+            const float v = Mpart[(j * per_row + q) * 32 + lane];
+            m = q == 0 ? dwf{v, 0.0f} : dw_add(m, {v, 0.0f});
+          }
         const dwf x = solve_row<KR>(m, Z, Vdw, R, lane);
         if (lane < R) {
           const uint32_t loc = smem_addr(&fd[i * kFP + lane]);
@@ -669,6 +683,11 @@ __global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
   }
 }
 
+template <int KR>
+__global__ void __launch_bounds__(kCThreads, 1) k_als_cluster(ClusterArgs a) {
+  als_cluster_body<KR>(a);
+}
+
 // the core's padded strides: S_1 = 1, S_{m+1} = S_m l_m rounded up to odd, so
 // that lanes stepping along any one mode hit distinct banks
 int pad_strides(const int* l, int N, int* S) {
@@ -679,6 +698,34 @@ int pad_strides(const int* l, int N, int* S) {
     if (m + 1 < N && !(s & 1)) s += 1;
   }
   return s;
+}
+
+int kr_for(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 24 ? 24 : 32; }
+
+// Shape-dependent fields of the arguments (widths, cluster size, padded
+// strides, work-item slots) and the dynamic shared memory for KR accumulators.
+size_t cluster_shape(int N, int R, const int* l, int cmax, ClusterArgs* a, int KR) {
+  ClusterArgs t{};
+  ClusterArgs* q = a ? a : &t;
+  q->N = N;
+  q->R = R;
+  int lmax = 1;
+  for (int m = 0; m < N; ++m) {
+    q->l[m] = l[m];
+    lmax = lmax > l[m] ? lmax : l[m];
+  }
+  q->C = lmax < cmax ? lmax : cmax;
+  q->core_smem = pad_strides(l, N, q->S);
+  int items = 1;
+  for (int n = 0; n < N; ++n) {
+    const int nrows = (l[n] + q->C - 1) / q->C;  // CTA 0 owns the most rows
+    int PC, S;
+    mttkrp_items(l, N, n, nrows, &PC, &S);
+    items = items > nrows * PC * S ? items : nrows * PC * S;
+  }
+  q->max_items = items;
+  const Layout L = make_layout(q->core_smem, N, KR, items);
+  return (size_t)L.total * sizeof(float);
 }
 
 template <int KR>
@@ -702,17 +749,11 @@ cudaError_t launch_kr(const ClusterArgs& a, size_t smem, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k_als_cluster<KR>, a);
 }
 
-int kr_for(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 24 ? 24 : 32; }
-
-size_t cluster_smem(const rcp_plan_s* p, ClusterArgs* a) {
-  int S[kMaxN];
-  const int core = pad_strides(p->l, p->N, S);
-  if (a) {
-    for (int m = 0; m < p->N; ++m) a->S[m] = S[m];
-    a->core_smem = core;
-  }
-  const Layout L = make_layout(core, p->N, kr_for(p->R));
-  return (size_t)L.total * sizeof(float);
+// Batched form: CTA b runs the whole ALS of problem b as a cluster of one CTA
+// (C = 1: every row owned, the "remote" stores land in its own shared memory).
+template <int KR>
+__global__ void __launch_bounds__(kCThreads, 1) k_als_cluster_batched(const ClusterArgs* args) {
+  als_cluster_body<KR>(args[blockIdx.x]);
 }
 
 }  // namespace
@@ -724,23 +765,15 @@ bool als_cluster_fits(const rcp_plan_s* p) {
   for (int m = 0; m < p->N; ++m)
     if (p->l[m] > 32) return false;
   if (p->core_elems >= (1LL << 20)) return false;
-  return cluster_smem(p, nullptr) <= 220 * 1024;
+  return cluster_shape(p->N, p->R, p->l, 8, nullptr, kr_for(p->R)) <= 220 * 1024;
 }
 
 cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_init_dev,
                                cudaStream_t s) {
   ClusterArgs a{};
+  const size_t smem = cluster_shape(p->N, p->R, p->l, 8, &a, kr_for(p->R));
   a.user_init_dev = user_init_dev;
-  a.N = p->N;
-  a.R = p->R;
-  int lmax = 1;
-  for (int m = 0; m < p->N; ++m) {
-    a.l[m] = p->l[m];
-    a.At[m] = p->At[m];
-    lmax = lmax > p->l[m] ? lmax : p->l[m];
-  }
-  a.C = lmax < 8 ? lmax : 8;
-  const size_t smem = cluster_smem(p, &a);
+  for (int m = 0; m < p->N; ++m) a.At[m] = p->At[m];
   a.B = B;
   a.lam = p->lam;
   a.facdw = (float2*)p->part;
@@ -755,6 +788,56 @@ cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_in
     case 24: return launch_kr<24>(a, smem, s);
     default: return launch_kr<32>(a, smem, s);
   }
+}
+
+// Arguments of problem b of a batch for k_als_cluster_batched: written into
+// *out (host); returns its shared-memory need for KR = kr_for(rmax), or 0 when
+// the problem is beyond the kernel (some l_n > 32).
+size_t cluster_batched_args(int N, int R, const int* l, int rmax, const float* B,
+                            double* const* At, double* lam, float2* facdw, DevState* st,
+                            uint64_t seed, double tol, int max_iters, const int* user_init_dev,
+                            void* out) {
+  for (int m = 0; m < N; ++m)
+    if (l[m] > 32) return 0;
+  ClusterArgs a{};
+  const size_t smem = cluster_shape(N, R, l, 1, &a, kr_for(rmax));
+  for (int m = 0; m < N; ++m) a.At[m] = At[m];
+  a.B = B;
+  a.lam = lam;
+  a.facdw = facdw;
+  a.st = st;
+  a.seed = seed;
+  a.tol = tol;
+  a.max_iters = max_iters;
+  a.user_init = 0;
+  a.user_init_dev = user_init_dev;
+  memcpy(out, &a, sizeof(a));
+  return smem;
+}
+
+size_t cluster_args_bytes() { return sizeof(ClusterArgs); }
+
+// Shared-memory limit of the batched kernel for this batch (once, at plan time:
+// the launch below may be captured into a graph).
+cudaError_t prepare_als_cluster_batched(int rmax, size_t smem) {
+  const int kr = kr_for(rmax);
+  const void* kern = kr == 8 ? (const void*)k_als_cluster_batched<8>
+                   : kr == 16 ? (const void*)k_als_cluster_batched<16>
+                   : kr == 24 ? (const void*)k_als_cluster_batched<24>
+                              : (const void*)k_als_cluster_batched<32>;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_als_cluster_batched(const void* dev_args, int count, int rmax, size_t smem,
+                                       cudaStream_t s) {
+  const ClusterArgs* args = (const ClusterArgs*)dev_args;
+  const int kr = kr_for(rmax);
+  count_launches(1);
+  if (kr == 8) k_als_cluster_batched<8><<<count, kCThreads, smem, s>>>(args);
+  else if (kr == 16) k_als_cluster_batched<16><<<count, kCThreads, smem, s>>>(args);
+  else if (kr == 24) k_als_cluster_batched<24><<<count, kCThreads, smem, s>>>(args);
+  else k_als_cluster_batched<32><<<count, kCThreads, smem, s>>>(args);
+  return cudaGetLastError();
 }
 
 }  // namespace rcp

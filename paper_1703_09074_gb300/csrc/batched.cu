@@ -286,6 +286,11 @@ struct rcp_batched_s {
   int* dummy_abort = nullptr;
   size_t als_smem = 0;
   int lmax = 1;
+  // ALS of every tensor by the one-cluster kernel with clusters of one CTA
+  void* cluArgs = nullptr;           // device table of its arguments
+  float2* facdw = nullptr;           // its double-word factor scratch, count x N x 32 x 32
+  size_t clu_smem = 0;
+  int rmax = 1;
   int row_grid_mult = 4, col_grid_mult = 4;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -325,6 +330,8 @@ void free_batched(rcp_batched_t p) {
   cudaFree(p->colItems);
   cudaFree(p->qrP);
   cudaFree(p->alsP);
+  cudaFree(p->cluArgs);
+  cudaFree(p->facdw);
   cudaFree(p->projP);
   cudaFree(p->stPtrs);
   cudaFree(p->counters);
@@ -382,7 +389,7 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
     if (mlp_forward_enqueue(p->net, p->ws_x, C, false, s) != RCP_OK) return RCP_ECUDA;
     RCPB_TRY(launch_ws_init(p->net->Y, p->ws_U, p->ws_meta, p->ws_items, C, s));
   }
-  RCPB_TRY(launch_als_batched(p->alsP, C, p->als_smem, s));
+  RCPB_TRY(launch_als_cluster_batched(p->cluArgs, C, p->rmax, p->clu_smem, s));
   count_launches(2);
   k_b_backproject<<<C * p->N, 256, 0, s>>>(p->projP, p->N);
   RCPB_TRY(cudaGetLastError());
@@ -519,6 +526,33 @@ rcp_status build_tables(rcp_batched_t p) {
       !up(&p->colItems, cItems) || !up(&p->alsP, als) || !up(&p->projP, proj) || !up(&p->stPtrs, sts))
     return RCP_ENOMEM;
   p->als_host = als;
+  // the one-cluster ALS arguments (clusters of one CTA); the learned start sets the
+  // user_init word of the PersArgs table, which these arguments point at
+  {
+    std::vector<char> host((size_t)C * cluster_args_bytes());
+    int rmax = 1;
+    for (int b = 0; b < C; ++b) rmax = std::max(rmax, p->t[b].R);
+    p->rmax = rmax;
+    if (cudaMalloc((void**)&p->facdw, (size_t)C * N * 32 * 32 * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&p->cluArgs, host.size()) != cudaSuccess)
+      return RCP_ENOMEM;
+    size_t smax = 0;
+    for (int b = 0; b < C; ++b) {
+      auto& t = p->t[b];
+      const size_t sm = cluster_batched_args(
+          N, t.R, t.l, rmax, t.buf[(N - 1) % 2], t.At, t.lam_t, p->facdw + (size_t)b * N * 1024,
+          t.st, p->cfg[b].seed, p->cfg[b].tol, p->cfg[b].max_iters,
+          (const int*)((const char*)(p->alsP + b) + offsetof(PersArgs, user_init)),
+          host.data() + (size_t)b * cluster_args_bytes());
+      if (sm == 0) return RCP_EINVAL;
+      smax = std::max(smax, sm);
+    }
+    p->clu_smem = smax;
+    if (smax > 220 * 1024) return RCP_EINVAL;
+    if (cudaMemcpy(p->cluArgs, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        prepare_als_cluster_batched(rmax, smax) != cudaSuccess)
+      return RCP_ECUDA;
+  }
   // warm-start items: 3-way tensors with l_n <= 24 and R <= 16
   std::vector<WsItem> ws(C);
   for (int b = 0; b < C; ++b) {

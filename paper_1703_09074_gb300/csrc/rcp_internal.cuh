@@ -322,6 +322,14 @@ cudaError_t launch_backproject(rcp_plan_s* p, double* const* A_dev, double* lamb
 bool als_persistent_fits(const rcp_plan_s* p, bool f32);
 bool als_cluster_fits(const rcp_plan_s* p);
 cudaError_t launch_eig_init(rcp_plan_s* p, const double* B, double* gram, cudaStream_t s);
+size_t cluster_batched_args(int N, int R, const int* l, int rmax, const float* B,
+                            double* const* At, double* lam, float2* facdw, DevState* st,
+                            uint64_t seed, double tol, int max_iters, const int* user_init_dev,
+                            void* out);
+size_t cluster_args_bytes();
+cudaError_t prepare_als_cluster_batched(int rmax, size_t smem);
+cudaError_t launch_als_cluster_batched(const void* dev_args, int count, int rmax, size_t smem,
+                                       cudaStream_t s);
 void plan_ws_free(rcp_plan_s* p);
 rcp_status plan_ws_enqueue(rcp_plan_s* p, const int** flag_dev);
 int64_t bcd_scratch_elems(const rcp_plan_s* p);

@@ -617,6 +617,53 @@ k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, 
   }
 }
 
+// Column sweep over the mode-1 unfolding of an FP32 tensor (L = 1: column j is
+// the contiguous fibre X[:, j]): W[j, c] = sum_i X[i, j] Q[i, c] for the
+// kProjThreads columns of block jb.  Rows are taken 32 at a time: warp w loads
+// the 32-row segments of columns w, w + 8, ... (128 contiguous bytes per load
+// instruction) into a padded shared tile, and thread t then reads column t of
+// the tile (conflict-free) against the staged rows of Q.
+template <int LMAX>
+__device__ __forceinline__ void col_sweep_fibres(const float* __restrict__ T, ModeView v, int l,
+                                                 const double* __restrict__ Q,
+                                                 float* __restrict__ W, int bx, int nb) {
+  extern __shared__ double sm[];
+  constexpr int NT = kProjThreads, TP = kProjThreads + 1;
+  float* Qs = (float*)sm;          // 32 x LMAX
+  float* Xt = Qs + 32 * LMAX;      // 32 x TP
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int64_t jb = bx; jb * NT < v.J; jb += nb) {
+    const int64_t j0 = jb * NT, j = j0 + tid;
+    float acc[LMAX];
+#pragma unroll
+    for (int c = 0; c < LMAX; ++c) acc[c] = 0.0f;
+    for (int64_t i0 = 0; i0 < v.I; i0 += 32) {
+      const int ni = (int)min((int64_t)32, v.I - i0);
+      __syncthreads();
+      for (int k = tid; k < 32 * LMAX; k += NT) {
+        const int ii = k / LMAX, c = k - ii * LMAX;
+        Qs[k] = (ii < ni && c < l) ? (float)Q[(i0 + ii) + v.I * c] : 0.0f;
+      }
+#pragma unroll 4
+      for (int jj = warp; jj < NT; jj += NT / 32) {
+        const int64_t col = j0 + jj;
+        Xt[lane * TP + jj] = (col < v.J && lane < ni) ? __ldg(T + col * v.I + i0 + lane) : 0.0f;
+      }
+      __syncthreads();
+      for (int ii = 0; ii < ni; ++ii) {
+        const float x = Xt[ii * TP + tid];
+#pragma unroll
+        for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(x, Qs[ii * LMAX + c], acc[c]);
+      }
+    }
+    if (j < v.J) {
+#pragma unroll
+      for (int c = 0; c < LMAX; ++c)
+        if (c < l) W[c + (int64_t)l * j] = acc[c];
+    }
+  }
+}
+
 template <int LMAX>
 __global__ void __launch_bounds__(kProjThreads)
 k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
@@ -630,9 +677,14 @@ k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, 
     if (it >= nitems) break;
     const BItem w = items[it];
     const BColSweep p = P[w.b];
-    // Q staged 256 rows at a time: once per column block for I <= 256
-    col_sweep_body<LMAX, float, float, false, kProjThreads, kBatchQRows>(
-        p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr, w.bx, p.nb);
+    if (p.v.L == 1) {
+      // mode 1: columns are contiguous fibres, staged as coalesced tiles
+      col_sweep_fibres<LMAX>(p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, w.bx, p.nb);
+    } else {
+      // Q staged 256 rows at a time: once per column block for I <= 256
+      col_sweep_body<LMAX, float, float, false, kProjThreads, kBatchQRows>(
+          p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr, w.bx, p.nb);
+    }
     __syncthreads();
   }
 }
@@ -664,15 +716,18 @@ cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitem
                                int lmax, const float* const* xptrs, int grid, cudaStream_t s) {
   count_launches(1);
   const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
+  // dynamic shared memory: the staged rows of Q (kBatchQRows x b), or for mode 1
+  // 32 rows of Q and a 32 x (kProjThreads + 1) tile of X, whichever is larger
+  auto smem_for = [](int bb) {
+    return std::max((size_t)kBatchQRows * bb, (size_t)32 * bb + (size_t)32 * (kProjThreads + 1)) *
+           sizeof(float);
+  };
   if (b == 16) {
-    const size_t smem = (size_t)kBatchQRows * 16 * sizeof(float);
-    k_b_col_sweep<16><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+    k_b_col_sweep<16><<<grid, kProjThreads, smem_for(16), s>>>(P, items, nitems, counter, xptrs);
   } else if (b == 24) {
-    const size_t smem = (size_t)kBatchQRows * 24 * sizeof(float);
-    k_b_col_sweep<24><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+    k_b_col_sweep<24><<<grid, kProjThreads, smem_for(24), s>>>(P, items, nitems, counter, xptrs);
   } else if (b == 32) {
-    const size_t smem = (size_t)kBatchQRows * 32 * sizeof(float);
-    k_b_col_sweep<32><<<grid, kProjThreads, smem, s>>>(P, items, nitems, counter, xptrs);
+    k_b_col_sweep<32><<<grid, kProjThreads, smem_for(32), s>>>(P, items, nitems, counter, xptrs);
   } else {
     return cudaErrorInvalidValue;
   }
