@@ -14,7 +14,8 @@ Section 3.3.  Readings where the paper is silent or inconsistent:
 * The number of columns is l_n = min(k + p, I_n, J_n), so Y_n always has full
   column rank for generic data.
 * The sketch of mode n is taken of the current compressed tensor
-  (Algorithm 1, "X <- B_n" after each mode).
+  (Algorithm 1, "X <- B_n" after each mode); ``compress(independent=True)``
+  takes every sketch of X itself, the setting of Theorem 1.
 * ALS starts from seeded N(0,1) factors (stream = mode n, purpose = ALS init,
   row-major l_n x R) for modes 2..N; mode 1 is computed first and needs none.
 * ``norm`` in Algorithm 2 is the column 2-norm, applied every sweep; lambda is
@@ -92,21 +93,30 @@ def range_finder(T, n, l, q, seed, omega="f64", normalize="qr"):
     return Qn
 
 
-def compress(X, R, p, q, seed, omega="f64", normalize="qr", p_modes=None, skip=()):
+def compress(X, R, p, q, seed, omega="f64", normalize="qr", p_modes=None, skip=(),
+             independent=False):
     """Algorithm 1: returns the compressed tensor B and the bases [Q_1, ..., Q_N].
 
     Options of the remark after Algorithm 1: p_modes[n - 1] replaces p for
     mode n, and modes listed in ``skip`` (1-based) are not compressed
-    (Q_n = I, the tensor keeps I_n in that mode)."""
-    T = np.asarray(X, dtype=np.float64)
+    (Q_n = I, the tensor keeps I_n in that mode).
+
+    independent=True is the setting of Theorem 1 (Section 3.1.1): every Q_n is
+    the range finder of the unfolding X_(n) of the input itself (width
+    l_n = min(k + p, I_n, J_n) with J_n the product of the other input
+    dimensions), not of the partly compressed tensor; B = X x_1 Q_1^T ...
+    x_N Q_N^T is then the same chain of mode products."""
+    X = np.asarray(X, dtype=np.float64)
+    T = X
     Qs = []
     for n in range(1, T.ndim + 1):
         if n in skip:
             Qs.append(np.eye(T.shape[n - 1]))
             continue
         pn = p if p_modes is None else p_modes[n - 1]
-        l = sketch_width(R, pn, T.shape, n)
-        Qn = range_finder(T, n, l, q, seed, omega, normalize)
+        src = X if independent else T
+        l = sketch_width(R, pn, src.shape, n)
+        Qn = range_finder(src, n, l, q, seed, omega, normalize)
         Qs.append(Qn)
         T = ttm(T, Qn.T, n)
     return T, Qs
