@@ -93,10 +93,16 @@ enum {
                                   RCP_ESINGULAR instead of RCP_INFO_SHIFTED_QR        */
   RCP_FLAG_MODE_OVERSAMPLE = 4, /* use rcp_config.mode_oversample[n-1] as p for mode n
                                   (the remark after Algorithm 1)                       */
-  RCP_FLAG_LU_NORM = 8         /* normalise the power iterations with the pivoted LU
+  RCP_FLAG_LU_NORM = 8,        /* normalise the power iterations with the pivoted LU
                                   factor of Algorithm 1 steps 8-9 (P L of Y = P L U)
                                   instead of CholeskyQR: the same spans, a different
                                   basis until the final QR of step 12                  */
+  RCP_FLAG_INDEPENDENT = 16    /* the setting of Theorem 1: every mode's range finder
+                                  (steps 5-12) reads the unfolding X_(n) of the input
+                                  itself, not the partly compressed T_n, with
+                                  l_n = min(R + p_n, I_n, prod of the other I_m);
+                                  rcp_sketch then needs X for every mode, and the
+                                  mode products of step 13 are unchanged            */
 };
 
 /* Initial factors of the stage-2 solver on B (Algorithm 2 step 2, Algorithm 3
@@ -290,6 +296,30 @@ rcp_status rcp_profile_read(rcp_plan_t plan, int32_t kind, int32_t mode, int64_t
 rcp_status rcp_test_normals(uint64_t seed, uint32_t stream, uint32_t purpose, int64_t first,
                             int64_t count, double* out_dev, uint32_t* words_dev,
                             float* f32_out_dev, void* cuda_stream);
+
+/* Test hook: the device arithmetic building blocks, elementwise on n inputs
+ * (device arrays of doubles; n = 0 is a no-op).  op:
+ *   RCP_ARITH_DW_ADD   x + y  in double word (two FP32 numbers hi + lo)
+ *   RCP_ARITH_DW_MUL   x * y  in double word
+ *   RCP_ARITH_DW_RCP   1 / x  in double word (x > 0, normal FP32 range)
+ *   RCP_ARITH_DW_SQRT  sqrt x in double word (x > 0)
+ *   RCP_ARITH_RSQRT64  1 / sqrt x in FP64 (x > 0)
+ * The double-word ops first round each input to its nearest double word
+ * (hi = the FP32 rounding of x, lo = the FP32 rounding of x - hi); the result's
+ * components come back as doubles in out_hi_dev / out_lo_dev (out_lo_dev = 0
+ * for RSQRT64).  These operations carry the Gram solves of Algorithm 2 and the
+ * factorisations of the QR steps of Algorithm 1.  y_dev is read by the binary
+ * ops only.  Errors: RCP_EINVAL for an unknown op, n < 0 or a missing array.
+ * cuda_stream: cudaStream_t.  Asynchronous. */
+enum rcp_arith_op {
+  RCP_ARITH_DW_ADD = 0,
+  RCP_ARITH_DW_MUL = 1,
+  RCP_ARITH_DW_RCP = 2,
+  RCP_ARITH_DW_SQRT = 3,
+  RCP_ARITH_RSQRT64 = 4
+};
+rcp_status rcp_test_arith(int32_t op, const double* x_dev, const double* y_dev, int64_t n,
+                          double* out_hi_dev, double* out_lo_dev, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Batched form: many tensors of uneven shapes decomposed together.  Every

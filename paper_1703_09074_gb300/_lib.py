@@ -17,8 +17,10 @@ RCP_OK, RCP_EINVAL, RCP_ENOMEM, RCP_ECUDA, RCP_ESINGULAR, RCP_ENAN, RCP_ETIMEOUT
 RCP_DTYPE_F64, RCP_DTYPE_F32 = 0, 1
 RCP_PREC_F64, RCP_PREC_MIXED = 0, 1
 RCP_FLAG_HOST_STAGING, RCP_FLAG_NO_SHIFT, RCP_FLAG_MODE_OVERSAMPLE, RCP_FLAG_LU_NORM = 1, 2, 4, 8
+RCP_FLAG_INDEPENDENT = 16
 RCP_INIT_RANDN, RCP_INIT_LEARNED, RCP_INIT_EIG = 0, 1, 2
 RCP_SOLVER_ALS, RCP_SOLVER_BCD = 0, 1
+RCP_ARITH_DW_ADD, RCP_ARITH_DW_MUL, RCP_ARITH_DW_RCP, RCP_ARITH_DW_SQRT, RCP_ARITH_RSQRT64 = range(5)
 RCP_INFO_SHIFTED_QR, RCP_INFO_ALS_REGULARISED, RCP_INFO_LEARNED_INIT = 1, 2, 4
 WS_LPAD, WS_RPAD = 24, 16
 MLP_IN, MLP_HIDDEN, MLP_OUT = 13824, 512, 1152
@@ -107,6 +109,9 @@ SIGNATURES = {
     "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_uint64, P, P, P]),
+    "rcp_test_arith": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "rcp_test_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_int64, ctypes.c_int64, P, P, P, P]),
 }

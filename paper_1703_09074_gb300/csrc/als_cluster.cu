@@ -119,17 +119,6 @@ __device__ __forceinline__ dwf ld_dw(const float2* p) {
 
 __device__ __forceinline__ void st_dw(float2* p, dwf v) { *p = make_float2(v.hi, v.lo); }
 
-// sqrt of a positive double word s: the FP32 square root r of s.hi and one
-// correction (s - r^2) / (2 r) formed with the exact square of r (the
-// Karp-Markstein form of a Newton step); relative error about 2^-46.
-__device__ __forceinline__ dwf dw_sqrt(dwf s) {
-  const float r = __fsqrt_rn(s.hi);
-  const float r2 = __fmul_rn(r, r);
-  const float r2l = __fmaf_rn(r, r, -r2);
-  const float d = __fadd_rn(__fsub_rn(__fsub_rn(s.hi, r2), r2l), s.lo);
-  return dw_fast_two_sum(r, __fmul_rn(d, __fmul_rn(0.5f, fast_rcp(r))));
-}
-
 // Sum over the 32 lanes of v[0..31] with lane L receiving the total of v[L]:
 // a reduce-scatter of five butterfly steps (31 shuffles).
 template <int KR>
@@ -535,12 +524,15 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   for (int m = 1; m < N; ++m) gram_f32<KR>(F32, G32, m, a.l[m], R, tid);
   double nb2 = 0.0;
   for (int w = 0; w < kWarps; ++w) nb2 += red[2 * w] + red[2 * w + 1];
-  const double inv_nb2 = 1.0 / nb2;
+  // |B|^2 and its reciprocal in double word for the per-sweep fit (FP64
+  // instructions are long-latency on this part; the fit's chain stays in FP32)
+  const dwf nb2_dw = dw_from_double(nb2);
+  const dwf inv_nb2 = dw_rcp(nb2_dw);
   __syncthreads();
   build_V(N, R, 0, G32, Vdw, tid);
   __syncthreads();
 
-  double rho_prev = 0.0;
+  dwf rho_prev = {0.0f, 0.0f};
   int buf = 0, done = 0;
   for (int it = 1; it <= a.max_iters && !done; ++it) {
     for (int n = 0; n < N; ++n) {
@@ -593,19 +585,29 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
       cluster_sync();
       // ---- phase 4 (identical in every CTA): column norms, normalisation, FP32 copy
       {
+        // warp w: columns w, w + 12, w + 24 (those below R; the count is warp-uniform)
+        const int ncol = warp < R ? (R - warp + kWarps - 1) / kWarps : 0;
         dwf xv[3], nu2[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           const int r = warp + kWarps * t;
-          xv[t] = (r < R && lane < ln) ? ld_dw(&fd[lane * kFP + r]) : dwf{0.0f, 0.0f};
+          xv[t] = (t < ncol && lane < ln) ? ld_dw(&fd[lane * kFP + r]) : dwf{0.0f, 0.0f};
           nu2[t] = dw_mul(xv[t], xv[t]);
         }
-#pragma unroll
-        for (int t = 0; t < 3; ++t) nu2[t] = warp_sum_dw(nu2[t]);
+        if (ncol > 2) {
+          nu2[0] = warp_sum_dw(nu2[0]);
+          nu2[1] = warp_sum_dw(nu2[1]);
+          nu2[2] = warp_sum_dw(nu2[2]);
+        } else if (ncol == 2) {
+          nu2[0] = warp_sum_dw(nu2[0]);
+          nu2[1] = warp_sum_dw(nu2[1]);
+        } else if (ncol == 1) {
+          nu2[0] = warp_sum_dw(nu2[0]);
+        }
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           const int r = warp + kWarps * t;
-          if (r < R) {
+          if (t < ncol) {
             const bool pos = nu2[t].hi > 0.0f;
             const dwf nu = pos ? dw_sqrt(nu2[t]) : dwf{0.0f, 0.0f};
             const dwf inv = pos ? dw_rcp(nu) : dwf{0.0f, 0.0f};   // a zero column stays zero
@@ -635,31 +637,33 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
           bh = dw_add(bh, dw_mul(g, dw_mul(ld_dw(&lamd[r]), ld_dw(&lamd[c]))));
         }
         bh = warp_sum_dw(bh);
-        if (lane == 0) {
-          red[2 * warp] = (double)bh.hi;
-          red[2 * warp + 1] = (double)bh.lo;
-        }
+        float2* red2 = (float2*)red;
+        if (lane == 0) red2[warp] = make_float2(bh.hi, bh.lo);
         __syncthreads();
-        if (tid == 0) {
-          double bhat = 0.0;
-          for (int w = 0; w < kWarps; ++w) bhat += red[2 * w] + red[2 * w + 1];
-          dwf ip = {0.0f, 0.0f};
-          for (int c = 0; c < C; ++c) ip = dw_add(ip, ld_dw(&ipb[buf * 16 + c]));
-          const double ipd = dw_to_double(ip);
-          const double rho = 1.0 - (nb2 + bhat - 2.0 * ipd) * inv_nb2;
-          const bool conv = fabs(rho - rho_prev) < a.tol;
-          int dn = conv ? 1 : (it >= a.max_iters ? 2 : 0);
-          if (!isfinite(rho) || sh_bad) dn = 3;
-          rho_prev = rho;
-          sh_done = dn;
-          if (crank == 0) {
-            st->fit = rho;
-            st->ip = ipd;
-            st->fit_prev = rho;
-            st->als_iters = it;
-            st->norm_b2 = nb2;
-            if (!isfinite(rho) || sh_bad) set_status(st, RCP_ENAN);
-            if (dn) st->als_done = dn == 3 ? 2 : dn;
+        if (warp == 0) {
+          // rho = 1 - (|B|^2 + |Bhat|^2 - 2 <Bhat, B>) / |B|^2, in double word
+          const dwf bhat = warp_sum_dw(lane < kWarps ? ld_dw(&red2[lane]) : dwf{0.0f, 0.0f});
+          const dwf ip = warp_sum_dw(lane < C ? ld_dw(&ipb[buf * 16 + lane]) : dwf{0.0f, 0.0f});
+          if (lane == 0) {
+            const dwf resid = dw_add(dw_add(nb2_dw, bhat), {-2.0f * ip.hi, -2.0f * ip.lo});
+            const dwf rho = dw_add({1.0f, 0.0f}, dw_neg(dw_mul(resid, inv_nb2)));
+            const dwf drho = dw_add(rho, dw_neg(rho_prev));
+            const bool fin = isfinite(rho.hi) && isfinite(rho.lo);
+            const bool conv = fabs((double)drho.hi + (double)drho.lo) < a.tol;
+            int dn = conv ? 1 : (it >= a.max_iters ? 2 : 0);
+            if (!fin || sh_bad) dn = 3;
+            rho_prev = rho;
+            sh_done = dn;
+            if (crank == 0) {
+              const double rhod = dw_to_double(rho);
+              st->fit = rhod;
+              st->ip = dw_to_double(ip);
+              st->fit_prev = rhod;
+              st->als_iters = it;
+              st->norm_b2 = nb2;
+              if (!fin || sh_bad) set_status(st, RCP_ENAN);
+              if (dn) st->als_done = dn == 3 ? 2 : dn;
+            }
           }
         }
         __syncthreads();

@@ -9,8 +9,9 @@
 // The building blocks are the error-free transformations of Knuth (TwoSum),
 // Dekker (Fast2Sum) and the FMA product error, combined as in Joldes, Muller
 // and Popescu, "Tight and rigorous error bounds for basic building blocks of
-// double-word arithmetic", ACM TOMS 44(2), 2017: the sum has relative error at
-// most 3u^2 + 13u^3 and the product at most 4u^2, u = 2^-24.  The reciprocal
+// double-word arithmetic", ACM TOMS 44(2), 2017: the sum (AccurateDWPlusDW)
+// has relative error at most 3u^2 + 13u^3 and the product (DWTimesDW2, with the
+// lo * lo term) at most 5u^2, u = 2^-24.  The reciprocal
 // is Newton's iteration from the hardware approximation, its residual 1 - y r
 // formed with an FMA (Markstein 1990; Karp and Markstein 1997).  Every
 // operation is an explicitly rounded intrinsic, so the compiler can neither
@@ -63,6 +64,20 @@ __device__ __forceinline__ dwf dw_rcp(dwf y) {
   r = __fmaf_rn(r, __fmaf_rn(-y.hi, r, 1.0f), r);
   const float e = __fmaf_rn(-y.lo, r, __fmaf_rn(-y.hi, r, 1.0f));
   return dw_fast_two_sum(r, __fmul_rn(r, e));
+}
+
+// sqrt of a positive double word s: the FP32 square root r of s.hi and one
+// correction (s - r^2) / (2 r) formed with the exact square of r (the
+// Karp-Markstein form of a Newton step); relative error about 2^-46.
+__device__ __forceinline__ dwf dw_sqrt(dwf s) {
+  const float r = __fsqrt_rn(s.hi);
+  const float r2 = __fmul_rn(r, r);
+  const float r2l = __fmaf_rn(r, r, -r2);
+  const float d = __fadd_rn(__fsub_rn(__fsub_rn(s.hi, r2), r2l), s.lo);
+  float q;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(r));
+  q = __fmaf_rn(q, __fmaf_rn(-r, q, 1.0f), q);  // 1 / r, one Newton step
+  return dw_fast_two_sum(r, __fmul_rn(d, __fmul_rn(0.5f, q)));
 }
 
 // Nearest double-word of a double inside the FP32 exponent range.

@@ -76,3 +76,6 @@ def test_null_plan_handling(lib):
     assert lib.rcp_status_str(0) == b"ok"
     assert lib.rcp_status_str(99) == b"unknown status"
     assert lib.rcp_test_normals(0, 0, 0, -1, 1, None, None, None, None) == RCP_EINVAL
+    assert lib.rcp_test_arith(7, None, None, 1, None, None, None) == RCP_EINVAL
+    assert lib.rcp_test_arith(0, None, None, -1, None, None, None) == RCP_EINVAL
+    assert lib.rcp_test_arith(1, None, None, 4, None, None, None) == RCP_EINVAL
