@@ -32,7 +32,7 @@ class Plan:
     def __init__(self, dims, rank, oversample=10, power_iters=2, tol=1e-10, max_iters=50,
                  seed=0, in_dtype=torch.float32, precision="f64", host_staging=False,
                  stream=None, init="randn", solver="als", wait_budget=0, no_shift=False,
-                 skip_modes=(), mode_oversample=None, lu_norm=False):
+                 skip_modes=(), mode_oversample=None, lu_norm=False, independent=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.N = len(self.dims)
@@ -53,6 +53,7 @@ class Plan:
         cfg.flags = ((_lib.RCP_FLAG_HOST_STAGING if host_staging else 0) |
                      (_lib.RCP_FLAG_NO_SHIFT if no_shift else 0) |
                      (_lib.RCP_FLAG_LU_NORM if lu_norm else 0) |
+                     (_lib.RCP_FLAG_INDEPENDENT if independent else 0) |
                      (_lib.RCP_FLAG_MODE_OVERSAMPLE if mode_oversample is not None else 0))
         for n in skip_modes:   # 1-based modes left uncompressed
             cfg.skip_modes |= 1 << (int(n) - 1)

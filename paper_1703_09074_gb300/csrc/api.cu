@@ -176,7 +176,7 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   if (cfg->solver != RCP_SOLVER_ALS && cfg->solver != RCP_SOLVER_BCD) return RCP_EINVAL;
   if (cfg->wait_budget < 0) return RCP_EINVAL;
   if (cfg->flags & ~(RCP_FLAG_HOST_STAGING | RCP_FLAG_NO_SHIFT | RCP_FLAG_MODE_OVERSAMPLE |
-                     RCP_FLAG_LU_NORM))
+                     RCP_FLAG_LU_NORM | RCP_FLAG_INDEPENDENT))
     return RCP_EINVAL;
   if (cfg->skip_modes & ~((1 << N) - 1)) return RCP_EINVAL;
   if ((cfg->flags & RCP_FLAG_LU_NORM) && cfg->precision != RCP_PREC_F64) return RCP_EINVAL;
@@ -191,10 +191,11 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     // every l_n = min(R + p, I_n, J_n) must lie in [R, RCP_MAX_L] (checked before any CUDA call)
     int64_t cur[kMaxN];
     for (int n = 0; n < N; ++n) cur[n] = cfg->dims[n];
+    const bool indep = (cfg->flags & RCP_FLAG_INDEPENDENT) != 0;
     for (int n = 0; n < N; ++n) {
       int64_t J = 1;
       for (int m = 0; m < N; ++m)
-        if (m != n) J *= cur[m];
+        if (m != n) J *= indep ? cfg->dims[m] : cur[m];
       if ((cfg->flags & RCP_FLAG_MODE_OVERSAMPLE) && cfg->mode_oversample[n] < 0) return RCP_EINVAL;
       const int64_t l = mode_width(cfg, n, cur[n], J);
       if (l < cfg->rank || l > RCP_MAX_L) return RCP_EINVAL;
@@ -224,13 +225,20 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   int64_t cur[kMaxN];
   for (int n = 0; n < N; ++n) cur[n] = p->dims[n] = cfg->dims[n];
   int64_t bufmax = 1, Imax = 1, part_max = 1, gpart_max = 1, norm_max = 1, red_max = 1;
+  const bool indep = (cfg->flags & RCP_FLAG_INDEPENDENT) != 0;
   for (int n = 0; n < N; ++n) {
     int64_t J = 1, L = 1, Rt = 1;
     for (int m = 0; m < N; ++m)
       if (m != n) J *= cur[m];
     for (int m = 0; m < n; ++m) L *= cur[m];
     for (int m = n + 1; m < N; ++m) Rt *= cur[m];
-    const int64_t l = mode_width(cfg, n, cur[n], J);
+    // mode n of X itself: the operand of the independent sketches
+    ModeView xv{1, p->dims[n], 1, 1};
+    for (int m = 0; m < n; ++m) xv.L *= p->dims[m];
+    for (int m = n + 1; m < N; ++m) xv.Rt *= p->dims[m];
+    xv.J = xv.L * xv.Rt;
+    p->xview[n] = xv;
+    const int64_t l = mode_width(cfg, n, cur[n], indep ? xv.J : J);
     if (l < cfg->rank || l > RCP_MAX_L) {
       delete p;
       return RCP_EINVAL;
@@ -245,6 +253,13 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     const int ng = project_grid(p->view[n], p->nsm);
     gpart_max = std::max(gpart_max, (int64_t)ng * (l * (l + 1) / 2));
     norm_max = std::max(norm_max, (int64_t)ns * ((cur[n] + 255) / 256));
+    if (indep) {  // the range finder's W and partials over X_(n)
+      bufmax = std::max(bufmax, xv.J * l);
+      const int nsx = sketch_splits(xv, p->nsm);
+      part_max = std::max(part_max, (int64_t)nsx * xv.I * l);
+      gpart_max = std::max(gpart_max, (int64_t)project_grid(xv, p->nsm) * (l * (l + 1) / 2));
+      norm_max = std::max(norm_max, (int64_t)nsx * ((xv.I + 255) / 256));
+    }
     cur[n] = l;
   }
   p->core_elems = 1;
@@ -312,7 +327,10 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
   }
   if (cfg->flags & RCP_FLAG_LU_NORM) {
     int64_t mrows = 1;
-    for (int n = 0; n < N; ++n) mrows = std::max(mrows, std::max(p->view[n].I, p->view[n].J));
+    for (int n = 0; n < N; ++n) {
+      mrows = std::max(mrows, std::max(p->view[n].I, p->view[n].J));
+      if (indep) mrows = std::max(mrows, p->xview[n].J);
+    }
     A(dalloc((uint8_t**)&p->lu_used, mrows));
     A(dalloc(&p->lu_cval, 2 * (int64_t)p->nsm));
     A(dalloc((int64_t**)&p->lu_cidx, 2 * (int64_t)p->nsm));
@@ -357,11 +375,12 @@ rcp_status sketch_f64(rcp_plan_t p, const void* X, int mode) {
   cudaStream_t s = p->stream;
   const bool ns = (p->cfg.flags & RCP_FLAG_NO_SHIFT) != 0;
   const int n0 = mode - 1;
-  const ModeView v = p->view[n0];
+  const bool indep = (p->cfg.flags & RCP_FLAG_INDEPENDENT) != 0;
+  const ModeView v = indep ? p->xview[n0] : p->view[n0];
   const int l = p->l[n0];
-  int dt = 0;
-  const void* T = mode_input(p, X, mode, &dt);
-  double* W = mode_output(p, mode);
+  int dt = p->cfg.in_dtype;
+  const void* T = indep ? X : mode_input(p, X, mode, &dt);
+  double* W = mode_output(p, mode);  // scratch here; rcp_compress writes T_{n+1} there later
   const int nsplit = sketch_splits(v, p->nsm);
   const int64_t ny = v.I * l;
   // Y = T_(n) Omega_n (step 6); mode 1 also accumulates |X|^2
@@ -430,9 +449,10 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
   cudaStream_t s = p->stream;
   const bool ns = (p->cfg.flags & RCP_FLAG_NO_SHIFT) != 0;
   const int n0 = mode - 1;
-  const ModeView v = p->view[n0];
+  const bool indep = (p->cfg.flags & RCP_FLAG_INDEPENDENT) != 0;
+  const ModeView v = indep ? p->xview[n0] : p->view[n0];
   const int l = p->l[n0];
-  const float* T = (const float*)(mode == 1 ? X : p->bufT[(mode - 2) % 2]);
+  const float* T = (const float*)(mode == 1 || indep ? X : p->bufT[(mode - 2) % 2]);
   float* W = (float*)mode_output(p, mode);
   const int64_t ny = v.I * l;
   if (mode == 1 && p->tc1) {
@@ -502,7 +522,7 @@ extern "C" {
 
 rcp_status rcp_sketch(rcp_plan_t p, const void* X, int32_t mode, double* Q_out) {
   if (!valid_plan(p) || mode < 1 || mode > p->N) return RCP_EINVAL;
-  if (mode == 1 && !X) return RCP_EINVAL;
+  if ((mode == 1 || (p->cfg.flags & RCP_FLAG_INDEPENDENT)) && !X) return RCP_EINVAL;
   if (mode == 1) {
     p->sketched = p->compressed = 0;  // a new decomposition starts at mode 1
   } else if (p->compressed != mode - 1) {

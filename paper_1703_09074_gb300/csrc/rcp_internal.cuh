@@ -62,6 +62,7 @@ struct rcp_plan_s {
   int64_t dims[rcp::kMaxN];
   int l[rcp::kMaxN];
   rcp::ModeView view[rcp::kMaxN];
+  rcp::ModeView xview[rcp::kMaxN];   // mode n of the input X itself (independent sketches)
   int64_t core_elems;  // l_1 ... l_N
   int nsm;
 

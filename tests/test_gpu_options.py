@@ -90,3 +90,48 @@ def test_invalid_options_are_rejected():
         Plan((100, 30, 20), 3, 4, 1, skip_modes=(1,), in_dtype=torch.float64)
     with pytest.raises(RcpError):   # the LU variant is a plain-path option
         Plan((100, 30, 20), 3, 4, 1, lu_norm=True, in_dtype=torch.float32, precision="mixed")
+
+
+# ---------------------------------------------------------------- independent sketches
+
+@pytest.mark.parametrize("dims,R,p,q", [((60, 45, 40), 4, 6, 1), ((30, 24, 20, 16), 3, 5, 2)])
+def test_independent_sketches_match_oracle(dims, R, p, q):
+    # Theorem 1's setting: every Q_n from X_(n) itself; B by the same chain
+    w = synth.cp_tensor(dims, R, seed=7, snr_db=20.0, dtype="f64", p=p, q=q)
+    g = _run(w, R, p, q, 10, 4, independent=True)
+    o = oracle.rcp.rcp_als(w.X, R, p, q, 0.0, 10, 4, independent=True)
+    _check(g, o)
+
+
+def test_independent_with_lu_skip_and_mode_oversampling():
+    w = synth.cp_tensor((40, 24, 36), 3, seed=8, snr_db=15.0, dtype="f32", p=4, q=1)
+    g = _run(w, 3, 4, 1, 10, 6, independent=True, lu_norm=True, skip_modes=(2,),
+             mode_oversample=(2, 0, 6))
+    o = oracle.rcp.rcp_als(w.X, 3, 4, 1, 0.0, 10, 6, independent=True, normalize="lu",
+                           skip=(2,), p_modes=(2, 0, 6))
+    assert [q.shape[1] for q in g["Q"]] == [5, 24, 9]
+    _check(g, o)
+
+
+def test_independent_sketches_mixed_form():
+    # mode 1 on the tensor cores, modes 2-3 by the FP32 sweeps over X itself
+    w = synth.cp_tensor((64, 48, 40), 4, seed=9, snr_db=25.0, dtype="f32", p=6, q=1)
+    g = _run(w, 4, 6, 1, 30, 2, precision="mixed", independent=True)
+    o = oracle.rcp.rcp_als(w.X, 4, 6, 1, 0.0, 30, 2, independent=True, omega="f32")
+    assert g["res"]["device_status"] == 0
+    for Qg, Qo in zip(g["Q"], o["Q"]):
+        # top-R principal angles between the GPU and oracle bases
+        s = np.linalg.svd(Qo.T @ Qg, compute_uv=False)
+        assert s[:4].min() > 1 - 1e-6
+    assert g["res"]["norm_x2"] == pytest.approx(o["normX2"], rel=1e-6)
+    assert g["res"]["rel_err"] == pytest.approx(o["rel_err_identity"], rel=1e-3)
+
+
+def test_independent_plan_needs_x_for_every_mode():
+    from paper_1703_09074_gb300 import Plan, _lib
+    w = synth.cp_tensor((20, 16, 12), 2, seed=1, snr_db=20.0, dtype="f64", p=2, q=0)
+    X = torch.from_numpy(np.ascontiguousarray(w.kolda)).cuda()
+    with Plan(w.dims, 2, 2, 0, in_dtype=torch.float64, independent=True) as pl:
+        pl.sketch(X, 1)
+        pl.compress(X, 1)
+        assert pl.lib.rcp_sketch(pl.h, None, 2, None) == _lib.RCP_EINVAL
