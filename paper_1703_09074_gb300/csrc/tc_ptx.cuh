@@ -1,7 +1,7 @@
 // Inline-PTX helpers for the 5th-generation tensor cores of sm_103a (tcgen05):
 // tensor-memory allocation, shared-memory matrix descriptors, kind::tf32 and
-// kind::f16 (BF16) MMA issue, completion tracking through mbarriers (with bounded waits), and
-// tensor-memory loads.  Written from the public PTX ISA description of
+// kind::f16 (BF16) MMA issue, completion tracking through mbarriers (with
+// bounded waits), tensor-memory loads, and 2D TMA tile loads.  Written from the public PTX ISA description of
 // tcgen05; no other code is involved.
 #pragma once
 
@@ -49,6 +49,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
 // Make this thread's generic-proxy shared-memory writes visible to the tensor cores.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arrive on the mbarrier (one of its expected arrivals), release semantics.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive and raise the barrier's expected transaction count by `bytes` (the
+// bytes of the bulk copies that will complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// ---------------------------------------------------------------- TMA
+// 2D tiled bulk copy global -> shared through a tensor map (a __grid_constant__
+// kernel parameter); the bytes complete on the mbarrier.  x is the innermost
+// coordinate; x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }
 
 // ---------------------------------------------------------------- tensor memory

@@ -27,6 +27,9 @@
 //   product T_2 = X x_1 Q_1^T (step 13).  M = J (128 columns j per block),
 //   N = l, K = I: K is X's contiguous direction, so 16-byte loads go straight
 //   into the swizzled tile.  Persistent CTAs walk j-blocks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "rcp_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -476,6 +479,215 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
   if (warp == 0) tc::tmem_dealloc(tbase, NCOLS);
 }
 
+// Column sweep with TMA-fed stages (the form used whenever the tensor maps
+// can be built).  Per 32-row chunk kc of X's contiguous direction i and block
+// of 128 columns j:
+//   producer (warp 0)   one thread: the 128 x 32 tile of X and the 2NP x 32
+//                       tile of [Q^T hi; Q^T lo] land by TMA in the 128-byte
+//                       swizzled K-major layout the MMA reads;
+//   converters (2-5)    split the X tile in place into its TF32 truncation and
+//                       write the remainder to a second tile (same layout);
+//   issuer (warp 1)     one thread: X_hi [Q_hi | Q_lo] (N = 2 NP) and X_lo Q_hi
+//                       (N = NP) into the same accumulator, so columns
+//                       [0, NP) collect hi*hi + lo*hi and [NP, 2 NP) hi*lo;
+//   epilogue (6-9)      the sum of the two halves, written out; two
+//                       accumulators, so block b's epilogue overlaps block
+//                       b + 1's MMAs.
+// X is read once, each element written and read twice in shared memory (the
+// split) and read twice by the tensor cores: about 29 bytes of shared-memory
+// traffic per element with the B tiles.
+constexpr int kColsThreads = 320;
+constexpr int kEpiPitchPad = 1;
+
+template <int NP, int STAGES, bool TTM>
+__global__ void __launch_bounds__(kColsThreads, 1)
+k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+              int64_t J, int l, int nkc, float* __restrict__ out, DevState* st) {
+  constexpr uint32_t kA = kATile;
+  constexpr uint32_t kB = 2 * NP * 128;
+  constexpr uint32_t kStage = 2 * kA + kB;
+  constexpr uint32_t NACC = 2 * NP;          // tensor-memory columns of one accumulator
+  constexpr uint32_t IDESC_W = tc::idesc_tf32(128, 2 * NP);
+  constexpr uint32_t IDESC_N = tc::idesc_tf32(128, NP);
+  constexpr int EP = NP + kEpiPitchPad;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* ep = (float*)(sm + STAGES * kStage);  // TTM epilogue rows (4 warps x 32 rows x EP)
+  __shared__ uint64_t full[STAGES], conv[STAGES], empty[STAGES], accf[2], acce[2];
+  __shared__ uint32_t tbase_sh;
+  __shared__ volatile int abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], 4);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4);
+    }
+    abort_sh = 0;
+    tc::fence_mbar_init();
+    tc::tma_prefetch_desc(&tmX);
+    tc::tma_prefetch_desc(&tmQ);
+  }
+  if (warp == 1) tc::tmem_alloc(&tbase_sh, 2 * NACC);
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
+  const uint32_t tbase = tbase_sh;
+
+  const int64_t njb = (J + 127) / 128;
+  const int64_t nblk = njb > blockIdx.x ? (njb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t total = nblk * nkc;
+  bool ok = true;
+  auto fail = [&]() {
+    ok = false;
+    abort_sh = 1;
+  };
+
+  if (warp == 0) {
+    // ---- producer
+    int64_t issued = 0;
+    if (lane == 0) {
+      for (int64_t g = 0; g < total && !abort_sh; ++g) {
+        const int s = (int)(g % STAGES);
+        if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
+        const int kc = (int)(g % nkc);
+        uint8_t* A = sm + s * kStage;
+        tc::mbar_arrive_expect_tx(&full[s], kA + kB);
+        tc::tma_load_2d(A, &tmX, 32 * kc, (int32_t)(jblk * 128), &full[s]);
+        tc::tma_load_2d(A + 2 * kA, &tmQ, 32 * kc, 0, &full[s]);
+        issued = g + 1;
+      }
+      // every copy issued has landed before the CTA may leave (bounded)
+      for (int64_t g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1), kWaitBudget)) fail();
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    int64_t issued = 0;
+    if (lane == 0) {
+      for (int64_t g = 0; g < total && !abort_sh; ++g) {
+        const int s = (int)(g % STAGES);
+        const int64_t bl = g / nkc;
+        const int kc = (int)(g % nkc);
+        const int acc = (int)(bl & 1);
+        if (kc == 0 && bl >= 2 &&
+            !tc::mbar_wait(&acce[acc], (uint32_t)((bl / 2 - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        if (!tc::mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        tc::tc_fence_after_sync();
+        const uint32_t d = tbase + (uint32_t)acc * NACC;
+        const uint32_t ah = tc::smem_u32(sm + s * kStage);
+        const uint32_t al = ah + kA;
+        const uint32_t bq = ah + 2 * kA;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          tc::mma_tf32(d, tc::desc_kmajor_sw128(ah + 32u * k), tc::desc_kmajor_sw128(bq + 32u * k),
+                       IDESC_W, (kc > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          tc::mma_tf32(d, tc::desc_kmajor_sw128(al + 32u * k), tc::desc_kmajor_sw128(bq + 32u * k),
+                       IDESC_N, 1u);
+        tc::mma_commit(&empty[s]);
+        if (kc == nkc - 1) tc::mma_commit(&accf[acc]);
+        issued = g + 1;
+      }
+      // the tensor cores are done with every stage before the CTA may leave
+      for (int64_t g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&empty[g % STAGES], (uint32_t)((g / STAGES) & 1), kWaitBudget)) fail();
+    }
+  } else if (warp < 6) {
+    // ---- converters: 128 threads, 8 float4 of the 1024 in a tile each
+    const int t = tid - 64;
+    for (int64_t g = 0; g < total && !abort_sh; ++g) {
+      const int s = (int)(g % STAGES);
+      if (!tc::mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      float4* A = (float4*)(sm + s * kStage);
+      float4* L = (float4*)(sm + s * kStage + kA);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int idx = t + 128 * k;
+        const float4 v = A[idx];
+        float4 h, lo;
+        h.x = tf32_hi(v.x); lo.x = v.x - h.x;
+        h.y = tf32_hi(v.y); lo.y = v.y - h.y;
+        h.z = tf32_hi(v.z); lo.z = v.z - h.z;
+        h.w = tf32_hi(v.w); lo.w = v.w - h.w;
+        A[idx] = h;
+        L[idx] = lo;
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[s]);
+    }
+  } else {
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    for (int64_t bl = 0; bl < nblk && !abort_sh; ++bl) {
+      const int acc = (int)(bl & 1);
+      if (!tc::mbar_wait(&accf[acc], (uint32_t)((bl / 2) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      tc::tc_fence_after_sync();
+      const int64_t jblk = blockIdx.x + bl * gridDim.x;
+      const int64_t j = jblk * 128 + 32 * q + lane;
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * NACC;
+#pragma unroll
+      for (int cg = 0; cg < NP / 32; ++cg) {
+        float a[32], b[32];
+        tc::tmem_ld32(ta + (uint32_t)(cg * 32), a);
+        tc::tmem_ld32(ta + (uint32_t)(NP + cg * 32), b);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int c = cg * 32 + k;
+          const float v = a[k] + b[k];
+          if (TTM) {
+            ep[(32 * q + lane) * EP + c] = v;
+          } else if (c < l && j < J) {
+            out[(int64_t)c * J + j] = v;
+          }
+        }
+      }
+      tc::tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[acc]);
+      if (TTM) {
+        // rows j0 .. j0 + 31 of the row-major J x l output are one contiguous run
+        const int64_t j0 = jblk * 128 + 32 * q;
+        const int64_t nrow = J - j0 < 32 ? J - j0 : 32;
+        const int64_t n = nrow > 0 ? nrow * l : 0;
+        float* o = out + j0 * l;
+        for (int64_t e = lane; e < n; e += 32) {
+          const int r = (int)(e / l), c = (int)(e - (int64_t)r * l);
+          o[e] = ep[(32 * q + r) * EP + c];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (!ok) set_status(st, RCP_ETIMEOUT);
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tbase, 2 * NACC);
+}
+
 // QT = Q^T in FP32 split into TF32 hi + lo, padded with zeros to NP x Ipad.
 __global__ void k_q_to_qt32(const double* __restrict__ Q, int64_t I, int l, int NP, int64_t Ipad,
                             float* __restrict__ QTh, float* __restrict__ QTl) {
@@ -524,6 +736,52 @@ cudaError_t cols_launch(const float* X, int64_t I, int64_t J, int l, int64_t Ipa
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+// (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D FP32 tensor map over a row-major d1 x d0 array (row pitch d0), box
+// b1 x 32 with the 128-byte swizzle; out-of-range elements read as zero.
+bool tmap_2d_f32(CUtensorMap* m, const float* base, uint64_t d0, uint64_t d1, uint32_t b1) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc || ((uintptr_t)base & 15) || (d0 * 4) % 16) return false;
+  const cuuint64_t dims[2] = {d0, d1};
+  const cuuint64_t strides[1] = {d0 * 4};
+  const cuuint32_t box[2] = {32, b1};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NP, int STAGES, bool TTM>
+cudaError_t cols_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmQ, int64_t J, int l,
+                            int nkc, float* out, DevState* st, int grid, cudaStream_t s) {
+  auto kern = k_tc_cols_tma<NP, STAGES, TTM>;
+  const int smem = STAGES * (2 * kATile + 2 * NP * 128) +
+                   (TTM ? 4 * 32 * (NP + kEpiPitchPad) * 4 : 0) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<grid, kColsThreads, smem, s>>>(tmX, tmQ, J, l, nkc, out, st);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool tc_mode1_supported(int64_t I, int l) { return l <= 64 && I % 4 == 0 && I <= 4096; }
@@ -565,6 +823,27 @@ cudaError_t launch_tc_rows(const float* X, int64_t I, int64_t J, int l, uint64_t
 cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const float* QT, float* out,
                            bool ttm, DevState* st, int grid, cudaStream_t s) {
   const int64_t Ipad = tc_ipad(I);
+  {
+    // the TMA-fed form: one CTA per SM, persistent over the 128-column blocks
+    const int NP = tc_np(l);
+    CUtensorMap tmX, tmQ;
+    if (tmap_2d_f32(&tmX, X, (uint64_t)I, (uint64_t)J, 128) &&
+        tmap_2d_f32(&tmQ, QT, (uint64_t)Ipad, (uint64_t)(2 * NP), (uint32_t)(2 * NP))) {
+      int nsm = 0, dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaGetLastError();
+      const int64_t njb = (J + 127) / 128;
+      const int g = (int)(njb < nsm ? njb : nsm);
+      const int nkc = (int)(Ipad / 32);
+      if (NP == 32) {
+        if (ttm) return cols_tma_launch<32, 4, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        return cols_tma_launch<32, 4, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      }
+      if (ttm) return cols_tma_launch<64, 3, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      return cols_tma_launch<64, 3, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+    }
+  }
   if (tc_np(l) == 32) {
     if (ttm) return cols_launch<32, true>(X, I, J, l, Ipad, QT, out, st, grid, s);
     return cols_launch<32, false>(X, I, J, l, Ipad, QT, out, st, grid, s);
