@@ -315,10 +315,12 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     p->tc1 = !mode_skipped(cfg, 0) && tc_mode1_supported(p->dims[0], p->l[0]);
     int64_t p32 = 1;
     if (p->tc1) {
-      int ns = 0;
-      int64_t jc = 0;
+      // partials of either row sweep (register-staged or TMA-fed)
+      int ns = 0, nb = 0, rb = 0, ns2 = 0;
+      int64_t jc = 0, cper = 0;
       tc_rows_split(p->dims[0], p->view[0].J, p->nsm, &ns, &jc);
-      p32 = (int64_t)ns * p->dims[0] * p->l[0];
+      tc_rows_tma_shape(p->dims[0], p->view[0].J, p->nsm, &nb, &rb, &ns2, &cper);
+      p32 = (int64_t)std::max(ns, ns2) * p->dims[0] * p->l[0];
     }
     p->part32_elems = p32;
     A(dalloc(&p->part32, p32));
@@ -456,14 +458,19 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
   float* W = (float*)mode_output(p, mode);
   const int64_t ny = v.I * l;
   if (mode == 1 && p->tc1) {
+    // TMA-fed sweeps when X allows tensor maps (and the rows of the split W,
+    // J floats each, start on 16-byte boundaries), else the register-staged ones
+    const bool tma = tc_tma_ok(T) && v.J % 4 == 0;
     int nsplit = 0;
     int64_t jchunk = 0;
     tc_rows_split(v.I, v.J, p->nsm, &nsplit, &jchunk);
     const int cgrid = tc_cols_grid(v.J, p->nsm);
     {
+      // the sketch keeps the register-staged sweep: drawing Omega_1 per chunk is
+      // its cost, and two CTAs per SM spread it over twice the warps
       Span sp(p, RCP_KT_SKETCH, mode);
-      RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, jchunk,
-                             p->part32, p->normpart, p->dstate, s));
+      RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit,
+                             jchunk, p->part32, p->normpart, p->dstate, s));
     }
     RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
     const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA
@@ -473,12 +480,17 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
       RCP_TRY(launch_q_to_qt32(p->Y, v.I, l, p->QT32, s));
       {
         Span sp(p, RCP_KT_PROJECT, mode);
-        RCP_TRY(launch_tc_cols(T, v.I, v.J, l, p->QT32, W, false, p->dstate, cgrid, s));
+        RCP_TRY(launch_tc_cols(T, v.I, v.J, l, p->QT32, W, false, p->dstate, cgrid, s, tma, tma));
       }
       {
         Span sp(p, RCP_KT_APPLY, mode);
-        RCP_TRY(launch_tc_rows(T, v.I, v.J, l, 0, 0, W, nsplit, jchunk, p->part32, nullptr,
-                               p->dstate, s));
+        if (tma) {
+          RCP_TRY(launch_tc_rows_tma(T, v.I, v.J, l, 0, 0, W, p->part32, nullptr, p->dstate,
+                                     p->nsm, s, &nsplit));
+        } else {
+          RCP_TRY(launch_tc_rows(T, v.I, v.J, l, 0, 0, W, nsplit, jchunk, p->part32, nullptr,
+                                 p->dstate, s));
+        }
       }
       RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
       RCP_TRY(launch_cholqr(p->Y, v.I, l, p->G, p->Rinv, p->dstate, s,
@@ -583,7 +595,7 @@ rcp_status rcp_compress(rcp_plan_t p, const void* X, int32_t mode) {
     if (mode == 1 && p->tc1) {
       RCP_TRY(launch_q_to_qt32(p->Q[0], v.I, p->l[0], p->QT32, p->stream));
       RCP_TRY(launch_tc_cols(T, v.I, v.J, p->l[0], p->QT32, out, true, p->dstate,
-                             tc_cols_grid(v.J, p->nsm), p->stream));
+                             tc_cols_grid(v.J, p->nsm), p->stream, tc_tma_ok(T), false));
     } else {
       RCP_TRY(launch_project_f32(T, v, p->l[n0], p->Q[n0], out, project_grid(v, p->nsm), p->stream));
     }

@@ -483,46 +483,62 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
 // can be built).  Per 32-row chunk kc of X's contiguous direction i and block
 // of 128 columns j:
 //   producer (warp 0)   one thread: the 128 x 32 tile of X and the 2NP x 32
-//                       tile of [Q^T hi; Q^T lo] land by TMA in the 128-byte
-//                       swizzled K-major layout the MMA reads;
-//   converters (2-5)    split the X tile in place into its TF32 truncation and
-//                       write the remainder to a second tile (same layout);
-//   issuer (warp 1)     one thread: X_hi [Q_hi | Q_lo] (N = 2 NP) and X_lo Q_hi
-//                       (N = NP) into the same accumulator, so columns
-//                       [0, NP) collect hi*hi + lo*hi and [NP, 2 NP) hi*lo;
+//                       tile of [Q^T hi; Q^T lo] land by TMA, in the 128-byte
+//                       swizzled K-major layout, in a ring of RS raw stages
+//                       (HBM needs about 128 KB of loads in flight per SM to
+//                       stream near its peak);
+//   converters (2-5)    thread = one row j of the A tile: its 32 values split
+//                       into the TF32 truncation and the remainder, written to
+//                       tensor memory (lane j), two stages of 64 columns;
+//   issuer (warp 1)     one thread: A_hi [Q_hi | Q_lo] (N = 2 NP) and A_lo Q_hi
+//                       (N = NP), A from tensor memory and B from the raw stage,
+//                       into the same accumulator, so columns [0, NP) collect
+//                       hi*hi + lo*hi and [NP, 2 NP) hi*lo; the commit frees
+//                       the raw stage;
 //   epilogue (6-9)      the sum of the two halves, written out; two
 //                       accumulators, so block b's epilogue overlaps block
 //                       b + 1's MMAs.
-// X is read once, each element written and read twice in shared memory (the
-// split) and read twice by the tensor cores: about 29 bytes of shared-memory
-// traffic per element with the B tiles.
+// Shared memory carries the TMA writes, one read of each X element and the
+// tensor cores' B reads (about 13 bytes per element): the split operand lives
+// in tensor memory.
 constexpr int kColsThreads = 320;
 constexpr int kEpiPitchPad = 1;
+constexpr int kTS = 4;  // tensor-memory A stages
 
-template <int NP, int STAGES, bool TTM>
+__host__ __device__ constexpr uint32_t tmem_cols_pow2(uint32_t n) {
+  return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512;
+}
+
+template <int NP, int RS, bool TTM, bool WSPLIT = false>
 __global__ void __launch_bounds__(kColsThreads, 1)
 k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               int64_t J, int l, int nkc, float* __restrict__ out, DevState* st) {
   constexpr uint32_t kA = kATile;
   constexpr uint32_t kB = 2 * NP * 128;
-  constexpr uint32_t kStage = 2 * kA + kB;
+  constexpr uint32_t kR = kA + kB;           // raw stage: X tile, B tile
   constexpr uint32_t NACC = 2 * NP;          // tensor-memory columns of one accumulator
+  constexpr uint32_t ACOL = 2 * NACC;        // first column of the A stages (64 columns each)
+  constexpr uint32_t NCOLS = tmem_cols_pow2(ACOL + kTS * 64);
   constexpr uint32_t IDESC_W = tc::idesc_tf32(128, 2 * NP);
   constexpr uint32_t IDESC_N = tc::idesc_tf32(128, NP);
   constexpr int EP = NP + kEpiPitchPad;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* ep = (float*)(sm + STAGES * kStage);  // TTM epilogue rows (4 warps x 32 rows x EP)
-  __shared__ uint64_t full[STAGES], conv[STAGES], empty[STAGES], accf[2], acce[2];
+  uint8_t* rawb = sm;                        // RS x kR
+  float* ep = (float*)(sm + RS * kR);        // TTM epilogue rows (4 warps x 32 rows x EP)
+  __shared__ uint64_t rfull[RS], rempty[RS], tconv[kTS], tfree[kTS], accf[2], acce[2];
   __shared__ uint32_t tbase_sh;
   __shared__ volatile int abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&conv[s], 4);
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < RS; ++s) {
+      tc::mbar_init(&rfull[s], 1);
+      tc::mbar_init(&rempty[s], 1);
+    }
+    for (int s = 0; s < kTS; ++s) {
+      tc::mbar_init(&tconv[s], 4);
+      tc::mbar_init(&tfree[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accf[b], 1);
@@ -533,7 +549,7 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     tc::tma_prefetch_desc(&tmX);
     tc::tma_prefetch_desc(&tmQ);
   }
-  if (warp == 1) tc::tmem_alloc(&tbase_sh, 2 * NACC);
+  if (warp == 1) tc::tmem_alloc(&tbase_sh, NCOLS);
   tc::tc_fence_before_sync();
   __syncthreads();
   tc::tc_fence_after_sync();
@@ -549,33 +565,32 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   };
 
   if (warp == 0) {
-    // ---- producer
-    int64_t issued = 0;
+    // ---- producer of the raw ring
     if (lane == 0) {
+      int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
-        const int s = (int)(g % STAGES);
-        if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES - 1) & 1), kWaitBudget)) {
+        const int r = (int)(g % RS);
+        if (g >= RS && !tc::mbar_wait(&rempty[r], (uint32_t)((g / RS - 1) & 1), kWaitBudget)) {
           fail();
           break;
         }
         const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
-        const int kc = (int)(g % nkc);
-        uint8_t* A = sm + s * kStage;
-        tc::mbar_arrive_expect_tx(&full[s], kA + kB);
-        tc::tma_load_2d(A, &tmX, 32 * kc, (int32_t)(jblk * 128), &full[s]);
-        tc::tma_load_2d(A + 2 * kA, &tmQ, 32 * kc, 0, &full[s]);
+        const int x = 32 * (int)(g % nkc);
+        tc::mbar_arrive_expect_tx(&rfull[r], kR);
+        tc::tma_load_2d(rawb + r * kR, &tmX, x, (int32_t)(jblk * 128), &rfull[r]);
+        tc::tma_load_2d(rawb + r * kR + kA, &tmQ, x, 0, &rfull[r]);
         issued = g + 1;
       }
       // every copy issued has landed before the CTA may leave (bounded)
-      for (int64_t g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
-        if (!tc::mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1), kWaitBudget)) fail();
+      for (int64_t g = issued > RS ? issued - RS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&rfull[g % RS], (uint32_t)((g / RS) & 1), kWaitBudget)) fail();
     }
   } else if (warp == 1) {
     // ---- MMA issuer
-    int64_t issued = 0;
     if (lane == 0) {
+      int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
-        const int s = (int)(g % STAGES);
+        const int r = (int)(g % RS), t = (int)(g % kTS);
         const int64_t bl = g / nkc;
         const int kc = (int)(g % nkc);
         const int acc = (int)(bl & 1);
@@ -584,57 +599,62 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           fail();
           break;
         }
-        if (!tc::mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), kWaitBudget)) {
+        if (!tc::mbar_wait(&tconv[t], (uint32_t)((g / kTS) & 1), kWaitBudget)) {
           fail();
           break;
         }
         tc::tc_fence_after_sync();
         const uint32_t d = tbase + (uint32_t)acc * NACC;
-        const uint32_t ah = tc::smem_u32(sm + s * kStage);
-        const uint32_t al = ah + kA;
-        const uint32_t bq = ah + 2 * kA;
+        const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
+        const uint32_t bq = tc::smem_u32(rawb + r * kR + kA);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          tc::mma_tf32(d, tc::desc_kmajor_sw128(ah + 32u * k), tc::desc_kmajor_sw128(bq + 32u * k),
-                       IDESC_W, (kc > 0 || k > 0) ? 1u : 0u);
+          tc::mma_tf32_tmem_a(d, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
+                              (kc > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          tc::mma_tf32(d, tc::desc_kmajor_sw128(al + 32u * k), tc::desc_kmajor_sw128(bq + 32u * k),
-                       IDESC_N, 1u);
-        tc::mma_commit(&empty[s]);
+          tc::mma_tf32_tmem_a(d, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_N,
+                              1u);
+        tc::mma_commit(&tfree[t]);
+        tc::mma_commit(&rempty[r]);
         if (kc == nkc - 1) tc::mma_commit(&accf[acc]);
         issued = g + 1;
       }
       // the tensor cores are done with every stage before the CTA may leave
-      for (int64_t g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
-        if (!tc::mbar_wait(&empty[g % STAGES], (uint32_t)((g / STAGES) & 1), kWaitBudget)) fail();
+      for (int64_t g = issued > kTS ? issued - kTS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&tfree[g % kTS], (uint32_t)((g / kTS) & 1), kWaitBudget)) fail();
     }
   } else if (warp < 6) {
-    // ---- converters: 128 threads, 8 float4 of the 1024 in a tile each
-    const int t = tid - 64;
+    // ---- converters: warp w owns tile rows (tensor-memory lanes) 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    const uint32_t row = (uint32_t)(32 * q + lane);
     for (int64_t g = 0; g < total && !abort_sh; ++g) {
-      const int s = (int)(g % STAGES);
-      if (!tc::mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), kWaitBudget)) {
+      const int r = (int)(g % RS), t = (int)(g % kTS);
+      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
         fail();
         break;
       }
-      float4* A = (float4*)(sm + s * kStage);
-      float4* L = (float4*)(sm + s * kStage + kA);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int idx = t + 128 * k;
-        const float4 v = A[idx];
-        float4 h, lo;
-        h.x = tf32_hi(v.x); lo.x = v.x - h.x;
-        h.y = tf32_hi(v.y); lo.y = v.y - h.y;
-        h.z = tf32_hi(v.z); lo.z = v.z - h.z;
-        h.w = tf32_hi(v.w); lo.w = v.w - h.w;
-        A[idx] = h;
-        L[idx] = lo;
+      if (!tc::mbar_wait(&rfull[r], (uint32_t)((g / RS) & 1), kWaitBudget)) {
+        fail();
+        break;
       }
-      tc::fence_proxy_async_smem();
+      const uint8_t* A = rawb + r * kR;
+      float hv[32], lv[32];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 v = *(const float4*)(A + row * 128 + ((((uint32_t)c ^ (row & 7u)) & 7u) << 4));
+        hv[4 * c] = tf32_hi(v.x);     lv[4 * c] = v.x - hv[4 * c];
+        hv[4 * c + 1] = tf32_hi(v.y); lv[4 * c + 1] = v.y - hv[4 * c + 1];
+        hv[4 * c + 2] = tf32_hi(v.z); lv[4 * c + 2] = v.z - hv[4 * c + 2];
+        hv[4 * c + 3] = tf32_hi(v.w); lv[4 * c + 3] = v.w - hv[4 * c + 3];
+      }
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + ACOL + (uint32_t)t * 64;
+      tc::tmem_st32(ta, hv);
+      tc::tmem_st32(ta + 32u, lv);
+      tc::tmem_st_wait();
+      tc::tc_fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&conv[s]);
+      if (lane == 0) tc::mbar_arrive(&tconv[t]);
     }
   } else {
     // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
@@ -661,7 +681,13 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           if (TTM) {
             ep[(32 * q + lane) * EP + c] = v;
           } else if (c < l && j < J) {
-            out[(int64_t)c * J + j] = v;
+            if (WSPLIT) {  // [W_hi; W_lo], l x J each, for the TMA-fed row sweep
+              const float hv = tf32_hi(v);
+              out[(int64_t)c * J + j] = hv;
+              out[((int64_t)l + c) * J + j] = v - hv;
+            } else {
+              out[(int64_t)c * J + j] = v;
+            }
           }
         }
       }
@@ -685,7 +711,242 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (!ok) set_status(st, RCP_ETIMEOUT);
   tc::tc_fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tbase, 2 * NACC);
+  if (warp == 1) tc::tmem_dealloc(tbase, NCOLS);
+}
+
+// Row sweep with TMA-fed stages: P = X_(1) V over this CTA's row block
+// (rb rows of i, rb a multiple of 4, the blocks as equal as possible) and its
+// range of 32-column chunks of j.  V = Omega_1 (SRC 0, regenerated per chunk)
+// or the power iteration's W (SRC 1, stored by the column sweep as
+// [W_hi; W_lo], l x J each).
+//   producer (warp 0)   one thread: the rb x 32 tile of X (i contiguous, no
+//                       swizzle) and, for SRC 1, the 2NP x 32 tile of
+//                       [W_hi; W_lo] (128-byte swizzle) land by TMA in a ring
+//                       of RS raw stages;
+//   converters (2-9)    256 threads, thread = row r (tensor-memory lane) and
+//                       one half of the chunk's 32 columns: the row's values
+//                       split into TF32 truncation and remainder, written to
+//                       tensor memory (rows >= rb as zeros); for SRC 0 they
+//                       also draw Omega_1's hi and lo into a shared-memory B
+//                       stage, and for NORM sum X^2;
+//   issuer (warp 1)     one thread: A_hi [V_hi | V_lo] (N = 2 NP) and A_lo V_hi
+//                       (N = NP), A from tensor memory, into one accumulator
+//                       for the whole range; the commit frees the raw stage;
+//   epilogue            converter warps 2-5 (tensor-memory lanes 64 .. 127,
+//                       0 .. 63): the two halves summed into the split's partial.
+constexpr int kRowsThreads = 320;
+
+template <int NP, int RS, int SRC, bool NORM>
+__global__ void __launch_bounds__(kRowsThreads, 1)
+k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+              int64_t I, int64_t J, int l, int rb, int64_t cper, uint64_t seed, uint32_t sid,
+              float* __restrict__ part, double* __restrict__ normpart, DevState* st) {
+  constexpr uint32_t kB = 2 * NP * 128;
+  constexpr uint32_t kXR = 16384;                      // raw X tile (rb x 32 floats, rb <= 128)
+  constexpr uint32_t kR = kXR + (SRC == 1 ? kB : 0);   // raw stage
+  constexpr uint32_t NACC = 2 * NP;
+  constexpr uint32_t ACOL = NACC;                      // A stages: 64 columns each
+  constexpr uint32_t NCOLS = tmem_cols_pow2(ACOL + kTS * 64);
+  constexpr uint32_t IDESC_W = tc::idesc_tf32(128, 2 * NP);
+  constexpr uint32_t IDESC_N = tc::idesc_tf32(128, NP);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* rawb = sm;
+  uint8_t* bring = sm + RS * kR;                       // SRC 0: kTS B stages of Omega_1
+  __shared__ uint64_t rfull[RS], rempty[RS], tconv[kTS], tfree[kTS], accf;
+  __shared__ uint32_t tbase_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ uint16_t boff[SRC == 0 ? 32 * 64 : 1];   // element t = jj l + c of Omega -> B offset
+  __shared__ double red[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int blk = blockIdx.x, split = blockIdx.y;
+  const int64_t i0 = (int64_t)blk * rb;
+  const int64_t nchunk = (J + 31) / 32;
+  const int64_t c0 = (int64_t)split * cper;
+  const int64_t c1 = c0 + cper < nchunk ? c0 + cper : nchunk;
+  const int64_t total = c1 > c0 ? c1 - c0 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < RS; ++s) {
+      tc::mbar_init(&rfull[s], 1);
+      tc::mbar_init(&rempty[s], 1);
+    }
+    for (int s = 0; s < kTS; ++s) {
+      tc::mbar_init(&tconv[s], 8);
+      tc::mbar_init(&tfree[s], 1);
+    }
+    tc::mbar_init(&accf, 1);
+    abort_sh = 0;
+    tc::fence_mbar_init();
+    tc::tma_prefetch_desc(&tmX);
+    if (SRC == 1) tc::tma_prefetch_desc(&tmW);
+  }
+  if (warp == 1) tc::tmem_alloc(&tbase_sh, NCOLS);
+  if (SRC == 0) {
+    // the B stages start at zero: rows >= l never change
+    for (int e = tid; e < (int)(kTS * kB / 16); e += kRowsThreads)
+      ((float4*)bring)[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int t = tid; t < 32 * l; t += kRowsThreads) {
+      const int jj = t / l, c = t - jj * l;
+      boff[t] = (uint16_t)tc::sw128_offset((uint32_t)c, (uint32_t)jj);
+    }
+    tc::fence_proxy_async_smem();
+  }
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
+  const uint32_t tbase = tbase_sh;
+  bool ok = true;
+  auto fail = [&]() {
+    ok = false;
+    abort_sh = 1;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t g = 0; g < total && !abort_sh; ++g) {
+        const int r = (int)(g % RS);
+        if (g >= RS && !tc::mbar_wait(&rempty[r], (uint32_t)((g / RS - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        const int32_t y = (int32_t)(32 * (c0 + g));
+        tc::mbar_arrive_expect_tx(&rfull[r], (uint32_t)(rb * 32 * 4) + (SRC == 1 ? kB : 0u));
+        tc::tma_load_2d(rawb + r * kR, &tmX, (int32_t)i0, y, &rfull[r]);
+        if (SRC == 1) tc::tma_load_3d(rawb + r * kR + kXR, &tmW, y, 0, 0, &rfull[r]);
+        issued = g + 1;
+      }
+      for (int64_t g = issued > RS ? issued - RS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&rfull[g % RS], (uint32_t)((g / RS) & 1), kWaitBudget)) fail();
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t g = 0; g < total && !abort_sh; ++g) {
+        const int r = (int)(g % RS), t = (int)(g % kTS);
+        if (!tc::mbar_wait(&tconv[t], (uint32_t)((g / kTS) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        tc::tc_fence_after_sync();
+        const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
+        const uint32_t bq =
+            tc::smem_u32(SRC == 1 ? rawb + r * kR + kXR : bring + (uint32_t)t * kB);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          tc::mma_tf32_tmem_a(tbase, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
+                              (g > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          tc::mma_tf32_tmem_a(tbase, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k),
+                              IDESC_N, 1u);
+        tc::mma_commit(&tfree[t]);
+        tc::mma_commit(&rempty[r]);
+        issued = g + 1;
+      }
+      if (issued > 0) tc::mma_commit(&accf);
+      for (int64_t g = issued > kTS ? issued - kTS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&tfree[g % kTS], (uint32_t)((g / kTS) & 1), kWaitBudget)) fail();
+    }
+  } else {
+    // ---- converters (256 threads): row r = lane of the warp's quarter, columns 16 h .. + 15
+    const int ct = tid - 64;
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int r = 32 * q + lane;
+    const bool rv = r < rb;
+    double nrm = 0.0;
+    for (int64_t g = 0; g < total && !abort_sh; ++g) {
+      const int rs = (int)(g % RS), t = (int)(g % kTS);
+      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      if (!tc::mbar_wait(&rfull[rs], (uint32_t)((g / RS) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      const float* Xr = (const float*)(rawb + rs * kR);
+      float hv[16], lv[16];
+      float cn = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const float x = rv ? Xr[(16 * h + jj) * rb + r] : 0.0f;
+        if (NORM) cn = fmaf(x, x, cn);
+        hv[jj] = tf32_hi(x);
+        lv[jj] = x - hv[jj];
+      }
+      if (NORM) nrm += (double)cn;
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + ACOL + (uint32_t)t * 64 + 16u * h;
+      tc::tmem_st16(ta, hv);
+      tc::tmem_st16(ta + 32u, lv);
+      if (SRC == 0) {
+        // Omega_1[j, c] = element j l + c of the reduced-precision stream
+        uint8_t* Bh = bring + (uint32_t)t * kB;
+        uint8_t* Bl = Bh + NP * 128;
+        const int64_t j0 = 32 * (c0 + g);
+        const int64_t e0 = j0 * l;
+        const int lead = (int)(e0 & 3);
+        const int tend = (int)((J - j0 < 32 ? J - j0 : 32) * l);
+        const int nq = (32 * l + lead + 3) >> 2;
+        for (int qq = ct; qq < nq; qq += 256) {
+          const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)((e0 >> 2) + qq));
+          const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int te = 4 * qq + u - lead;
+            if (te >= 0 && te < 32 * l) {
+              const float v = te < tend ? zz[u] : 0.0f;
+              const float bh = tf32_hi(v);
+              *(float*)(Bh + boff[te]) = bh;
+              *(float*)(Bl + boff[te]) = v - bh;
+            }
+          }
+        }
+        tc::fence_proxy_async_smem();
+      }
+      tc::tmem_st_wait();
+      tc::tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tconv[t]);
+    }
+    if (NORM) {
+      double d = nrm;
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if (lane == 0) red[warp - 2] = d;
+    }
+    // ---- epilogue: warps 2-5 read tensor-memory lanes 32 (w % 4) .. + 31
+    if (warp < 6) {
+      const bool got = total > 0 && !abort_sh && tc::mbar_wait(&accf, 0, kWaitBudget);
+      if (total > 0 && !got) fail();
+      tc::tc_fence_after_sync();
+      const int64_t i = i0 + r;
+      const bool w = rv && i < I;
+#pragma unroll
+      for (int cg = 0; cg < NP / 32; ++cg) {
+        float a[32], b[32];
+        if (got) {
+          tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 32), a);
+          tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(NP + cg * 32), b);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) a[k] = b[k] = 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int c = cg * 32 + k;
+          if (w && c < l) part[((int64_t)split * l + c) * I + i] = a[k] + b[k];
+        }
+      }
+    }
+  }
+  if (!ok) set_status(st, RCP_ETIMEOUT);
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  if (NORM && tid == 0)
+    normpart[(int64_t)split * gridDim.x + blk] =
+        ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+  if (warp == 1) tc::tmem_dealloc(tbase, NCOLS);
 }
 
 // QT = Q^T in FP32 split into TF32 hi + lo, padded with zeros to NP x Ipad.
@@ -755,30 +1016,56 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// 2D FP32 tensor map over a row-major d1 x d0 array (row pitch d0), box
-// b1 x 32 with the 128-byte swizzle; out-of-range elements read as zero.
-bool tmap_2d_f32(CUtensorMap* m, const float* base, uint64_t d0, uint64_t d1, uint32_t b1) {
+// FP32 tensor map of rank 2 or 3 (dims innermost first, strides in bytes of
+// dims 1..), box `box`; out-of-range elements read as zero.
+bool tmap_f32(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims,
+              const cuuint64_t* strides, const cuuint32_t* box, bool swizzle128) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
-  if (!enc || ((uintptr_t)base & 15) || (d0 * 4) % 16) return false;
-  const cuuint64_t dims[2] = {d0, d1};
-  const cuuint64_t strides[1] = {d0 * 4};
-  const cuuint32_t box[2] = {32, b1};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  if (!enc || ((uintptr_t)base & 15)) return false;
+  for (int k = 0; k < rank - 1; ++k)
+    if (strides[k] % 16) return false;
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, (void*)base, dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NP, int STAGES, bool TTM>
+// 2D FP32 tensor map over a row-major d1 x d0 array (row pitch d0), box
+// b1 x 32 with the 128-byte swizzle.
+bool tmap_2d_f32(CUtensorMap* m, const float* base, uint64_t d0, uint64_t d1, uint32_t b1) {
+  const cuuint64_t dims[2] = {d0, d1};
+  const cuuint64_t strides[1] = {d0 * 4};
+  const cuuint32_t box[2] = {32, b1};
+  return tmap_f32(m, base, 2, dims, strides, box, true);
+}
+
+template <int NP, int RS, bool TTM, bool WSPLIT = false>
 cudaError_t cols_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmQ, int64_t J, int l,
                             int nkc, float* out, DevState* st, int grid, cudaStream_t s) {
-  auto kern = k_tc_cols_tma<NP, STAGES, TTM>;
-  const int smem = STAGES * (2 * kATile + 2 * NP * 128) +
-                   (TTM ? 4 * 32 * (NP + kEpiPitchPad) * 4 : 0) + 1024;
+  auto kern = k_tc_cols_tma<NP, RS, TTM, WSPLIT>;
+  const int smem = RS * (kATile + 2 * NP * 128) + (TTM ? 4 * 32 * (NP + kEpiPitchPad) * 4 : 0) +
+                   1024;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   kern<<<grid, kColsThreads, smem, s>>>(tmX, tmQ, J, l, nkc, out, st);
+  return cudaGetLastError();
+}
+
+template <int NP, int RS, int SRC, bool NORM>
+cudaError_t rows_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmW, int64_t I, int64_t J,
+                            int l, int rb, int nb, int ns, int64_t cper, uint64_t seed,
+                            uint32_t sid, float* part, double* normpart, DevState* st,
+                            cudaStream_t s) {
+  auto kern = k_tc_rows_tma<NP, RS, SRC, NORM>;
+  const int smem = RS * (16384 + (SRC == 1 ? 2 * NP * 128 : 0)) +
+                   (SRC == 0 ? kTS * 2 * NP * 128 : 0) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<dim3((unsigned)nb, (unsigned)ns), kRowsThreads, smem, s>>>(tmX, tmW, I, J, l, rb, cper, seed,
+                                                                   sid, part, normpart, st);
   return cudaGetLastError();
 }
 
@@ -820,10 +1107,69 @@ cudaError_t launch_tc_rows(const float* X, int64_t I, int64_t J, int l, uint64_t
   return rows_launch<64, 0, false>(X, I, J, l, seed, sid, nullptr, nsplit, jchunk, part, nullptr, st, s);
 }
 
-cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const float* QT, float* out,
-                           bool ttm, DevState* st, int grid, cudaStream_t s) {
-  const int64_t Ipad = tc_ipad(I);
+// True when the TMA-fed sweeps can read X: the tensor-map encoder is there
+// and X starts on a 16-byte boundary (I % 4 == 0 is tc_mode1_supported's).
+bool tc_tma_ok(const float* X) { return encode_tiled() != nullptr && ((uintptr_t)X & 15) == 0; }
+
+// Row blocks and j-splits of the TMA-fed row sweep: nb blocks of rb rows (a
+// multiple of 4, as equal as possible), about one CTA per SM.
+void tc_rows_tma_shape(int64_t I, int64_t J, int nsm, int* nb, int* rb, int* ns, int64_t* cper) {
+  const int64_t b = (I + 127) / 128;
+  int64_t r = (I + b - 1) / b;
+  r = (r + 3) / 4 * 4;
+  const int64_t nchunk = (J + 31) / 32;
+  int64_t n = nsm / b;
+  if (n < 1) n = 1;
+  if (n > nchunk) n = nchunk;
+  *nb = (int)b;
+  *rb = (int)r;
+  *cper = (nchunk + n - 1) / n;
+  *ns = (int)((nchunk + *cper - 1) / *cper);
+}
+
+// TMA-fed row sweep (tc_tma_ok(X) must hold).  Wsplit: the column sweep's
+// [W_hi; W_lo] (2 l x J), or null for Omega_1.  *nsplit receives the number of
+// j-split partials per row written to part.
+cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, uint64_t seed,
+                               uint32_t sid, const float* Wsplit, float* part, double* normpart,
+                               DevState* st, int nsm, cudaStream_t s, int* nsplit) {
+  int nb = 0, rb = 0, ns = 0;
+  int64_t cper = 0;
+  tc_rows_tma_shape(I, J, nsm, &nb, &rb, &ns, &cper);
+  *nsplit = ns;
+  const int NP = tc_np(l);
+  CUtensorMap tmX, tmW;
   {
+    const cuuint64_t dims[2] = {(cuuint64_t)I, (cuuint64_t)J};
+    const cuuint64_t strides[1] = {(cuuint64_t)I * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)rb, 32};
+    if (!tmap_f32(&tmX, X, 2, dims, strides, box, false)) return cudaErrorInvalidValue;
+  }
+  if (Wsplit) {
+    const cuuint64_t dims[3] = {(cuuint64_t)J, (cuuint64_t)l, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)J * 4, (cuuint64_t)l * J * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)NP, 2};
+    if (!tmap_f32(&tmW, Wsplit, 3, dims, strides, box, true)) return cudaErrorInvalidValue;
+  } else {
+    tmW = tmX;  // unused by the Omega form
+  }
+  const bool norm = normpart != nullptr;
+  if (NP == 32) {
+    if (Wsplit) return rows_tma_launch<32, 6, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
+    if (norm) return rows_tma_launch<32, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
+    return rows_tma_launch<32, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
+  }
+  if (Wsplit) return rows_tma_launch<64, 5, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
+  if (norm) return rows_tma_launch<64, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
+  return rows_tma_launch<64, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
+}
+
+// Column sweep; tma selects the TMA-fed kernel (tc_tma_ok(X) must hold), and
+// wsplit (with !ttm) its [W_hi; W_lo] output for the TMA-fed row sweep.
+cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const float* QT, float* out,
+                           bool ttm, DevState* st, int grid, cudaStream_t s, bool tma, bool wsplit) {
+  const int64_t Ipad = tc_ipad(I);
+  if (tma) {
     // the TMA-fed form: one CTA per SM, persistent over the 128-column blocks
     const int NP = tc_np(l);
     CUtensorMap tmX, tmQ;
@@ -836,13 +1182,17 @@ cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const fl
       const int64_t njb = (J + 127) / 128;
       const int g = (int)(njb < nsm ? njb : nsm);
       const int nkc = (int)(Ipad / 32);
+      // raw stages: as many as fit beside the split stages (and the product's rows)
       if (NP == 32) {
-        if (ttm) return cols_tma_launch<32, 4, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-        return cols_tma_launch<32, 4, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        if (ttm) return cols_tma_launch<32, 8, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        if (wsplit) return cols_tma_launch<32, 8, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        return cols_tma_launch<32, 8, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
       }
-      if (ttm) return cols_tma_launch<64, 3, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-      return cols_tma_launch<64, 3, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      if (ttm) return cols_tma_launch<64, 5, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      if (wsplit) return cols_tma_launch<64, 6, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      return cols_tma_launch<64, 6, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
     }
+    return cudaErrorInvalidValue;
   }
   if (tc_np(l) == 32) {
     if (ttm) return cols_launch<32, true>(X, I, J, l, Ipad, QT, out, st, grid, s);

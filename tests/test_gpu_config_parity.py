@@ -90,12 +90,42 @@ def _run_plan(w, seed=0, tol=None, max_iters=None):
 
 @pytest.mark.slow
 def test_4way_full_size_matches_oracle_step_by_step():
-    # 128 x 128 x 128 x 64 FP32 (512 MB), R = 32, p = 16, q = 1, 50 ALS sweeps
+    # 128 x 128 x 128 x 64 FP32 (512 MB), R = 32, p = 16, q = 1.
+    # Compression is compared with the oracle's as for the other workloads.
+    # ALS is compared on the GPU's own B: on this workload 50 sweeps from the
+    # seeded start do not converge and the iteration amplifies rounding (a
+    # relative change of 5e-5 in B, or the FP32 MTTKRP against the oracle's
+    # FP64 one, moves the 50-sweep CP model by several per cent), so the
+    # factors are compared after 3 sweeps, and after 50 sweeps only the fit.
     w = synth.config("c3_128cubed_x64_f32")
     Qg, Bg, Atg, lamg, res = _run_plan(w)
     o = oracle.rcp.rcp_als(w.X, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, 0,
                            omega="f32")
-    _compare(w.rank, Qg, Bg, Atg, lamg, res["rel_err"], o)
+    R = w.rank
+    full = []
+    for n, (qg, qo) in enumerate(zip(Qg, o["Q"]), start=1):
+        s = _sines(qg, qo)
+        assert s[:R].max() < 1e-3, (n, s[:R].max())
+        full.append(s.max())
+    Bo = o["B"]
+    dB = np.linalg.norm(_to_oracle_basis(Bg, Qg, o["Q"]) - Bo)
+    assert dB <= sum(full) * np.sqrt(o["normX2"]) + 1e-5 * np.linalg.norm(Bo), (dB, full)
+    assert dB <= 1e-3 * np.linalg.norm(Bo), dB
+    B64 = np.asarray(Bg, dtype=np.float64)
+    # 3 sweeps on the same B: the factors agree
+    _q, B3, At3, lam3, res3 = _run_plan(w, max_iters=3)
+    assert np.array_equal(B3, Bg)  # the compression is deterministic
+    lam_o, At_o, rho_o, _it, _h = oracle.rcp.cp_als(B64, R, 0.0, 3, 0)
+    K3 = tensor.kruskal(lam_o, At_o)
+    dK = np.linalg.norm(tensor.kruskal(lam3, At3) - K3) / np.linalg.norm(K3)
+    assert dK < 1e-4, dK
+    assert res3["fit"] == pytest.approx(rho_o, abs=1e-6)
+    # 50 sweeps: the fit the oracle reaches on the same B, and the error identity
+    _l, _A, rho50, _i, _h = oracle.rcp.cp_als(B64, R, w.tol, w.max_iters, 0)
+    assert abs(res["fit"] - rho50) < 5e-3, (res["fit"], rho50)
+    nb2 = np.linalg.norm(B64) ** 2
+    res2 = res["norm_x2"] - nb2 + nb2 * (1.0 - res["fit"])
+    assert res["rel_err"] == pytest.approx(np.sqrt(res2 / res["norm_x2"]), rel=1e-6)
 
 
 def test_flowlike_reduced_matches_oracle_step_by_step():
