@@ -466,11 +466,14 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     tc_rows_split(v.I, v.J, p->nsm, &nsplit, &jchunk);
     const int cgrid = tc_cols_grid(v.J, p->nsm);
     {
-      // the sketch keeps the register-staged sweep: drawing Omega_1 per chunk is
-      // its cost, and two CTAs per SM spread it over twice the warps
       Span sp(p, RCP_KT_SKETCH, mode);
-      RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit,
-                             jchunk, p->part32, p->normpart, p->dstate, s));
+      if (tma) {
+        RCP_TRY(launch_tc_rows_tma(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr,
+                                   p->part32, p->normpart, p->dstate, p->nsm, s, &nsplit));
+      } else {
+        RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit,
+                               jchunk, p->part32, p->normpart, p->dstate, s));
+      }
     }
     RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
     const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA

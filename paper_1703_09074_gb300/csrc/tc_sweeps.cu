@@ -482,40 +482,38 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
 // Column sweep with TMA-fed stages (the form used whenever the tensor maps
 // can be built).  Per 32-row chunk kc of X's contiguous direction i and block
 // of 128 columns j:
-//   producer (warp 0)   one thread: the 128 x 32 tile of X and the 2NP x 32
-//                       tile of [Q^T hi; Q^T lo] land by TMA, in the 128-byte
-//                       swizzled K-major layout, in a ring of RS raw stages
-//                       (HBM needs about 128 KB of loads in flight per SM to
-//                       stream near its peak);
-//   converters (2-5)    thread = one row j of the A tile: its 32 values split
-//                       into the TF32 truncation and the remainder, written to
-//                       tensor memory (lane j), two stages of 64 columns;
-//   issuer (warp 1)     one thread: A_hi [Q_hi | Q_lo] (N = 2 NP) and A_lo Q_hi
-//                       (N = NP), A from tensor memory and B from the raw stage,
-//                       into the same accumulator, so columns [0, NP) collect
-//                       hi*hi + lo*hi and [NP, 2 NP) hi*lo; the commit frees
-//                       the raw stage;
-//   epilogue (6-9)      the sum of the two halves, written out; two
-//                       accumulators, so block b's epilogue overlaps block
-//                       b + 1's MMAs.
-// Shared memory carries the TMA writes, one read of each X element and the
-// tensor cores' B reads (about 13 bytes per element): the split operand lives
-// in tensor memory.
-constexpr int kColsThreads = 320;
+//   X producer (warp 0)  one thread: the 128 x 32 tile of X lands by TMA, in
+//                        the 128-byte swizzled K-major layout, in a ring of RS
+//                        stages that the converters free as soon as they have
+//                        read it: HBM needs about 128 KB of loads in flight per
+//                        SM, and a stage held through the MMAs' completion
+//                        would leave too few in flight;
+//   B producer (warp 10) one thread: the 2NP x 32 tile of [Q^T hi; Q^T lo] (from
+//                        L2) into a ring of kTS stages freed by the MMAs;
+//   converters (2-5)     thread = one row j of the A tile: its 32 values split
+//                        into the TF32 truncation and the remainder, written to
+//                        tensor memory (lane j), kTS stages of 64 columns;
+//   issuer (warp 1)      one thread: A_hi [Q_hi | Q_lo] (N = 2 NP) and A_lo Q_hi
+//                        (N = NP), A from tensor memory, into one accumulator,
+//                        so columns [0, NP) collect hi*hi + lo*hi and
+//                        [NP, 2 NP) hi*lo;
+//   epilogue (6-9)       the sum of the two halves, written out; two
+//                        accumulators, so block b's epilogue overlaps block
+//                        b + 1's MMAs.
+constexpr int kColsThreads = 352;
 constexpr int kEpiPitchPad = 1;
-constexpr int kTS = 4;  // tensor-memory A stages
+constexpr int kTS = 4;  // tensor-memory A stages and B stages
 
 __host__ __device__ constexpr uint32_t tmem_cols_pow2(uint32_t n) {
   return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512;
 }
 
-template <int NP, int RS, bool TTM, bool WSPLIT = false>
+template <int NP, int RS, int BS, bool TTM, bool WSPLIT = false>
 __global__ void __launch_bounds__(kColsThreads, 1)
 k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
               int64_t J, int l, int nkc, float* __restrict__ out, DevState* st) {
   constexpr uint32_t kA = kATile;
   constexpr uint32_t kB = 2 * NP * 128;
-  constexpr uint32_t kR = kA + kB;           // raw stage: X tile, B tile
   constexpr uint32_t NACC = 2 * NP;          // tensor-memory columns of one accumulator
   constexpr uint32_t ACOL = 2 * NACC;        // first column of the A stages (64 columns each)
   constexpr uint32_t NCOLS = tmem_cols_pow2(ACOL + kTS * 64);
@@ -524,9 +522,11 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   constexpr int EP = NP + kEpiPitchPad;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* rawb = sm;                        // RS x kR
-  float* ep = (float*)(sm + RS * kR);        // TTM epilogue rows (4 warps x 32 rows x EP)
-  __shared__ uint64_t rfull[RS], rempty[RS], tconv[kTS], tfree[kTS], accf[2], acce[2];
+  uint8_t* rawb = sm;                        // RS x 16 KB of X
+  uint8_t* bring = sm + RS * kA;             // BS x kB of [Q_hi; Q_lo]
+  float* ep = (float*)(bring + BS * kB);     // TTM epilogue rows (4 warps x 32 rows x EP)
+  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kTS], tfree[kTS], accf[2],
+      acce[2];
   __shared__ uint32_t tbase_sh;
   __shared__ volatile int abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -534,7 +534,11 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (tid == 0) {
     for (int s = 0; s < RS; ++s) {
       tc::mbar_init(&rfull[s], 1);
-      tc::mbar_init(&rempty[s], 1);
+      tc::mbar_init(&rempty[s], 4);
+    }
+    for (int s = 0; s < BS; ++s) {
+      tc::mbar_init(&bfull[s], 1);
+      tc::mbar_init(&bfree[s], 1);
     }
     for (int s = 0; s < kTS; ++s) {
       tc::mbar_init(&tconv[s], 4);
@@ -565,7 +569,7 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   };
 
   if (warp == 0) {
-    // ---- producer of the raw ring
+    // ---- producer of the X ring
     if (lane == 0) {
       int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
@@ -575,38 +579,55 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           break;
         }
         const int64_t jblk = blockIdx.x + (g / nkc) * gridDim.x;
-        const int x = 32 * (int)(g % nkc);
-        tc::mbar_arrive_expect_tx(&rfull[r], kR);
-        tc::tma_load_2d(rawb + r * kR, &tmX, x, (int32_t)(jblk * 128), &rfull[r]);
-        tc::tma_load_2d(rawb + r * kR + kA, &tmQ, x, 0, &rfull[r]);
+        tc::mbar_arrive_expect_tx(&rfull[r], kA);
+        tc::tma_load_2d(rawb + r * kA, &tmX, 32 * (int)(g % nkc), (int32_t)(jblk * 128), &rfull[r]);
         issued = g + 1;
       }
       // every copy issued has landed before the CTA may leave (bounded)
       for (int64_t g = issued > RS ? issued - RS : 0; g < issued; ++g)
         if (!tc::mbar_wait(&rfull[g % RS], (uint32_t)((g / RS) & 1), kWaitBudget)) fail();
     }
-  } else if (warp == 1) {
-    // ---- MMA issuer
+  } else if (warp == 10) {
+    // ---- producer of the B ring
     if (lane == 0) {
       int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
-        const int r = (int)(g % RS), t = (int)(g % kTS);
-        const int64_t bl = g / nkc;
-        const int kc = (int)(g % nkc);
-        const int acc = (int)(bl & 1);
+        const int b = (int)(g % BS);
+        if (g >= BS && !tc::mbar_wait(&bfree[b], (uint32_t)((g / BS - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&bfull[b], kB);
+        tc::tma_load_2d(bring + b * kB, &tmQ, 32 * (int)(g % nkc), 0, &bfull[b]);
+        issued = g + 1;
+      }
+      for (int64_t g = issued > BS ? issued - BS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer.  This thread's shared-memory accesses (barrier polls, flags)
+    // wait behind its MMAs in flight, so the loop makes one poll per chunk and
+    // keeps its indices in registers (no divisions).
+    if (lane == 0) {
+      int64_t issued = 0;
+      int kc = 0, t = 0, b = 0, acc = 0;
+      int64_t bl = 0;
+      uint32_t tph = 0;
+      for (int64_t g = 0; g < total; ++g) {
         if (kc == 0 && bl >= 2 &&
             !tc::mbar_wait(&acce[acc], (uint32_t)((bl / 2 - 1) & 1), kWaitBudget)) {
           fail();
           break;
         }
-        if (!tc::mbar_wait(&tconv[t], (uint32_t)((g / kTS) & 1), kWaitBudget)) {
+        // one wait per chunk: the converters also vouch for the B tile
+        if (!tc::mbar_wait(&tconv[t], tph, kWaitBudget)) {
           fail();
           break;
         }
         tc::tc_fence_after_sync();
         const uint32_t d = tbase + (uint32_t)acc * NACC;
         const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
-        const uint32_t bq = tc::smem_u32(rawb + r * kR + kA);
+        const uint32_t bq = tc::smem_u32(bring + b * kB);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           tc::mma_tf32_tmem_a(d, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
@@ -616,13 +637,23 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tc::mma_tf32_tmem_a(d, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_N,
                               1u);
         tc::mma_commit(&tfree[t]);
-        tc::mma_commit(&rempty[r]);
+        tc::mma_commit(&bfree[b]);
         if (kc == nkc - 1) tc::mma_commit(&accf[acc]);
         issued = g + 1;
+        if (++t == kTS) {
+          t = 0;
+          tph ^= 1u;
+        }
+        if (++b == BS) b = 0;
+        if (++kc == nkc) {
+          kc = 0;
+          ++bl;
+          acc ^= 1;
+        }
       }
       // the tensor cores are done with every stage before the CTA may leave
-      for (int64_t g = issued > kTS ? issued - kTS : 0; g < issued; ++g)
-        if (!tc::mbar_wait(&tfree[g % kTS], (uint32_t)((g / kTS) & 1), kWaitBudget)) fail();
+      for (int64_t g = issued > BS ? issued - BS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&bfree[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
     }
   } else if (warp < 6) {
     // ---- converters: warp w owns tile rows (tensor-memory lanes) 32 (w % 4) .. + 31
@@ -630,15 +661,11 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const uint32_t row = (uint32_t)(32 * q + lane);
     for (int64_t g = 0; g < total && !abort_sh; ++g) {
       const int r = (int)(g % RS), t = (int)(g % kTS);
-      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
-        fail();
-        break;
-      }
       if (!tc::mbar_wait(&rfull[r], (uint32_t)((g / RS) & 1), kWaitBudget)) {
         fail();
         break;
       }
-      const uint8_t* A = rawb + r * kR;
+      const uint8_t* A = rawb + r * kA;
       float hv[32], lv[32];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -648,13 +675,24 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         hv[4 * c + 2] = tf32_hi(v.z); lv[4 * c + 2] = v.z - hv[4 * c + 2];
         hv[4 * c + 3] = tf32_hi(v.w); lv[4 * c + 3] = v.w - hv[4 * c + 3];
       }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&rempty[r]);  // the raw tile is in registers now
+      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      tc::tc_fence_after_sync();
       const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + ACOL + (uint32_t)t * 64;
       tc::tmem_st32(ta, hv);
       tc::tmem_st32(ta + 32u, lv);
       tc::tmem_st_wait();
       tc::tc_fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tconv[t]);
+      if (lane == 0) {
+        // the B tile of this chunk has landed too (the issuer waits on tconv only)
+        if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
+        tc::mbar_arrive(&tconv[t]);
+      }
     }
   } else {
     // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
@@ -719,10 +757,12 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 // range of 32-column chunks of j.  V = Omega_1 (SRC 0, regenerated per chunk)
 // or the power iteration's W (SRC 1, stored by the column sweep as
 // [W_hi; W_lo], l x J each).
-//   producer (warp 0)   one thread: the rb x 32 tile of X (i contiguous, no
-//                       swizzle) and, for SRC 1, the 2NP x 32 tile of
-//                       [W_hi; W_lo] (128-byte swizzle) land by TMA in a ring
-//                       of RS raw stages;
+//   X producer (warp 0) one thread: the rb x 32 tile of X (i contiguous, no
+//                       swizzle) lands by TMA in a ring of RS stages that the
+//                       converters free once they have read it;
+//   B producer (10)     SRC 1: one thread, the 2NP x 32 tile of [W_hi; W_lo]
+//                       (128-byte swizzle) into a ring of kTS stages freed by
+//                       the MMAs;
 //   converters (2-9)    256 threads, thread = row r (tensor-memory lane) and
 //                       one half of the chunk's 32 columns: the row's values
 //                       split into TF32 truncation and remainder, written to
@@ -731,19 +771,18 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 //                       stage, and for NORM sum X^2;
 //   issuer (warp 1)     one thread: A_hi [V_hi | V_lo] (N = 2 NP) and A_lo V_hi
 //                       (N = NP), A from tensor memory, into one accumulator
-//                       for the whole range; the commit frees the raw stage;
+//                       for the whole range;
 //   epilogue            converter warps 2-5 (tensor-memory lanes 64 .. 127,
 //                       0 .. 63): the two halves summed into the split's partial.
-constexpr int kRowsThreads = 320;
+constexpr int kRowsThreads = 352;
 
-template <int NP, int RS, int SRC, bool NORM>
+template <int NP, int RS, int BS, int SRC, bool NORM>
 __global__ void __launch_bounds__(kRowsThreads, 1)
 k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               int64_t I, int64_t J, int l, int rb, int64_t cper, uint64_t seed, uint32_t sid,
               float* __restrict__ part, double* __restrict__ normpart, DevState* st) {
   constexpr uint32_t kB = 2 * NP * 128;
-  constexpr uint32_t kXR = 16384;                      // raw X tile (rb x 32 floats, rb <= 128)
-  constexpr uint32_t kR = kXR + (SRC == 1 ? kB : 0);   // raw stage
+  constexpr uint32_t kXR = 16384;                      // X stage (rb x 32 floats, rb <= 128)
   constexpr uint32_t NACC = 2 * NP;
   constexpr uint32_t ACOL = NACC;                      // A stages: 64 columns each
   constexpr uint32_t NCOLS = tmem_cols_pow2(ACOL + kTS * 64);
@@ -752,8 +791,8 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* rawb = sm;
-  uint8_t* bring = sm + RS * kR;                       // SRC 0: kTS B stages of Omega_1
-  __shared__ uint64_t rfull[RS], rempty[RS], tconv[kTS], tfree[kTS], accf;
+  uint8_t* bring = sm + RS * kXR;                      // BS B stages (Omega_1 or [W_hi; W_lo])
+  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kTS], tfree[kTS], accf;
   __shared__ uint32_t tbase_sh;
   __shared__ volatile int abort_sh;
   __shared__ uint16_t boff[SRC == 0 ? 32 * 64 : 1];   // element t = jj l + c of Omega -> B offset
@@ -769,7 +808,11 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (tid == 0) {
     for (int s = 0; s < RS; ++s) {
       tc::mbar_init(&rfull[s], 1);
-      tc::mbar_init(&rempty[s], 1);
+      tc::mbar_init(&rempty[s], 8);
+    }
+    for (int s = 0; s < BS; ++s) {
+      tc::mbar_init(&bfull[s], 1);
+      tc::mbar_init(&bfree[s], 1);
     }
     for (int s = 0; s < kTS; ++s) {
       tc::mbar_init(&tconv[s], 8);
@@ -784,7 +827,7 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp == 1) tc::tmem_alloc(&tbase_sh, NCOLS);
   if (SRC == 0) {
     // the B stages start at zero: rows >= l never change
-    for (int e = tid; e < (int)(kTS * kB / 16); e += kRowsThreads)
+    for (int e = tid; e < (int)(BS * kB / 16); e += kRowsThreads)
       ((float4*)bring)[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int t = tid; t < 32 * l; t += kRowsThreads) {
       const int jj = t / l, c = t - jj * l;
@@ -811,28 +854,43 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           fail();
           break;
         }
-        const int32_t y = (int32_t)(32 * (c0 + g));
-        tc::mbar_arrive_expect_tx(&rfull[r], (uint32_t)(rb * 32 * 4) + (SRC == 1 ? kB : 0u));
-        tc::tma_load_2d(rawb + r * kR, &tmX, (int32_t)i0, y, &rfull[r]);
-        if (SRC == 1) tc::tma_load_3d(rawb + r * kR + kXR, &tmW, y, 0, 0, &rfull[r]);
+        tc::mbar_arrive_expect_tx(&rfull[r], (uint32_t)(rb * 32 * 4));
+        tc::tma_load_2d(rawb + r * kXR, &tmX, (int32_t)i0, (int32_t)(32 * (c0 + g)), &rfull[r]);
         issued = g + 1;
       }
       for (int64_t g = issued > RS ? issued - RS : 0; g < issued; ++g)
         if (!tc::mbar_wait(&rfull[g % RS], (uint32_t)((g / RS) & 1), kWaitBudget)) fail();
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
+  } else if (warp == 10) {
+    if (SRC == 1 && lane == 0) {
       int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
-        const int r = (int)(g % RS), t = (int)(g % kTS);
-        if (!tc::mbar_wait(&tconv[t], (uint32_t)((g / kTS) & 1), kWaitBudget)) {
+        const int b = (int)(g % BS);
+        if (g >= BS && !tc::mbar_wait(&bfree[b], (uint32_t)((g / BS - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&bfull[b], kB);
+        tc::tma_load_3d(bring + b * kB, &tmW, (int32_t)(32 * (c0 + g)), 0, 0, &bfull[b]);
+        issued = g + 1;
+      }
+      for (int64_t g = issued > BS ? issued - BS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
+    }
+  } else if (warp == 1) {
+    // MMA issuer: one poll per chunk, indices in registers (see the column sweep)
+    if (lane == 0) {
+      int64_t issued = 0;
+      int t = 0, b = 0;
+      uint32_t tph = 0;
+      for (int64_t g = 0; g < total; ++g) {
+        if (!tc::mbar_wait(&tconv[t], tph, kWaitBudget)) {
           fail();
           break;
         }
         tc::tc_fence_after_sync();
         const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
-        const uint32_t bq =
-            tc::smem_u32(SRC == 1 ? rawb + r * kR + kXR : bring + (uint32_t)t * kB);
+        const uint32_t bq = tc::smem_u32(bring + (uint32_t)b * kB);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           tc::mma_tf32_tmem_a(tbase, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
@@ -842,12 +900,17 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tc::mma_tf32_tmem_a(tbase, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k),
                               IDESC_N, 1u);
         tc::mma_commit(&tfree[t]);
-        tc::mma_commit(&rempty[r]);
+        tc::mma_commit(&bfree[b]);
         issued = g + 1;
+        if (++t == kTS) {
+          t = 0;
+          tph ^= 1u;
+        }
+        if (++b == BS) b = 0;
       }
       if (issued > 0) tc::mma_commit(&accf);
-      for (int64_t g = issued > kTS ? issued - kTS : 0; g < issued; ++g)
-        if (!tc::mbar_wait(&tfree[g % kTS], (uint32_t)((g / kTS) & 1), kWaitBudget)) fail();
+      for (int64_t g = issued > BS ? issued - BS : 0; g < issued; ++g)
+        if (!tc::mbar_wait(&bfree[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
     }
   } else {
     // ---- converters (256 threads): row r = lane of the warp's quarter, columns 16 h .. + 15
@@ -858,15 +921,11 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     double nrm = 0.0;
     for (int64_t g = 0; g < total && !abort_sh; ++g) {
       const int rs = (int)(g % RS), t = (int)(g % kTS);
-      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
-        fail();
-        break;
-      }
       if (!tc::mbar_wait(&rfull[rs], (uint32_t)((g / RS) & 1), kWaitBudget)) {
         fail();
         break;
       }
-      const float* Xr = (const float*)(rawb + rs * kR);
+      const float* Xr = (const float*)(rawb + rs * kXR);
       float hv[16], lv[16];
       float cn = 0.0f;
 #pragma unroll
@@ -877,12 +936,24 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         lv[jj] = x - hv[jj];
       }
       if (NORM) nrm += (double)cn;
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&rempty[rs]);  // the X tile is in registers now
+      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
+        fail();
+        break;
+      }
+      tc::tc_fence_after_sync();
       const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + ACOL + (uint32_t)t * 64 + 16u * h;
       tc::tmem_st16(ta, hv);
       tc::tmem_st16(ta + 32u, lv);
       if (SRC == 0) {
         // Omega_1[j, c] = element j l + c of the reduced-precision stream
-        uint8_t* Bh = bring + (uint32_t)t * kB;
+        const int b = (int)(g % BS);
+        if (g >= BS && !tc::mbar_wait(&bfree[b], (uint32_t)((g / BS - 1) & 1), kWaitBudget)) {
+          fail();
+          break;
+        }
+        uint8_t* Bh = bring + (uint32_t)b * kB;
         uint8_t* Bl = Bh + NP * 128;
         const int64_t j0 = 32 * (c0 + g);
         const int64_t e0 = j0 * l;
@@ -908,7 +979,11 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tc::tmem_st_wait();
       tc::tc_fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tconv[t]);
+      if (lane == 0) {
+        if (SRC == 1 && !tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget))
+          fail();
+        tc::mbar_arrive(&tconv[t]);
+      }
     }
     if (NORM) {
       double d = nrm;
@@ -1040,12 +1115,12 @@ bool tmap_2d_f32(CUtensorMap* m, const float* base, uint64_t d0, uint64_t d1, ui
   return tmap_f32(m, base, 2, dims, strides, box, true);
 }
 
-template <int NP, int RS, bool TTM, bool WSPLIT = false>
+template <int NP, int RS, int BS, bool TTM, bool WSPLIT = false>
 cudaError_t cols_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmQ, int64_t J, int l,
                             int nkc, float* out, DevState* st, int grid, cudaStream_t s) {
-  auto kern = k_tc_cols_tma<NP, RS, TTM, WSPLIT>;
-  const int smem = RS * (kATile + 2 * NP * 128) + (TTM ? 4 * 32 * (NP + kEpiPitchPad) * 4 : 0) +
-                   1024;
+  auto kern = k_tc_cols_tma<NP, RS, BS, TTM, WSPLIT>;
+  const int smem = RS * kATile + BS * 2 * NP * 128 +
+                   (TTM ? 4 * 32 * (NP + kEpiPitchPad) * 4 : 0) + 1024;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
@@ -1053,14 +1128,13 @@ cudaError_t cols_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmQ, int6
   return cudaGetLastError();
 }
 
-template <int NP, int RS, int SRC, bool NORM>
+template <int NP, int RS, int BS, int SRC, bool NORM>
 cudaError_t rows_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmW, int64_t I, int64_t J,
                             int l, int rb, int nb, int ns, int64_t cper, uint64_t seed,
                             uint32_t sid, float* part, double* normpart, DevState* st,
                             cudaStream_t s) {
-  auto kern = k_tc_rows_tma<NP, RS, SRC, NORM>;
-  const int smem = RS * (16384 + (SRC == 1 ? 2 * NP * 128 : 0)) +
-                   (SRC == 0 ? kTS * 2 * NP * 128 : 0) + 1024;
+  auto kern = k_tc_rows_tma<NP, RS, BS, SRC, NORM>;
+  const int smem = RS * 16384 + BS * 2 * NP * 128 + 1024;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
@@ -1155,13 +1229,13 @@ cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, uint
   }
   const bool norm = normpart != nullptr;
   if (NP == 32) {
-    if (Wsplit) return rows_tma_launch<32, 6, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
-    if (norm) return rows_tma_launch<32, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
-    return rows_tma_launch<32, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
+    if (Wsplit) return rows_tma_launch<32, 8, 8, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
+    if (norm) return rows_tma_launch<32, 8, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
+    return rows_tma_launch<32, 8, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
   }
-  if (Wsplit) return rows_tma_launch<64, 5, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
-  if (norm) return rows_tma_launch<64, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
-  return rows_tma_launch<64, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
+  if (Wsplit) return rows_tma_launch<64, 6, 6, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
+  if (norm) return rows_tma_launch<64, 6, 6, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
+  return rows_tma_launch<64, 6, 6, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
 }
 
 // Column sweep; tma selects the TMA-fed kernel (tc_tma_ok(X) must hold), and
@@ -1183,14 +1257,15 @@ cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const fl
       const int g = (int)(njb < nsm ? njb : nsm);
       const int nkc = (int)(Ipad / 32);
       // raw stages: as many as fit beside the split stages (and the product's rows)
+      // X stages and B stages: as many as fit (about 128 KB of X in flight)
       if (NP == 32) {
-        if (ttm) return cols_tma_launch<32, 8, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-        if (wsplit) return cols_tma_launch<32, 8, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-        return cols_tma_launch<32, 8, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        if (ttm) return cols_tma_launch<32, 8, 8, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        if (wsplit) return cols_tma_launch<32, 8, 8, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+        return cols_tma_launch<32, 8, 8, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
       }
-      if (ttm) return cols_tma_launch<64, 5, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-      if (wsplit) return cols_tma_launch<64, 6, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
-      return cols_tma_launch<64, 6, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      if (ttm) return cols_tma_launch<64, 6, 6, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      if (wsplit) return cols_tma_launch<64, 6, 6, false, true>(tmX, tmQ, J, l, nkc, out, st, g, s);
+      return cols_tma_launch<64, 6, 6, false>(tmX, tmQ, J, l, nkc, out, st, g, s);
     }
     return cudaErrorInvalidValue;
   }
