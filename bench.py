@@ -44,9 +44,10 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + written) per launch of the mode-1 tensor-core sweeps, from one ncu
-# capture of the current kernels (profiles/tc_sweeps_mode1_400cubed.md); None elsewhere.
-NCU_TRAFFIC = {("c2", "mixed", "apply"): 275.27e6 + 3.58e6,
-               ("c2", "mixed", "project"): 256.86e6 + 14.30e6}
+# capture of the current kernels (profiles/tc_sweeps_mode1_400cubed.md); None elsewhere
+# and for kernels changed since their capture.
+NCU_TRAFFIC = {("c2", "mixed", "apply"): 294.496e6 + 3.713e6,
+               ("c2", "mixed", "project"): 256.200e6 + 25.038e6}
 
 # GB300 FP64 arithmetic peak for ALU-bound FP64 kernels: 1.06 TFLOP/s, measured on
 # this part with an FMA-chain kernel (profiles/fp64_fp32_fma_peak_gb300.md); the
@@ -293,12 +294,21 @@ def run_ours(args):
                 "peak_source": "measured FP64 FMA rate (FMA-chain probe; not in the measured-peaks file)",
                 "algorithmic": f"{flops:.4g} FLOP per launch (2 I J l)"}
     else:
-        achieved = xbytes / per_launch_s / 1e9
+        # algorithmic bytes per launch: one read of X plus the small operand the sweep
+        # streams (the power iteration's W is stored split into TF32 hi and lo, 2 l J
+        # floats, read by the apply sweep and written by the project sweep; the mode
+        # product writes T_2, l J floats)
+        extra = {"sketch": 0, "apply": 8 * J * l1, "project": 8 * J * l1, "ttm": 4 * J * l1}[dom]
+        abytes = xbytes + extra
+        achieved = abytes / per_launch_s / 1e9
+        what = {"sketch": "one read of X", "apply": "one read of X + W_hi, W_lo read",
+                "project": "one read of X + W_hi, W_lo written",
+                "ttm": "one read of X + T_2 written"}[dom]
         roof = {"bound": "hbm", "kernel": f"mode-1 {dom} sweep", "achieved": achieved,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                 "traffic": NCU_TRAFFIC.get((args.workload, args.precision, dom)),
                 "peak_source": src,
-                "algorithmic": f"{xbytes} B per launch (one read of X)"}
+                "algorithmic": f"{abytes} B per launch ({what})"}
     sketch_gbs = xbytes / (sk_ms / sk_n / 1e3) / 1e9 if sk_n else None
     # ALS (one launch per decomposition): time per mode update and share of the step
     als_ms = stages["als"]["ms_per_step"]

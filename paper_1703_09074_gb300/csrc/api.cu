@@ -467,13 +467,8 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
     const int cgrid = tc_cols_grid(v.J, p->nsm);
     {
       Span sp(p, RCP_KT_SKETCH, mode);
-      if (tma) {
-        RCP_TRY(launch_tc_rows_tma(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr,
-                                   p->part32, p->normpart, p->dstate, p->nsm, s, &nsplit));
-      } else {
-        RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit,
-                               jchunk, p->part32, p->normpart, p->dstate, s));
-      }
+      RCP_TRY(launch_tc_rows(T, v.I, v.J, l, p->cfg.seed, (uint32_t)mode, nullptr, nsplit, jchunk,
+                             p->part32, p->normpart, p->dstate, s));
     }
     RCP_TRY(launch_reduce_f32(p->part32, nsplit, ny, p->Y, s));
     const int64_t nn = (int64_t)nsplit * ((v.I + 127) / 128);  // one partial per row-sweep CTA
@@ -488,8 +483,7 @@ rcp_status sketch_mixed(rcp_plan_t p, const void* X, int mode) {
       {
         Span sp(p, RCP_KT_APPLY, mode);
         if (tma) {
-          RCP_TRY(launch_tc_rows_tma(T, v.I, v.J, l, 0, 0, W, p->part32, nullptr, p->dstate,
-                                     p->nsm, s, &nsplit));
+          RCP_TRY(launch_tc_rows_tma(T, v.I, v.J, l, W, p->part32, p->dstate, p->nsm, s, &nsplit));
         } else {
           RCP_TRY(launch_tc_rows(T, v.I, v.J, l, 0, 0, W, nsplit, jchunk, p->part32, nullptr,
                                  p->dstate, s));

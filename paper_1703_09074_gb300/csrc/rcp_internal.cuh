@@ -302,9 +302,8 @@ cudaError_t launch_tc_cols(const float* X, int64_t I, int64_t J, int l, const fl
                            bool ttm, DevState* st, int grid, cudaStream_t s, bool tma, bool wsplit);
 bool tc_tma_ok(const float* X);
 void tc_rows_tma_shape(int64_t I, int64_t J, int nsm, int* nb, int* rb, int* ns, int64_t* cper);
-cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, uint64_t seed,
-                               uint32_t sid, const float* Wsplit, float* part, double* normpart,
-                               DevState* st, int nsm, cudaStream_t s, int* nsplit);
+cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, const float* Wsplit,
+                               float* part, DevState* st, int nsm, cudaStream_t s, int* nsplit);
 cudaError_t launch_q_to_qt32(const double* Q, int64_t I, int l, float* QT, cudaStream_t s);
 cudaError_t launch_reduce_f32(const float* part, int64_t nsplit, int64_t n, double* out,
                               cudaStream_t s);

@@ -502,7 +502,9 @@ k_tc_cols(const float* __restrict__ X, int64_t I, int64_t J, int l, int64_t Ipad
 //                        b + 1's MMAs.
 constexpr int kColsThreads = 352;
 constexpr int kEpiPitchPad = 1;
-constexpr int kTS = 4;  // tensor-memory A stages and B stages
+constexpr int kTS = 4;  // tensor-memory A stages
+constexpr int kGrp = 2; // chunks per hand-off to the MMA thread (kTS / kGrp hand-off slots)
+constexpr int kSlots = kTS / kGrp;
 
 __host__ __device__ constexpr uint32_t tmem_cols_pow2(uint32_t n) {
   return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512;
@@ -525,8 +527,8 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   uint8_t* rawb = sm;                        // RS x 16 KB of X
   uint8_t* bring = sm + RS * kA;             // BS x kB of [Q_hi; Q_lo]
   float* ep = (float*)(bring + BS * kB);     // TTM epilogue rows (4 warps x 32 rows x EP)
-  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kTS], tfree[kTS], accf[2],
-      acce[2];
+  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kSlots], tfree[kSlots],
+      accf[2], acce[2];
   __shared__ uint32_t tbase_sh;
   __shared__ volatile int abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -540,7 +542,7 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tc::mbar_init(&bfull[s], 1);
       tc::mbar_init(&bfree[s], 1);
     }
-    for (int s = 0; s < kTS; ++s) {
+    for (int s = 0; s < kSlots; ++s) {
       tc::mbar_init(&tconv[s], 4);
       tc::mbar_init(&tfree[s], 1);
     }
@@ -606,49 +608,56 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
   } else if (warp == 1) {
     // ---- MMA issuer.  This thread's shared-memory accesses (barrier polls, flags)
-    // wait behind its MMAs in flight, so the loop makes one poll per chunk and
-    // keeps its indices in registers (no divisions).
+    // wait behind its MMAs in flight, so the loop polls once per group of kGrp
+    // chunks and keeps its indices in registers (no divisions).
     if (lane == 0) {
       int64_t issued = 0;
-      int kc = 0, t = 0, b = 0, acc = 0;
+      int kc = 0, b = 0, acc = 0, slot = 0;
       int64_t bl = 0;
-      uint32_t tph = 0;
-      for (int64_t g = 0; g < total; ++g) {
-        if (kc == 0 && bl >= 2 &&
-            !tc::mbar_wait(&acce[acc], (uint32_t)((bl / 2 - 1) & 1), kWaitBudget)) {
-          fail();
-          break;
-        }
-        // one wait per chunk: the converters also vouch for the B tile
-        if (!tc::mbar_wait(&tconv[t], tph, kWaitBudget)) {
+      uint32_t sph = 0;
+      for (int64_t g0 = 0; g0 < total; g0 += kGrp) {
+        // the group's chunks are converted and their B tiles have landed
+        if (!tc::mbar_wait(&tconv[slot], sph, kWaitBudget)) {
           fail();
           break;
         }
         tc::tc_fence_after_sync();
-        const uint32_t d = tbase + (uint32_t)acc * NACC;
-        const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
-        const uint32_t bq = tc::smem_u32(bring + b * kB);
+        bool bad = false;
+        for (int c = 0; c < kGrp && g0 + c < total; ++c) {
+          if (kc == 0 && bl >= 2 &&
+              !tc::mbar_wait(&acce[acc], (uint32_t)((bl / 2 - 1) & 1), kWaitBudget)) {
+            bad = true;
+            break;
+          }
+          const uint32_t d = tbase + (uint32_t)acc * NACC;
+          const uint32_t ahi = tbase + ACOL + (uint32_t)(slot * kGrp + c) * 64;
+          const uint32_t bq = tc::smem_u32(bring + b * kB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          tc::mma_tf32_tmem_a(d, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
-                              (kc > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k)
+            tc::mma_tf32_tmem_a(d, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
+                                (kc > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          tc::mma_tf32_tmem_a(d, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_N,
-                              1u);
-        tc::mma_commit(&tfree[t]);
-        tc::mma_commit(&bfree[b]);
-        if (kc == nkc - 1) tc::mma_commit(&accf[acc]);
-        issued = g + 1;
-        if (++t == kTS) {
-          t = 0;
-          tph ^= 1u;
+          for (int k = 0; k < 4; ++k)
+            tc::mma_tf32_tmem_a(d, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k),
+                                IDESC_N, 1u);
+          tc::mma_commit(&bfree[b]);
+          if (kc == nkc - 1) tc::mma_commit(&accf[acc]);
+          issued = g0 + c + 1;
+          if (++b == BS) b = 0;
+          if (++kc == nkc) {
+            kc = 0;
+            ++bl;
+            acc ^= 1;
+          }
         }
-        if (++b == BS) b = 0;
-        if (++kc == nkc) {
-          kc = 0;
-          ++bl;
-          acc ^= 1;
+        tc::mma_commit(&tfree[slot]);
+        if (bad) {
+          fail();
+          break;
+        }
+        if (++slot == kSlots) {
+          slot = 0;
+          sph ^= 1u;
         }
       }
       // the tensor cores are done with every stage before the CTA may leave
@@ -677,7 +686,12 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&rempty[r]);  // the raw tile is in registers now
-      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
+      // group gq = g / kGrp uses slot gq % kSlots (A stages slot kGrp .. + kGrp - 1);
+      // its first chunk waits until the MMAs of the slot's previous group are done
+      const int64_t gq = g / kGrp;
+      const int slot = (int)(gq % kSlots), cg = (int)(g % kGrp);
+      if (cg == 0 && gq >= kSlots &&
+          !tc::mbar_wait(&tfree[slot], (uint32_t)((gq / kSlots - 1) & 1), kWaitBudget)) {
         fail();
         break;
       }
@@ -691,7 +705,7 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (lane == 0) {
         // the B tile of this chunk has landed too (the issuer waits on tconv only)
         if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
-        tc::mbar_arrive(&tconv[t]);
+        if (cg == kGrp - 1 || g == total - 1) tc::mbar_arrive(&tconv[slot]);
       }
     }
   } else {
@@ -752,23 +766,23 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (warp == 1) tc::tmem_dealloc(tbase, NCOLS);
 }
 
-// Row sweep with TMA-fed stages: P = X_(1) V over this CTA's row block
-// (rb rows of i, rb a multiple of 4, the blocks as equal as possible) and its
-// range of 32-column chunks of j.  V = Omega_1 (SRC 0, regenerated per chunk)
-// or the power iteration's W (SRC 1, stored by the column sweep as
-// [W_hi; W_lo], l x J each).
+// Row sweep with TMA-fed stages for the power iteration's apply step,
+// P = X_(1) W over this CTA's row block (rb rows of i, rb a multiple of 4, the
+// blocks as equal as possible) and its range of 32-column chunks of j; W is
+// stored by the column sweep as [W_hi; W_lo], l x J each.  (The sketch, whose
+// cost is drawing Omega_1 per chunk, keeps the register-staged k_tc_rows: two
+// CTAs of 8 warps per SM share the draw.  A TMA-fed form measured slower with
+// the draw in its converters, and slower still with four generator warps.)
 //   X producer (warp 0) one thread: the rb x 32 tile of X (i contiguous, no
 //                       swizzle) lands by TMA in a ring of RS stages that the
 //                       converters free once they have read it;
-//   B producer (10)     SRC 1: one thread, the 2NP x 32 tile of [W_hi; W_lo]
+//   B producer (10)     one thread: the 2NP x 32 tile of [W_hi; W_lo]
 //                       (128-byte swizzle) into a ring of kTS stages freed by
 //                       the MMAs;
 //   converters (2-9)    256 threads, thread = row r (tensor-memory lane) and
 //                       one half of the chunk's 32 columns: the row's values
 //                       split into TF32 truncation and remainder, written to
-//                       tensor memory (rows >= rb as zeros); for SRC 0 they
-//                       also draw Omega_1's hi and lo into a shared-memory B
-//                       stage, and for NORM sum X^2;
+//                       tensor memory (rows >= rb as zeros);
 //   issuer (warp 1)     one thread: A_hi [V_hi | V_lo] (N = 2 NP) and A_lo V_hi
 //                       (N = NP), A from tensor memory, into one accumulator
 //                       for the whole range;
@@ -776,11 +790,11 @@ k_tc_cols_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 //                       0 .. 63): the two halves summed into the split's partial.
 constexpr int kRowsThreads = 352;
 
-template <int NP, int RS, int BS, int SRC, bool NORM>
+template <int NP, int RS, int BS>
 __global__ void __launch_bounds__(kRowsThreads, 1)
 k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
-              int64_t I, int64_t J, int l, int rb, int64_t cper, uint64_t seed, uint32_t sid,
-              float* __restrict__ part, double* __restrict__ normpart, DevState* st) {
+              int64_t I, int64_t J, int l, int rb, int64_t cper, float* __restrict__ part,
+              DevState* st) {
   constexpr uint32_t kB = 2 * NP * 128;
   constexpr uint32_t kXR = 16384;                      // X stage (rb x 32 floats, rb <= 128)
   constexpr uint32_t NACC = 2 * NP;
@@ -791,12 +805,10 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* rawb = sm;
-  uint8_t* bring = sm + RS * kXR;                      // BS B stages (Omega_1 or [W_hi; W_lo])
-  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kTS], tfree[kTS], accf;
+  uint8_t* bring = sm + RS * kXR;                      // BS B stages of [W_hi; W_lo]
+  __shared__ uint64_t rfull[RS], rempty[RS], bfull[BS], bfree[BS], tconv[kSlots], tfree[kSlots], accf;
   __shared__ uint32_t tbase_sh;
   __shared__ volatile int abort_sh;
-  __shared__ uint16_t boff[SRC == 0 ? 32 * 64 : 1];   // element t = jj l + c of Omega -> B offset
-  __shared__ double red[8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int blk = blockIdx.x, split = blockIdx.y;
   const int64_t i0 = (int64_t)blk * rb;
@@ -814,7 +826,7 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tc::mbar_init(&bfull[s], 1);
       tc::mbar_init(&bfree[s], 1);
     }
-    for (int s = 0; s < kTS; ++s) {
+    for (int s = 0; s < kSlots; ++s) {
       tc::mbar_init(&tconv[s], 8);
       tc::mbar_init(&tfree[s], 1);
     }
@@ -822,19 +834,9 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     abort_sh = 0;
     tc::fence_mbar_init();
     tc::tma_prefetch_desc(&tmX);
-    if (SRC == 1) tc::tma_prefetch_desc(&tmW);
+    tc::tma_prefetch_desc(&tmW);
   }
   if (warp == 1) tc::tmem_alloc(&tbase_sh, NCOLS);
-  if (SRC == 0) {
-    // the B stages start at zero: rows >= l never change
-    for (int e = tid; e < (int)(BS * kB / 16); e += kRowsThreads)
-      ((float4*)bring)[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int t = tid; t < 32 * l; t += kRowsThreads) {
-      const int jj = t / l, c = t - jj * l;
-      boff[t] = (uint16_t)tc::sw128_offset((uint32_t)c, (uint32_t)jj);
-    }
-    tc::fence_proxy_async_smem();
-  }
   tc::tc_fence_before_sync();
   __syncthreads();
   tc::tc_fence_after_sync();
@@ -862,7 +864,7 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         if (!tc::mbar_wait(&rfull[g % RS], (uint32_t)((g / RS) & 1), kWaitBudget)) fail();
     }
   } else if (warp == 10) {
-    if (SRC == 1 && lane == 0) {
+    if (lane == 0) {
       int64_t issued = 0;
       for (int64_t g = 0; g < total && !abort_sh; ++g) {
         const int b = (int)(g % BS);
@@ -878,35 +880,39 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
     }
   } else if (warp == 1) {
-    // MMA issuer: one poll per chunk, indices in registers (see the column sweep)
+    // MMA issuer: one poll per group of kGrp chunks, indices in registers (see
+    // the column sweep)
     if (lane == 0) {
       int64_t issued = 0;
-      int t = 0, b = 0;
-      uint32_t tph = 0;
-      for (int64_t g = 0; g < total; ++g) {
-        if (!tc::mbar_wait(&tconv[t], tph, kWaitBudget)) {
+      int b = 0, slot = 0;
+      uint32_t sph = 0;
+      for (int64_t g0 = 0; g0 < total; g0 += kGrp) {
+        if (!tc::mbar_wait(&tconv[slot], sph, kWaitBudget)) {
           fail();
           break;
         }
         tc::tc_fence_after_sync();
-        const uint32_t ahi = tbase + ACOL + (uint32_t)t * 64;
-        const uint32_t bq = tc::smem_u32(bring + (uint32_t)b * kB);
+        for (int c = 0; c < kGrp && g0 + c < total; ++c) {
+          const int64_t g = g0 + c;
+          const uint32_t ahi = tbase + ACOL + (uint32_t)(slot * kGrp + c) * 64;
+          const uint32_t bq = tc::smem_u32(bring + (uint32_t)b * kB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          tc::mma_tf32_tmem_a(tbase, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
-                              (g > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k)
+            tc::mma_tf32_tmem_a(tbase, ahi + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k), IDESC_W,
+                                (g > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          tc::mma_tf32_tmem_a(tbase, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k),
-                              IDESC_N, 1u);
-        tc::mma_commit(&tfree[t]);
-        tc::mma_commit(&bfree[b]);
-        issued = g + 1;
-        if (++t == kTS) {
-          t = 0;
-          tph ^= 1u;
+          for (int k = 0; k < 4; ++k)
+            tc::mma_tf32_tmem_a(tbase, ahi + 32u + 8u * k, tc::desc_kmajor_sw128(bq + 32u * k),
+                                IDESC_N, 1u);
+          tc::mma_commit(&bfree[b]);
+          issued = g + 1;
+          if (++b == BS) b = 0;
         }
-        if (++b == BS) b = 0;
+        tc::mma_commit(&tfree[slot]);
+        if (++slot == kSlots) {
+          slot = 0;
+          sph ^= 1u;
+        }
       }
       if (issued > 0) tc::mma_commit(&accf);
       for (int64_t g = issued > BS ? issued - BS : 0; g < issued; ++g)
@@ -914,11 +920,9 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
   } else {
     // ---- converters (256 threads): row r = lane of the warp's quarter, columns 16 h .. + 15
-    const int ct = tid - 64;
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int r = 32 * q + lane;
     const bool rv = r < rb;
-    double nrm = 0.0;
     for (int64_t g = 0; g < total && !abort_sh; ++g) {
       const int rs = (int)(g % RS), t = (int)(g % kTS);
       if (!tc::mbar_wait(&rfull[rs], (uint32_t)((g / RS) & 1), kWaitBudget)) {
@@ -927,18 +931,18 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       const float* Xr = (const float*)(rawb + rs * kXR);
       float hv[16], lv[16];
-      float cn = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         const float x = rv ? Xr[(16 * h + jj) * rb + r] : 0.0f;
-        if (NORM) cn = fmaf(x, x, cn);
         hv[jj] = tf32_hi(x);
         lv[jj] = x - hv[jj];
       }
-      if (NORM) nrm += (double)cn;
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&rempty[rs]);  // the X tile is in registers now
-      if (g >= kTS && !tc::mbar_wait(&tfree[t], (uint32_t)((g / kTS - 1) & 1), kWaitBudget)) {
+      const int64_t gq = g / kGrp;
+      const int slot = (int)(gq % kSlots), cg = (int)(g % kGrp);
+      if (cg == 0 && gq >= kSlots &&
+          !tc::mbar_wait(&tfree[slot], (uint32_t)((gq / kSlots - 1) & 1), kWaitBudget)) {
         fail();
         break;
       }
@@ -946,49 +950,13 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + ACOL + (uint32_t)t * 64 + 16u * h;
       tc::tmem_st16(ta, hv);
       tc::tmem_st16(ta + 32u, lv);
-      if (SRC == 0) {
-        // Omega_1[j, c] = element j l + c of the reduced-precision stream
-        const int b = (int)(g % BS);
-        if (g >= BS && !tc::mbar_wait(&bfree[b], (uint32_t)((g / BS - 1) & 1), kWaitBudget)) {
-          fail();
-          break;
-        }
-        uint8_t* Bh = bring + (uint32_t)b * kB;
-        uint8_t* Bl = Bh + NP * 128;
-        const int64_t j0 = 32 * (c0 + g);
-        const int64_t e0 = j0 * l;
-        const int lead = (int)(e0 & 3);
-        const int tend = (int)((J - j0 < 32 ? J - j0 : 32) * l);
-        const int nq = (32 * l + lead + 3) >> 2;
-        for (int qq = ct; qq < nq; qq += 256) {
-          const float4 z = normal_quad_f32(seed, sid, kPurposeSketch, (uint64_t)((e0 >> 2) + qq));
-          const float zz[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int te = 4 * qq + u - lead;
-            if (te >= 0 && te < 32 * l) {
-              const float v = te < tend ? zz[u] : 0.0f;
-              const float bh = tf32_hi(v);
-              *(float*)(Bh + boff[te]) = bh;
-              *(float*)(Bl + boff[te]) = v - bh;
-            }
-          }
-        }
-        tc::fence_proxy_async_smem();
-      }
       tc::tmem_st_wait();
       tc::tc_fence_before_sync();
       __syncwarp();
       if (lane == 0) {
-        if (SRC == 1 && !tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget))
-          fail();
-        tc::mbar_arrive(&tconv[t]);
+        if (!tc::mbar_wait(&bfull[g % BS], (uint32_t)((g / BS) & 1), kWaitBudget)) fail();
+        if (cg == kGrp - 1 || g == total - 1) tc::mbar_arrive(&tconv[slot]);
       }
-    }
-    if (NORM) {
-      double d = nrm;
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-      if (lane == 0) red[warp - 2] = d;
     }
     // ---- epilogue: warps 2-5 read tensor-memory lanes 32 (w % 4) .. + 31
     if (warp < 6) {
@@ -1018,9 +986,6 @@ k_tc_rows_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (!ok) set_status(st, RCP_ETIMEOUT);
   tc::tc_fence_before_sync();
   __syncthreads();
-  if (NORM && tid == 0)
-    normpart[(int64_t)split * gridDim.x + blk] =
-        ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
   if (warp == 1) tc::tmem_dealloc(tbase, NCOLS);
 }
 
@@ -1128,18 +1093,17 @@ cudaError_t cols_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmQ, int6
   return cudaGetLastError();
 }
 
-template <int NP, int RS, int BS, int SRC, bool NORM>
+template <int NP, int RS, int BS>
 cudaError_t rows_tma_launch(const CUtensorMap& tmX, const CUtensorMap& tmW, int64_t I, int64_t J,
-                            int l, int rb, int nb, int ns, int64_t cper, uint64_t seed,
-                            uint32_t sid, float* part, double* normpart, DevState* st,
+                            int l, int rb, int nb, int ns, int64_t cper, float* part, DevState* st,
                             cudaStream_t s) {
-  auto kern = k_tc_rows_tma<NP, RS, BS, SRC, NORM>;
+  auto kern = k_tc_rows_tma<NP, RS, BS>;
   const int smem = RS * 16384 + BS * 2 * NP * 128 + 1024;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<dim3((unsigned)nb, (unsigned)ns), kRowsThreads, smem, s>>>(tmX, tmW, I, J, l, rb, cper, seed,
-                                                                   sid, part, normpart, st);
+  kern<<<dim3((unsigned)nb, (unsigned)ns), kRowsThreads, smem, s>>>(tmX, tmW, I, J, l, rb, cper, part,
+                                                                   st);
   return cudaGetLastError();
 }
 
@@ -1201,12 +1165,11 @@ void tc_rows_tma_shape(int64_t I, int64_t J, int nsm, int* nb, int* rb, int* ns,
   *ns = (int)((nchunk + *cper - 1) / *cper);
 }
 
-// TMA-fed row sweep (tc_tma_ok(X) must hold).  Wsplit: the column sweep's
-// [W_hi; W_lo] (2 l x J), or null for Omega_1.  *nsplit receives the number of
-// j-split partials per row written to part.
-cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, uint64_t seed,
-                               uint32_t sid, const float* Wsplit, float* part, double* normpart,
-                               DevState* st, int nsm, cudaStream_t s, int* nsplit) {
+// TMA-fed row sweep of the power iteration (tc_tma_ok(X) must hold): P = X_(1) W
+// with Wsplit the column sweep's [W_hi; W_lo] (2 l x J).  *nsplit receives the
+// number of j-split partials per row written to part.
+cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, const float* Wsplit,
+                               float* part, DevState* st, int nsm, cudaStream_t s, int* nsplit) {
   int nb = 0, rb = 0, ns = 0;
   int64_t cper = 0;
   tc_rows_tma_shape(I, J, nsm, &nb, &rb, &ns, &cper);
@@ -1219,23 +1182,15 @@ cudaError_t launch_tc_rows_tma(const float* X, int64_t I, int64_t J, int l, uint
     const cuuint32_t box[2] = {(cuuint32_t)rb, 32};
     if (!tmap_f32(&tmX, X, 2, dims, strides, box, false)) return cudaErrorInvalidValue;
   }
-  if (Wsplit) {
+  {
     const cuuint64_t dims[3] = {(cuuint64_t)J, (cuuint64_t)l, 2};
     const cuuint64_t strides[2] = {(cuuint64_t)J * 4, (cuuint64_t)l * J * 4};
     const cuuint32_t box[3] = {32, (cuuint32_t)NP, 2};
     if (!tmap_f32(&tmW, Wsplit, 3, dims, strides, box, true)) return cudaErrorInvalidValue;
-  } else {
-    tmW = tmX;  // unused by the Omega form
   }
-  const bool norm = normpart != nullptr;
-  if (NP == 32) {
-    if (Wsplit) return rows_tma_launch<32, 8, 8, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
-    if (norm) return rows_tma_launch<32, 8, 8, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
-    return rows_tma_launch<32, 8, 8, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
-  }
-  if (Wsplit) return rows_tma_launch<64, 6, 6, 1, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, 0, 0, part, nullptr, st, s);
-  if (norm) return rows_tma_launch<64, 6, 6, 0, true>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, normpart, st, s);
-  return rows_tma_launch<64, 6, 6, 0, false>(tmX, tmW, I, J, l, rb, nb, ns, cper, seed, sid, part, nullptr, st, s);
+  // X stages and B stages: about 128 KB of X in flight
+  if (NP == 32) return rows_tma_launch<32, 8, 8>(tmX, tmW, I, J, l, rb, nb, ns, cper, part, st, s);
+  return rows_tma_launch<64, 6, 6>(tmX, tmW, I, J, l, rb, nb, ns, cper, part, st, s);
 }
 
 // Column sweep; tma selects the TMA-fed kernel (tc_tma_ok(X) must hold), and
