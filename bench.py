@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-compare", action="store_true",
                     help="skip the FP64 GPU path comparison (profiling runs)")
+    ap.add_argument("--init", choices=["randn", "eig", "learned"], default="randn",
+                    help="ALS start on the single-tensor workloads (learned: the warm-start "
+                         "network, trained first as for the batched workload, untimed)")
     ap.add_argument("--warm-start", choices=["learned", "random"], default="learned",
                     help="ALS initialisation of the batched workload")
     return ap.parse_args()
@@ -214,8 +217,25 @@ def run_ours(args):
         args.precision = "f64" if w.dtype == "f64" else "mixed"
     X = torch.from_numpy(w.kolda).to(dev)
     stream = torch.cuda.current_stream(dev)
+    train_info = None
+    net = None
+    if args.init == "learned":
+        from paper_1703_09074_gb300 import WarmStartNet
+        from paper_1703_09074_gb300 import warmstart as W
+        t0 = time.perf_counter()
+        data = W.generate(20480, seed=101, device=dev)
+        net = WarmStartNet(batch=256, seed=7, stream=stream)
+        val = W.Evaluator(256, seed=102, device=dev, budgets=(10,))
+        hist, best_epoch = W.train(net, data, epochs=10, lr=3e-4, evaluator=val)
+        val.close()
+        train_info = {"samples": int(data["x"].shape[0]), "epochs": 10, "best_epoch": best_epoch,
+                      "setup_s": time.perf_counter() - t0}
+        del data
     plan = Plan(w.dims, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, seed=0,
-                in_dtype=in_dt, precision=args.precision, host_staging=True, stream=stream)
+                in_dtype=in_dt, precision=args.precision, host_staging=True, stream=stream,
+                init=args.init)
+    if net is not None:
+        plan.set_warm_start(net)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -312,11 +332,16 @@ def run_ours(args):
     sketch_gbs = xbytes / (sk_ms / sk_n / 1e3) / 1e9 if sk_n else None
     # ALS (one launch per decomposition): time per mode update and share of the step
     als_ms = stages["als"]["ms_per_step"]
+    # the one-cluster kernel serves every l_n <= 32 with R <= 32 in the precision form
+    one_cluster = (args.precision == "mixed" and w.rank <= 32
+                   and max(plan.widths) <= 32)
     updates = max(res["iters"], 1) * len(w.dims)
     als_line = {"ms_per_step": als_ms, "us_per_mode_update": 1e3 * als_ms / updates,
                 "mode_updates": updates, "share_of_step": als_ms / (total_ms / args.steps),
-                "bound": "latency (dependent small solves on one cluster, no HBM traffic: "
-                         "the core stays in shared memory)"}
+                "bound": ("latency (dependent small solves on one cluster, no HBM traffic: "
+                          "the core stays in shared memory)") if one_cluster else
+                         ("latency and L2 (persistent cooperative kernel: dimension-tree "
+                          "MTTKRP over the core in L2, grid barriers between phases)")}
 
     # end to end through the host-buffer entry point (H2D of X and D2H of factors inside)
     e2e = []
@@ -338,7 +363,8 @@ def run_ours(args):
     f64_cmp = None
     if args.precision == "mixed" and not args.no_f64_compare:
         p64 = Plan(w.dims, w.rank, w.oversample, w.power_iters, w.tol, w.max_iters, seed=0,
-                   in_dtype=in_dt, precision="f64", stream=stream)
+                   in_dtype=in_dt, precision="f64", stream=stream,
+                   init=args.init if args.init != "learned" else "randn")
         p64.decompose(X)
         p64.result()
         e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -365,12 +391,16 @@ def run_ours(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "f64" else "f32acc/tf32",
             "data": "synthetic",
-            "config": {"workload": desc, "precision": args.precision,
-                       "l2": "X (256 MB) larger than L2, and a 512 MB L2 flush between steps",
+            "config": {"workload": desc, "precision": args.precision, "init": args.init,
+                       "l2": f"X ({xbytes / 1e6:.0f} MB) "
+                             f"{'larger' if xbytes > 129e6 else 'smaller'} than L2, "
+                             "and a 512 MB L2 flush between steps",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "sketch_pass_gbs": sketch_gbs,
             "fit": res["fit"], "rel_err": res["rel_err"], "als_iters": res["iters"],
             "fp64_gpu_path": f64_cmp,
+            "learned_start_used": bool(res["info"] & _lib.RCP_INFO_LEARNED_INIT) if net else None,
+            "training": train_info,
             "stages": stages,
             "mode1_sweeps": mode1,
             "roofline": roof,

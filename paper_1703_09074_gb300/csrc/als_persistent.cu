@@ -267,11 +267,145 @@ __device__ void als_body(const PersArgs& a, int g) {
       // and prepare the Gram solve during phase A; the others write partials.
       const int gw0 = (G > 1 && G >= 2 * ln) ? ln : 0;
       const int GW = G - gw0, gi = g - gw0;
+      constexpr bool kMixed = sizeof(TM) == 4;
+      if (kMixed && a.S != nullptr) {
+        // ---- phase A, dimension tree (mixed form, N >= 3, R <= 32): mode n's
+        // MTTKRP is M = S_c reduced over the modes other than n and c against
+        // their factors, with S_c = B x_c A_c^T (l_c contracted, the other modes
+        // kept, R columns).  c = 2 for mode 1 and c = 1 otherwise: S_1 is formed
+        // once per sweep, after mode 1's update, and serves modes 2..N.
+        const int c = n0 == 0 ? 1 : 0;
+        if (n0 <= 1) {
+          // S_c[rest, r] = sum_{i_c} B[a + Lc (i_c + l_c b)] A_c[i_c, r], rest = a + Lc b;
+          // thread per rest index, all R columns in registers (FP32 products and sums
+          // over l_c <= 64 terms), A_c in shared memory row by row
+          const int lc = a.dims[c];
+          int Lc = 1, Rc = 1;
+          for (int m = 0; m < c; ++m) Lc *= a.dims[m];
+          for (int m = c + 1; m < N; ++m) Rc *= a.dims[m];
+          const int nrest = Lc * Rc;
+          float* FcT = (float*)Bs;  // l_c x 32, row-major, zero beyond R
+          for (int e = tid; e < lc * 32; e += kThreads) {
+            const int i = e >> 5, r = e & 31;
+            FcT[e] = r < R ? (float)Fac[foff[c] + i + lc * r] : 0.0f;
+          }
+          __syncthreads();
+          double nbs = 0.0;
+          const bool want_nb = it == 1 && n0 == 0;
+          for (int rest = gi * kThreads + tid; gi >= 0 && rest < nrest; rest += GW * kThreads) {
+            const int bq = rest / Lc, aq = rest - bq * Lc;
+            const float* Bp = (const float*)a.B + aq + (int64_t)Lc * lc * bq;
+            float* Sp = a.S + (int64_t)rest * 32;
+            // two passes of 16 columns; FP32 sums of 8 terms carried into double-word
+            // accumulators (Knuth's TwoSum), so each S entry is accurate to a few u
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+              float shi[16], slo[16];
+#pragma unroll
+              for (int r = 0; r < 16; ++r) shi[r] = slo[r] = 0.0f;
+              for (int ic0 = 0; ic0 < lc; ic0 += 8) {
+                float t[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) t[r] = 0.0f;
+                const int ic1 = min(lc, ic0 + 8);
+                for (int ic = ic0; ic < ic1; ++ic) {
+                  const float x = Bp[(int64_t)Lc * ic];
+                  if (want_nb && h == 0) nbs = fma((double)x, (double)x, nbs);
+                  const float4* f = (const float4*)(FcT + ic * 32 + 16 * h);
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+                    const float4 v = f[q];
+                    t[4 * q] = fmaf(x, v.x, t[4 * q]);
+                    t[4 * q + 1] = fmaf(x, v.y, t[4 * q + 1]);
+                    t[4 * q + 2] = fmaf(x, v.z, t[4 * q + 2]);
+                    t[4 * q + 3] = fmaf(x, v.w, t[4 * q + 3]);
+                  }
+                }
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                  const dwf u2 = dw_two_sum(shi[r], t[r]);
+                  shi[r] = u2.hi;
+                  slo[r] = __fadd_rn(slo[r], u2.lo);
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                ((float4*)(Sp + 16 * h))[q] =
+                    make_float4(shi[4 * q] + slo[4 * q], shi[4 * q + 1] + slo[4 * q + 1],
+                                shi[4 * q + 2] + slo[4 * q + 2], shi[4 * q + 3] + slo[4 * q + 3]);
+            }
+          }
+          if (want_nb && gi >= 0) {
+            for (int o = 16; o > 0; o >>= 1) nbs += __shfl_down_sync(0xffffffffu, nbs, o);
+            if (lane == 0) red[8 + warp] = nbs;
+            __syncthreads();
+            if (tid == 0) {
+              double sb = 0.0;
+              for (int w = 0; w < kWarps; ++w) sb += red[8 + w];
+              a.nbp[gi] = sb;
+            }
+          }
+          // every CTA's part of S_c is written before any CTA reduces it
+          if (!phase_sync(a, G, epoch)) { ok = false; break; }
+        }
+        // M partials: warp w takes rows i = w, w + 8, ... of mode n; the CTA takes a
+        // range of the multi-indices p over the modes other than n and c; lane r
+        // accumulates sum_p S_c[(i, p), r] prod_{m != n, c} A_m[p_m, r] in FP32 over
+        // the CTA's range (fixed order; the partials are summed in FP64 after)
+        if (gi >= 0) {
+          int np_ = 1;
+          for (int m = 0; m < N; ++m)
+            if (m != n0 && m != c) np_ *= a.dims[m];
+          // stride of mode n in S_c's index (Kolda order over the modes other than c)
+          int sn = 1;
+          for (int m = 0; m < n0; ++m)
+            if (m != c) sn *= a.dims[m];
+          const int per = (np_ + GW - 1) / GW;
+          const int p0 = gi * per, p1 = min(np_, p0 + per);
+          constexpr int kRowsPerWarp = 8;  // l_n <= 64
+          // double-word accumulators of exact products (TwoProduct by FMA, TwoSum)
+          float mhi[kRowsPerWarp], mlo[kRowsPerWarp];
+#pragma unroll
+          for (int k = 0; k < kRowsPerWarp; ++k) mhi[k] = mlo[k] = 0.0f;
+          for (int pp = p0; pp < p1; ++pp) {
+            // digits of pp over the modes other than n and c, the S_c offset and weight
+            int q = pp, off = 0, st_ = 1;
+            float wgt = lane < R ? 1.0f : 0.0f;
+            for (int m = 0; m < N; ++m) {
+              if (m == c) continue;
+              if (m != n0) {
+                const int d = q % a.dims[m];
+                q /= a.dims[m];
+                off += d * st_;
+                if (lane < R) wgt *= (float)Fac[foff[m] + d + a.dims[m] * lane];
+              }
+              st_ *= a.dims[m];
+            }
+#pragma unroll
+            for (int k = 0; k < kRowsPerWarp; ++k) {
+              const int i = warp + kWarps * k;
+              if (i < ln) {
+                const float sv = a.S[(int64_t)(off + i * sn) * 32 + lane];
+                const float pv = __fmul_rn(sv, wgt);
+                const float pe = __fmaf_rn(sv, wgt, -pv);
+                const dwf u2 = dw_two_sum(mhi[k], pv);
+                mhi[k] = u2.hi;
+                mlo[k] = __fadd_rn(mlo[k], __fadd_rn(u2.lo, pe));
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kRowsPerWarp; ++k) {
+            const int i = warp + kWarps * k;
+            if (i < ln && lane < R)
+              a.part[(int64_t)gi * nout + i + ln * lane] = (double)mhi[k] + (double)mlo[k];
+          }
+        }
+      } else {
       // ---- phase A: MTTKRP partial over this CTA's column tiles
       // Each thread owns register blocks of outputs (below) and forms their tile
       // sums with independent FMA chains.  The mixed form sums its FP32 tile sums
       // across tiles in double-word FP32 (Knuth's TwoSum), the FP64 path in FP64.
-      constexpr bool kMixed = sizeof(TM) == 4;
       double acc[kMixed ? 1 : KACC];
       float ahi[kMixed ? KACC : 1], alo[kMixed ? KACC : 1];
 #pragma unroll
@@ -295,7 +429,7 @@ __device__ void als_body(const PersArgs& a, int g) {
       // B tile: Bs[i][jj] = B[(j % L) + L (i + ln (j / L))], with lanes along the
       // contiguous index (i for mode 1, the column otherwise).  The next tile is
       // loaded into registers while the current one is multiplied: kPS slots per
-      // thread, 8 for l_n <= 64, 4 for the batched kernel (l_n <= 32).
+      // thread, 8 for l_n <= 64, 4 for a small register budget (l_n <= 32).
       constexpr int kPS = KACC >= 8 ? 8 : 4;
       auto b_slot = [&](int s2, int& i, int& jj) {
         if (L == 1) {
@@ -438,6 +572,7 @@ __device__ void als_body(const PersArgs& a, int g) {
           for (int w = 0; w < kWarps; ++w) s += red[8 + w];
           a.nbp[gi] = s;
         }
+      }
       }
       if (gw0 > 0 && g < ln) prepare_solve(n0);
       if (!phase_sync(a, G, epoch)) { ok = false; break; }
@@ -819,15 +954,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_als_persistent(PersArgs a) {
   als_body<TM, KACC>(a, blockIdx.x);
 }
 
-// Batched form: CTA b runs the whole ALS of problem b alone (G = 1).
-// Batched problems have l_n <= 32 and R <= 32: one 2 x 2 block of MTTKRP
-// outputs per thread, which leaves registers for two CTAs per SM.
-template <typename TM>
-__global__ void __launch_bounds__(kThreads, 2) k_als_batched(const PersArgs* __restrict__ args) {
-  const PersArgs a = args[blockIdx.x];
-  als_body<TM, 4>(a, 0);
-}
-
 template <typename TM>
 size_t smem_bytes(const rcp_plan_s* p) {
   int lmax = 1, ftot = 0;
@@ -889,6 +1015,8 @@ cudaError_t launch_typed(rcp_plan_s* p, const void* B, const int* user_init_dev,
   a.user_init = p->user_init ? 1 : 0;
   a.budget = p->cfg.wait_budget;
   a.user_init_dev = user_init_dev;
+  // mixed form: the dimension-tree MTTKRP when the plan holds its scratch
+  a.S = sizeof(TM) == 4 ? p->als_S : nullptr;
   // R <= 32: each row-owning CTA inverts V in double-word arithmetic (path 3)
   a.direct64 = 0;
   void* args[] = {&a};
@@ -908,31 +1036,6 @@ bool als_persistent_fits(const rcp_plan_s* p, bool f32) {
   if (p->core_elems >= (1LL << 31)) return false;
   const size_t smem = f32 ? smem_bytes<float>(p) : smem_bytes<double>(p);
   return smem <= 200 * 1024;
-}
-
-size_t als_smem_bytes_f32(int N, int R, const int* l) {
-  int lmax = 1, ftot = 0;
-  for (int m = 0; m < N; ++m) {
-    lmax = lmax > l[m] ? lmax : l[m];
-    ftot += l[m] * R;
-  }
-  const size_t RR = R, NN = N;
-  const size_t d = NN * RR * RR + RR * (RR + 1) + RR + (size_t)lmax * RR + RR + 64 + kWarps * 64;
-  const size_t f = (RR * (RR + 1) > 1024 ? RR * (RR + 1) : 1024) + RR;
-  return d * sizeof(double) + f * sizeof(float) + 16 +
-         ((size_t)ftot + (size_t)lmax * kBP + (size_t)kTileJ * RR) * sizeof(float) + 16 +
-         (size_t)2 * 32 * 64 * sizeof(float2) + NN * RR * RR * sizeof(float);
-}
-
-cudaError_t prepare_als_batched(size_t smem) {
-  return cudaFuncSetAttribute(k_als_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
-}
-
-cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s) {
-  count_launches(1);
-  k_als_batched<float><<<count, kThreads, smem, s>>>(dev_args);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, const int* user_init_dev,

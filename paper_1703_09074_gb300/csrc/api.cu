@@ -112,6 +112,7 @@ void free_plan(rcp_plan_t p) {
   cudaFree(p->lu_cidx);
   cudaFree(p->lu_prow);
   cudaFree(p->lam_stage);
+  cudaFree(p->als_S);
   if (p->prof) {
     for (int k = 0; k < p->prof_cap; ++k) {
       cudaEventDestroy(p->prof[k].a);
@@ -326,6 +327,16 @@ rcp_status rcp_plan(const rcp_config* cfg, void* stream, rcp_plan_t* out) {
     A(dalloc(&p->part32, p32));
     A(dalloc(&p->QT32, (int64_t)2 * 64 * tc_ipad(Imax)));
     A(dalloc(&p->Bcore_own, p->core_elems));
+    // the dimension-tree MTTKRP of the persistent ALS kernel (cores beyond the
+    // one-cluster kernel): B contracted over mode 1 or 2, R <= 32 columns
+    if (st == RCP_OK && N >= 3 && p->R <= 32 && !als_cluster_fits(p)) {
+      int lmx = 1;
+      for (int n = 0; n < N; ++n) lmx = lmx > p->l[n] ? lmx : p->l[n];
+      if (lmx <= 64) {
+        const int64_t rest = p->core_elems / (p->l[0] < p->l[1] ? p->l[0] : p->l[1]);
+        A(dalloc(&p->als_S, rest * 32));
+      }
+    }
   }
   if (cfg->flags & RCP_FLAG_LU_NORM) {
     int64_t mrows = 1;

@@ -284,7 +284,6 @@ struct rcp_batched_s {
   const float** xptrs_host = nullptr;  // pinned
   unsigned* dummy_bar = nullptr;
   int* dummy_abort = nullptr;
-  size_t als_smem = 0;
   int lmax = 1;
   // ALS of every tensor by the one-cluster kernel with clusters of one CTA
   void* cluArgs = nullptr;           // device table of its arguments
@@ -717,13 +716,6 @@ rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
   }
   // counters: one per batched sweep launch
   p->ncounters = N * (2 + 2 * std::max(0, cfgs[0].power_iters)) + 4;
-  int lsm[kMaxN];
-  size_t smax = 0;
-  for (int b = 0; b < count; ++b) {
-    for (int n = 0; n < N; ++n) lsm[n] = p->t[b].l[n];
-    smax = std::max(smax, als_smem_bytes_f32(N, p->t[b].R, lsm));
-  }
-  p->als_smem = smax;
   if (cudaMalloc((void**)&p->counters, sizeof(unsigned) * p->ncounters) != cudaSuccess ||
       cudaMalloc((void**)&p->xptrs_dev, sizeof(float*) * count) != cudaSuccess ||
       cudaMallocHost((void**)&p->xptrs_host, sizeof(float*) * count) != cudaSuccess ||
@@ -736,8 +728,7 @@ rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
   memset(p->xptrs_host, 0, sizeof(float*) * count);
   if (cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      prepare_als_batched(p->als_smem) != cudaSuccess) {
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     free_batched(p);
     return RCP_ECUDA;

@@ -119,6 +119,7 @@ struct rcp_plan_s {
 
   // learned warm start of the single-tensor path (rcp_set_warm_start)
   rcp_plan_ws_s* ws;
+  float* als_S;   // contracted core of the dimension-tree MTTKRP (mixed form, large cores)
 
   // host staging (rcp_decompose_host)
   void* X_stage;
@@ -233,6 +234,8 @@ struct PersArgs {
   int direct64;          // solve with the FP64 Cholesky factor only (no FP32 factor + refinement)
   long long budget;      // clock cycles per grid-barrier wait (0: the default)
   const int* user_init_dev;  // when set, a device word that replaces user_init
+  float* S;              // mixed form, N >= 3, R <= 32: the contracted core of the
+                         // dimension-tree MTTKRP (core / l_c x 32 floats), else null
 };
 
 // ---------------------------------------------------------------- batched form
@@ -342,9 +345,6 @@ cudaError_t launch_bcd(rcp_plan_s* p, const void* B, bool f32, double* scratch,
                        const int* user_init_dev, cudaStream_t s);
 cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_init_dev,
                                cudaStream_t s);
-size_t als_smem_bytes_f32(int N, int R, const int* l);
-cudaError_t prepare_als_batched(size_t smem);
-cudaError_t launch_als_batched(const PersArgs* dev_args, int count, size_t smem, cudaStream_t s);
 cudaError_t launch_als_persistent(rcp_plan_s* p, const void* B, bool f32, const int* user_init_dev,
                                   cudaStream_t s);
 cudaError_t launch_to_f64(const void* src, int src_dtype, int64_t n, double* dst, cudaStream_t s);
