@@ -503,7 +503,10 @@ def run_batched(args):
             "dtype": "f32acc/tf32 sweeps, f64 QR and Gram solves, bf16 network",
             "data": "synthetic",
             "config": {"workload": WORKLOADS["c5"][1], "tensors": len(ws), "bytes": nbytes,
-                       "warm_start": args.warm_start, "autotuned_ctas_per_sm": list(choice),
+                       "warm_start": args.warm_start,
+                       "autotuned": {"row_ctas_per_sm": choice[0], "col_ctas_per_sm": choice[1],
+                                     "row_loads_in_flight": choice[2],
+                                     "col_blocks_per_item": choice[3]},
                        "l2": "inputs (3 GB) larger than L2, 512 MB flush between steps"},
             "tensors_per_s": total_tensors / (ms / 1e3),
             "input_gbs": nbytes / (ms / 1e3) / 1e9,

@@ -346,10 +346,15 @@ rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
  * updating them).  Asynchronous otherwise. */
 rcp_status rcp_batched_run(rcp_batched_t plan, const void* const* X_dev);
 
-/* Choose the launch shapes of the batched sweeps (persistent CTAs per SM for
- * the row and column sweeps, candidates 1, 2, 4, 8) by timing a complete
- * batch run per candidate pair on X_dev; keeps the fastest for later runs
- * and writes it to choice[0..1] when choice is not NULL.  Synchronises. */
+/* Choose the launch and tile shapes of the batched sweeps by timing complete
+ * batch runs on X_dev: a coordinate search, two passes, over
+ *   choice[0]  persistent CTAs per SM of the row sweeps     (1, 2, 4, 8)
+ *   choice[1]  persistent CTAs per SM of the column sweeps  (1, 2, 4, 8)
+ *   choice[2]  loads in flight per thread in the row sweeps (4, 8)
+ *   choice[3]  256-column blocks per column work item       (1, 2, 4, 8)
+ * None of them changes the order of any sum, so every choice gives bit-identical
+ * results.  Keeps the fastest for later runs and writes it to choice[0..3] when
+ * choice is not NULL (4 int32).  Synchronises.  RCP_EINVAL / RCP_ECUDA. */
 rcp_status rcp_batched_autotune(rcp_batched_t plan, const void* const* X_dev, int32_t* choice);
 
 /* Results of tensor `index` after a run: factors A_n (A_dev[n-1], device,

@@ -280,9 +280,11 @@ class BatchedPlan:
         check(self.lib.rcp_batched_run(self.h, self._ptrs(Xs)), "rcp_batched_run")
 
     def autotune(self, Xs):
-        ch = (ctypes.c_int32 * 2)()
+        """Tune the batched sweeps' shapes on Xs; returns (row CTAs/SM, column CTAs/SM,
+        row-sweep loads in flight, column blocks per item)."""
+        ch = (ctypes.c_int32 * 4)()
         check(self.lib.rcp_batched_autotune(self.h, self._ptrs(Xs), ch), "rcp_batched_autotune")
-        return ch[0], ch[1]
+        return tuple(ch)
 
     def result(self, b):
         A = [torch.empty((self.ranks[b], I), dtype=torch.float64, device=self.device)

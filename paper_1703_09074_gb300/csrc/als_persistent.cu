@@ -296,44 +296,55 @@ __device__ void als_body(const PersArgs& a, int g) {
             const int bq = rest / Lc, aq = rest - bq * Lc;
             const float* Bp = (const float*)a.B + aq + (int64_t)Lc * lc * bq;
             float* Sp = a.S + (int64_t)rest * 32;
-            // two passes of 16 columns; FP32 sums of 8 terms carried into double-word
-            // accumulators (Knuth's TwoSum), so each S entry is accurate to a few u
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-              float shi[16], slo[16];
+            // all 32 columns in one pass: FP32 sums of 8 terms (packed FMAs, two
+            // columns per instruction) carried into double-word accumulators (Knuth's
+            // TwoSum), so each S entry is accurate to a few u; the next 8 values of
+            // the fibre are loaded while the current 8 are multiplied
+            float shi[32], slo[32];
 #pragma unroll
-              for (int r = 0; r < 16; ++r) shi[r] = slo[r] = 0.0f;
-              for (int ic0 = 0; ic0 < lc; ic0 += 8) {
-                float t[16];
+            for (int r = 0; r < 32; ++r) shi[r] = slo[r] = 0.0f;
+            float xc[8], xn[8];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) t[r] = 0.0f;
-                const int ic1 = min(lc, ic0 + 8);
-                for (int ic = ic0; ic < ic1; ++ic) {
-                  const float x = Bp[(int64_t)Lc * ic];
-                  if (want_nb && h == 0) nbs = fma((double)x, (double)x, nbs);
-                  const float4* f = (const float4*)(FcT + ic * 32 + 16 * h);
+            for (int u = 0; u < 8; ++u) xc[u] = u < lc ? Bp[(int64_t)Lc * u] : 0.0f;
+            for (int ic0 = 0; ic0 < lc; ic0 += 8) {
 #pragma unroll
-                  for (int q = 0; q < 4; ++q) {
+              for (int u = 0; u < 8; ++u)
+                xn[u] = ic0 + 8 + u < lc ? Bp[(int64_t)Lc * (ic0 + 8 + u)] : 0.0f;
+              float2 t[16];
+#pragma unroll
+              for (int r = 0; r < 16; ++r) t[r] = make_float2(0.0f, 0.0f);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if (ic0 + u < lc) {
+                  const float x = xc[u];
+                  if (want_nb) nbs = fma((double)x, (double)x, nbs);
+                  const float2 xx = make_float2(x, x);
+                  const float4* f = (const float4*)(FcT + (ic0 + u) * 32);
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) {
                     const float4 v = f[q];
-                    t[4 * q] = fmaf(x, v.x, t[4 * q]);
-                    t[4 * q + 1] = fmaf(x, v.y, t[4 * q + 1]);
-                    t[4 * q + 2] = fmaf(x, v.z, t[4 * q + 2]);
-                    t[4 * q + 3] = fmaf(x, v.w, t[4 * q + 3]);
+                    t[2 * q] = __ffma2_rn(xx, make_float2(v.x, v.y), t[2 * q]);
+                    t[2 * q + 1] = __ffma2_rn(xx, make_float2(v.z, v.w), t[2 * q + 1]);
                   }
-                }
-#pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                  const dwf u2 = dw_two_sum(shi[r], t[r]);
-                  shi[r] = u2.hi;
-                  slo[r] = __fadd_rn(slo[r], u2.lo);
                 }
               }
 #pragma unroll
-              for (int q = 0; q < 4; ++q)
-                ((float4*)(Sp + 16 * h))[q] =
-                    make_float4(shi[4 * q] + slo[4 * q], shi[4 * q + 1] + slo[4 * q + 1],
-                                shi[4 * q + 2] + slo[4 * q + 2], shi[4 * q + 3] + slo[4 * q + 3]);
+              for (int r = 0; r < 16; ++r) {
+                const dwf u0 = dw_two_sum(shi[2 * r], t[r].x);
+                shi[2 * r] = u0.hi;
+                slo[2 * r] = __fadd_rn(slo[2 * r], u0.lo);
+                const dwf u1 = dw_two_sum(shi[2 * r + 1], t[r].y);
+                shi[2 * r + 1] = u1.hi;
+                slo[2 * r + 1] = __fadd_rn(slo[2 * r + 1], u1.lo);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) xc[u] = xn[u];
             }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              ((float4*)Sp)[q] = make_float4(shi[4 * q] + slo[4 * q], shi[4 * q + 1] + slo[4 * q + 1],
+                                             shi[4 * q + 2] + slo[4 * q + 2],
+                                             shi[4 * q + 3] + slo[4 * q + 3]);
           }
           if (want_nb && gi >= 0) {
             for (int o = 16; o > 0; o >>= 1) nbs += __shfl_down_sync(0xffffffffu, nbs, o);
@@ -367,30 +378,53 @@ __device__ void als_body(const PersArgs& a, int g) {
           float mhi[kRowsPerWarp], mlo[kRowsPerWarp];
 #pragma unroll
           for (int k = 0; k < kRowsPerWarp; ++k) mhi[k] = mlo[k] = 0.0f;
-          for (int pp = p0; pp < p1; ++pp) {
-            // digits of pp over the modes other than n and c, the S_c offset and weight
-            int q = pp, off = 0, st_ = 1;
-            float wgt = lane < R ? 1.0f : 0.0f;
-            for (int m = 0; m < N; ++m) {
-              if (m == c) continue;
-              if (m != n0) {
-                const int d = q % a.dims[m];
-                q /= a.dims[m];
-                off += d * st_;
-                if (lane < R) wgt *= (float)Fac[foff[m] + d + a.dims[m] * lane];
-              }
-              st_ *= a.dims[m];
-            }
+          // kPQ multi-indices per step: their S loads are all in flight before the
+          // first is accumulated (the accumulation order is that of pp)
+          constexpr int kPQ = 4;
+          for (int pp = p0; pp < p1; pp += kPQ) {
+            int offv[kPQ];
+            float wv[kPQ];
 #pragma unroll
-            for (int k = 0; k < kRowsPerWarp; ++k) {
-              const int i = warp + kWarps * k;
-              if (i < ln) {
-                const float sv = a.S[(int64_t)(off + i * sn) * 32 + lane];
-                const float pv = __fmul_rn(sv, wgt);
-                const float pe = __fmaf_rn(sv, wgt, -pv);
-                const dwf u2 = dw_two_sum(mhi[k], pv);
-                mhi[k] = u2.hi;
-                mlo[k] = __fadd_rn(mlo[k], __fadd_rn(u2.lo, pe));
+            for (int e = 0; e < kPQ; ++e) {
+              // digits of pp + e over the modes other than n and c, the S_c offset and
+              // weight (weight 0 past the range)
+              int q = pp + e, off = 0, st_ = 1;
+              float wgt = (lane < R && pp + e < p1) ? 1.0f : 0.0f;
+              for (int m = 0; m < N; ++m) {
+                if (m == c) continue;
+                if (m != n0) {
+                  const int d = q % a.dims[m];
+                  q /= a.dims[m];
+                  off += d * st_;
+                  if (lane < R) wgt *= (float)Fac[foff[m] + d + a.dims[m] * lane];
+                }
+                st_ *= a.dims[m];
+              }
+              offv[e] = pp + e < p1 ? off : 0;
+              wv[e] = wgt;
+            }
+            float sv[kPQ][kRowsPerWarp];
+#pragma unroll
+            for (int e = 0; e < kPQ; ++e)
+#pragma unroll
+              for (int k = 0; k < kRowsPerWarp; ++k) {
+                const int i = warp + kWarps * k;
+                sv[e][k] = i < ln ? a.S[(int64_t)(offv[e] + i * sn) * 32 + lane] : 0.0f;
+              }
+#pragma unroll
+            for (int e = 0; e < kPQ; ++e) {
+              if (pp + e < p1) {
+#pragma unroll
+                for (int k = 0; k < kRowsPerWarp; ++k) {
+                  const int i = warp + kWarps * k;
+                  if (i < ln) {
+                    const float pv = __fmul_rn(sv[e][k], wv[e]);
+                    const float pe = __fmaf_rn(sv[e][k], wv[e], -pv);
+                    const dwf u2 = dw_two_sum(mhi[k], pv);
+                    mhi[k] = u2.hi;
+                    mlo[k] = __fadd_rn(mlo[k], __fadd_rn(u2.lo, pe));
+                  }
+                }
               }
             }
           }

@@ -259,7 +259,6 @@ struct rcp_batched_s {
     ModeView view[kMaxN];
     int nsplit[kMaxN];
     int64_t jchunk[kMaxN];
-    int ncolitems[kMaxN];
     int64_t core;
     float* buf[2];
     double *Y, *part, *normpart, *lam, *lam_t, *nu, *rows, *ipp, *nbp, *alspart;
@@ -273,7 +272,10 @@ struct rcp_batched_s {
   BColSweep* colP = nullptr;   // [N][2][count]
   BItem* rowItems = nullptr;   // concatenated per mode
   BItem* colItems = nullptr;
-  std::vector<int> rowItemOff, rowItemCnt, colItemOff, colItemCnt;
+  // column items for each candidate of blocks per item (kColBlocks); colItemOff and
+  // colItemCnt are indexed [candidate][mode]
+  std::vector<int> rowItemOff, rowItemCnt;
+  std::vector<std::vector<int>> colItemOff, colItemCnt;
   BQr* qrP = nullptr;          // [N][3][count]: initial, power-iteration, final
   PersArgs* alsP = nullptr;
   BProj* projP = nullptr;
@@ -290,7 +292,9 @@ struct rcp_batched_s {
   float2* facdw = nullptr;           // its double-word factor scratch, count x N x 32 x 32
   size_t clu_smem = 0;
   int rmax = 1;
-  int row_grid_mult = 4, col_grid_mult = 4;
+  // launch and tile shapes of the batched sweeps, chosen by rcp_batched_autotune:
+  // persistent CTAs per SM, row-sweep loads in flight, column blocks per item
+  int row_grid_mult = 4, col_grid_mult = 4, row_depth = 8, col_blocks_idx = 2;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t gstream = nullptr;    // own stream: the graph is captured and replayed here
@@ -314,6 +318,9 @@ namespace {
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// candidates for the column sweep's blocks of 256 columns per work item
+constexpr int kColBlocks[4] = {1, 2, 4, 8};
 
 void free_batched(rcp_batched_t p) {
   if (!p) return;
@@ -363,23 +370,25 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
     BColSweep* cW = p->colP + ((size_t)n * 2 + 0) * C;
     BColSweep* cT = p->colP + ((size_t)n * 2 + 1) * C;
     const BItem* ri = p->rowItems + p->rowItemOff[n];
-    const BItem* ci = p->colItems + p->colItemOff[n];
+    const int cb = p->col_blocks_idx;
+    const BItem* ci = p->colItems + p->colItemOff[cb][n];
+    const int ncol = p->colItemCnt[cb][n];
     RCPB_TRY(launch_b_row_sweep(rO, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, false,
-                                p->xptrs_dev, rgrid, s));
+                                p->row_depth, p->xptrs_dev, rgrid, s));
     count_launches(1);
     k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (q == 0 ? 2 : 0)) * C);
     RCPB_TRY(cudaGetLastError());
     for (int it = 0; it < q; ++it) {
-      RCPB_TRY(launch_b_col_sweep(cW, ci, p->colItemCnt[n], p->counters + ctr++, p->lmax,
-                                  p->xptrs_dev, cgrid, s));
+      RCPB_TRY(launch_b_col_sweep(cW, ci, ncol, p->counters + ctr++, p->lmax,
+                                  n == 0, p->xptrs_dev, cgrid, s));
       RCPB_TRY(launch_b_row_sweep(rW, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, true,
-                                  p->xptrs_dev, rgrid, s));
+                                  p->row_depth, p->xptrs_dev, rgrid, s));
       count_launches(1);
       k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (it == q - 1 ? 2 : 1)) * C);
       RCPB_TRY(cudaGetLastError());
     }
-    RCPB_TRY(launch_b_col_sweep(cT, ci, p->colItemCnt[n], p->counters + ctr++, p->lmax,
-                                p->xptrs_dev, cgrid, s));
+    RCPB_TRY(launch_b_col_sweep(cT, ci, ncol, p->counters + ctr++, p->lmax,
+                                n == 0, p->xptrs_dev, cgrid, s));
   }
   if (p->net) {
     // learned warm start: canonical inputs, one forward pass, initial factors
@@ -405,8 +414,8 @@ rcp_status build_tables(rcp_batched_t p) {
   std::vector<BItem> rItems, cItems;
   p->rowItemOff.assign(N, 0);
   p->rowItemCnt.assign(N, 0);
-  p->colItemOff.assign(N, 0);
-  p->colItemCnt.assign(N, 0);
+  p->colItemOff.assign(4, std::vector<int>(N, 0));
+  p->colItemCnt.assign(4, std::vector<int>(N, 0));
   // largest tensors first
   std::vector<int> order(C);
   std::iota(order.begin(), order.end(), 0);
@@ -415,7 +424,6 @@ rcp_status build_tables(rcp_batched_t p) {
   });
   for (int n = 0; n < N; ++n) {
     p->rowItemOff[n] = (int)rItems.size();
-    p->colItemOff[n] = (int)cItems.size();
     for (int b : order) {
       auto& t = p->t[b];
       const ModeView v = t.view[n];
@@ -425,7 +433,6 @@ rcp_status build_tables(rcp_batched_t p) {
       const int gx = sweep_row_blocks(v.I);
       for (int by = 0; by < t.nsplit[n]; ++by)
         for (int bx = 0; bx < gx; ++bx) rItems.push_back(BItem{b, bx, by});
-      for (int bx = 0; bx < t.ncolitems[n]; ++bx) cItems.push_back(BItem{b, bx, 0});
       BRowSweep r{};
       r.T = Tin;
       r.v = v;
@@ -448,7 +455,6 @@ rcp_status build_tables(rcp_batched_t p) {
       c.l = l;
       c.Q = t.Y;
       c.W = Wout;
-      c.nb = t.ncolitems[n];
       colP[((size_t)n * 2 + 0) * C + b] = c;
       c.Q = t.Q[n];
       colP[((size_t)n * 2 + 1) * C + b] = c;
@@ -467,8 +473,19 @@ rcp_status build_tables(rcp_batched_t p) {
       }
     }
     p->rowItemCnt[n] = (int)rItems.size() - p->rowItemOff[n];
-    p->colItemCnt[n] = (int)cItems.size() - p->colItemOff[n];
   }
+  // column items: tensor b's item bx covers its 256-column blocks bx, bx + nb, ...
+  // where nb (the item's by) is its item count, kColBlocks[k] blocks per item
+  for (int k = 0; k < 4; ++k)
+    for (int n = 0; n < N; ++n) {
+      p->colItemOff[k][n] = (int)cItems.size();
+      for (int b : order) {
+        const int64_t blocks = (p->t[b].view[n].J + kBColBlock - 1) / kBColBlock;
+        const int nb = (int)std::max<int64_t>(1, (blocks + kColBlocks[k] - 1) / kColBlocks[k]);
+        for (int bx = 0; bx < nb; ++bx) cItems.push_back(BItem{b, bx, nb});
+      }
+      p->colItemCnt[k][n] = (int)cItems.size() - p->colItemOff[k][n];
+    }
   // ALS and recovery
   std::vector<PersArgs> als(C);
   std::vector<BProj> proj(C);
@@ -653,7 +670,6 @@ rcp_status rcp_plan_batched(const rcp_config* cfgs, int32_t count, void* stream,
       int ns = (int)std::min<int64_t>(64, std::max<int64_t>(1, (J + 2047) / 2048));
       t.nsplit[n] = ns;
       t.jchunk[n] = (J + ns - 1) / ns;
-      t.ncolitems[n] = (int)std::max<int64_t>(1, (J + 1023) / 1024);  // 4 blocks of 256 columns
       bufmax = std::max(bufmax, J * l);
       partmax = std::max(partmax, (int64_t)ns * cur[n] * l);
       Imax = std::max(Imax, cur[n]);
@@ -786,36 +802,55 @@ rcp_status rcp_batched_run(rcp_batched_t p, const void* const* X_dev) {
 rcp_status rcp_batched_autotune(rcp_batched_t p, const void* const* X_dev, int32_t* choice) {
   if (!p || !X_dev) return RCP_EINVAL;
   for (int b = 0; b < p->count; ++b) p->xptrs_host[b] = (const float*)X_dev[b];
-  const int cands[] = {1, 2, 4, 8};
   cudaEvent_t a, b2;
   RCPB_TRY(cudaEventCreate(&a));
   RCPB_TRY(cudaEventCreate(&b2));
+  // one timed batch run (after one untimed) at the current shapes
+  auto time_run = [&](float* ms) -> rcp_status {
+    RCPB_TRY(cudaStreamSynchronize(p->stream));
+    RCPB_TRY(cudaStreamSynchronize(p->gstream));
+    if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;
+    RCPB_TRY(cudaEventRecord(a, p->gstream));
+    if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;
+    RCPB_TRY(cudaEventRecord(b2, p->gstream));
+    RCPB_TRY(cudaEventSynchronize(b2));
+    RCPB_TRY(cudaEventElapsedTime(ms, a, b2));
+    return RCP_OK;
+  };
+  // coordinate search, two passes over the four knobs; none of them changes an
+  // operation's order, so every candidate gives the same bits
+  struct Knob {
+    int* field;
+    std::vector<int> vals;
+  };
+  Knob knobs[4] = {{&p->row_grid_mult, {1, 2, 4, 8}},
+                   {&p->col_grid_mult, {1, 2, 4, 8}},
+                   {&p->row_depth, {4, 8}},
+                   {&p->col_blocks_idx, {0, 1, 2, 3}}};
   float best = 1e30f;
-  int br = 4, bc = 4;
-  for (int r : cands) {
-    for (int c : cands) {
-      p->row_grid_mult = r;
-      p->col_grid_mult = c;
-      RCPB_TRY(cudaStreamSynchronize(p->stream));
-      RCPB_TRY(cudaStreamSynchronize(p->gstream));
-      if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;  // warm
-      RCPB_TRY(cudaEventRecord(a, p->gstream));
-      if (enqueue_batched(p, p->gstream) != RCP_OK) return RCP_ECUDA;
-      RCPB_TRY(cudaEventRecord(b2, p->gstream));
-      RCPB_TRY(cudaEventSynchronize(b2));
-      float ms = 0.0f;
-      RCPB_TRY(cudaEventElapsedTime(&ms, a, b2));
-      if (ms < best) {
-        best = ms;
-        br = r;
-        bc = c;
+  rcp_status st = time_run(&best);
+  for (int pass = 0; pass < 2 && st == RCP_OK; ++pass) {
+    for (auto& k : knobs) {
+      const int keep = *k.field;
+      int bestv = keep;
+      for (int v : k.vals) {
+        if (v == keep) continue;
+        *k.field = v;
+        float ms = 0.0f;
+        st = time_run(&ms);
+        if (st != RCP_OK) break;
+        if (ms < best) {
+          best = ms;
+          bestv = v;
+        }
       }
+      *k.field = bestv;
+      if (st != RCP_OK) break;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b2);
-  p->row_grid_mult = br;
-  p->col_grid_mult = bc;
+  if (st != RCP_OK) return st;
   if (p->exec) {  // re-capture with the chosen shapes on the next run
     cudaGraphExecDestroy(p->exec);
     cudaGraphDestroy(p->graph);
@@ -823,8 +858,10 @@ rcp_status rcp_batched_autotune(rcp_batched_t p, const void* const* X_dev, int32
     p->graph = nullptr;
   }
   if (choice) {
-    choice[0] = br;
-    choice[1] = bc;
+    choice[0] = p->row_grid_mult;
+    choice[1] = p->col_grid_mult;
+    choice[2] = p->row_depth;
+    choice[3] = kColBlocks[p->col_blocks_idx];
   }
   return RCP_OK;
 }

@@ -265,8 +265,10 @@ struct BColSweep {  // W = T_(n)^T Q for one tensor, W in the Kolda layout of T_
   int l;
   const double* Q;
   float* W;
-  int nb;
 };
+// Columns per block of the batched column sweep (its CTA width).  A column work
+// item (b, bx, nb) covers tensor b's blocks bx, bx + nb, bx + 2 nb, ...
+constexpr int kBColBlock = 256;
 
 // ---------------------------------------------------------------- launchers
 // Sweeps over the working tensor (sweeps_f64.cu).
@@ -284,10 +286,11 @@ cudaError_t launch_mttkrp_f64(const double* B, ModeView v, int R, const KrDims& 
                               double* part, cudaStream_t s);
 int project_grid(const ModeView& v, int nsm);
 cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitems, unsigned* counter,
-                               int lmax, bool use_w, const float* const* xptrs, int grid,
-                               cudaStream_t s);
+                               int lmax, bool use_w, int depth, const float* const* xptrs,
+                               int grid, cudaStream_t s);
 cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitems, unsigned* counter,
-                               int lmax, const float* const* xptrs, int grid, cudaStream_t s);
+                               int lmax, bool mode1, const float* const* xptrs, int grid,
+                               cudaStream_t s);
 int sweep_rows_per_cta(int64_t I);
 int sweep_row_blocks(int64_t I);
 int sketch_splits(const ModeView& v, int nsm);

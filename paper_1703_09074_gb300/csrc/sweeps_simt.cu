@@ -17,6 +17,7 @@ namespace {
 
 constexpr int kRowTile = 32;      // columns j staged per step of the row sweep
 constexpr int kProjThreads = 256; // columns j per CTA step of the column sweep
+static_assert(kProjThreads == kBColBlock, "batched column items count blocks of kProjThreads");
 constexpr int kProjRows = 32;     // rows of Q staged per step of the column sweep
 constexpr int kBatchQRows = 256;  // the same for the batched column sweep (FP32 Q)
 
@@ -479,28 +480,43 @@ int project_grid(const ModeView& v, int nsm) {
 
 namespace {
 
-// Row sweep of the batched form (FP32, l <= 32).  A block of few rows would leave
-// most of a 256-thread CTA idle with one thread per row, so the threads form G
-// groups of ceil32(rows) threads: one staging round fills G tiles of kRowTile
-// columns, group g multiplies tile g, and the G partial sums of each row meet
-// in shared memory in a fixed order.  The outputs are those of row_sweep_body.
-template <int LMAX, int SRC>
+// acc[c] += x v[c] for c < LB, two columns per packed FP32 FMA (each lane is an
+// fmaf: the sums are those of the scalar loop).  v is 16-byte aligned, LB % 4 == 0.
+template <int LB>
+__device__ __forceinline__ void fma_row2(float2 (&acc)[LB / 2], float x, const float* v) {
+  const float2 xx = make_float2(x, x);
+#pragma unroll
+  for (int c = 0; c < LB; c += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(v + c);
+    acc[c / 2] = __ffma2_rn(xx, make_float2(q.x, q.y), acc[c / 2]);
+    acc[c / 2 + 1] = __ffma2_rn(xx, make_float2(q.z, q.w), acc[c / 2 + 1]);
+  }
+}
+
+constexpr int kRowGroups = 8;  // column groups of the batched row sweep
+
+// Row sweep of the batched form (FP32, l <= LB <= 32).  A block of few rows would
+// leave most of a 256-thread CTA idle with one thread per row, so the threads form
+// G groups of ceil32(rows) threads: one staging round fills G tiles of kRowTile
+// columns, group g multiplies tile g, and the G partial sums of each row meet in
+// shared memory in a fixed order.  The outputs are those of row_sweep_body.  Vs
+// (kRowGroups kRowTile x LB floats), offs, offw and nred are the kernel's shared
+// buffers, so that one launch can run several widths LB.
+template <int LB, int SRC, int U>
 __device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__ T, ModeView v,
                                                        int64_t rows_per_cta, int l,
                                                        uint64_t seed, uint32_t sid,
                                                        const float* __restrict__ W,
                                                        int64_t jchunk, double* __restrict__ part,
                                                        double* __restrict__ normpart, int bx,
-                                                       int by, int gx) {
+                                                       int by, int gx, float* vs, int64_t* offs,
+                                                       int64_t* offw, double* nred) {
   const bool NORM = normpart != nullptr;  // mode 1 of the sketch also sums X^2
-  constexpr int kMaxG = 8;
-  __shared__ float Vs[kMaxG * kRowTile][LMAX];
-  __shared__ int64_t offs[kMaxG * kRowTile];
-  __shared__ int64_t offw[kMaxG * kRowTile];
+  float(*Vs)[LB] = reinterpret_cast<float(*)[LB]>(vs);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int rpc = (int)rows_per_cta;
   const int rpc32 = (rpc + 31) & ~31;
-  const int G = max(1, min(kMaxG, nthr / rpc32));
+  const int G = max(1, min(kRowGroups, nthr / rpc32));
   const int grp = tid / rpc32, r = tid - grp * rpc32;
   const int64_t i = (int64_t)bx * rows_per_cta + r;
   const bool row_ok = grp < G && r < rpc && i < v.I;
@@ -508,11 +524,11 @@ __device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__
   const int64_t j1 = min(v.J, j0 + jchunk);
   const int TW = G * kRowTile;  // columns per staging round
 
-  float acc[LMAX];
+  float2 acc[LB / 2];
 #pragma unroll
-  for (int c = 0; c < LMAX; ++c) acc[c] = 0.0f;
+  for (int c = 0; c < LB / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
   double nrm = 0.0;
-  for (int k = tid; k < kMaxG * kRowTile * LMAX; k += nthr) (&Vs[0][0])[k] = 0.0f;
+  for (int k = tid; k < kRowGroups * kRowTile * LB; k += nthr) vs[k] = 0.0f;
   __syncthreads();
 
   for (int64_t jt = j0; jt < j1; jt += TW) {
@@ -548,7 +564,6 @@ __device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__
     if (row_ok) {
       // group grp's tile: columns grp kRowTile .. of the round; U loads in flight
       const int c0 = grp * kRowTile, c1 = min(nj, c0 + kRowTile);
-      constexpr int U = 8;
       float tn = 0.0f;
       int jj = c0;
       for (; jj + U <= c1; jj += U) {
@@ -558,36 +573,39 @@ __device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (NORM) tn = fmaf(xs[u], xs[u], tn);
-#pragma unroll
-          for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(xs[u], Vs[jj + u][c], acc[c]);
+          fma_row2<LB>(acc, xs[u], Vs[jj + u]);
         }
       }
       for (; jj < c1; ++jj) {
         const float x = __ldg(T + offs[jj] + v.L * i);
         if (NORM) tn = fmaf(x, x, tn);
-#pragma unroll
-        for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(x, Vs[jj][c], acc[c]);
+        fma_row2<LB>(acc, x, Vs[jj]);
       }
       if (NORM) nrm += (double)tn;
     }
     __syncthreads();
   }
-  // groups 1..G-1 hand their sums to group 0 through Vs (G rpc32 LMAX <= its size)
-  float* red = &Vs[0][0];
+  // groups 1..G-1 hand their sums to group 0 through Vs (G rpc32 LB <= its size)
+  float2* red = reinterpret_cast<float2*>(vs);
   if (grp > 0 && grp < G)
 #pragma unroll
-    for (int c = 0; c < LMAX; ++c) red[(grp * rpc32 + r) * LMAX + c] = acc[c];
+    for (int c = 0; c < LB / 2; ++c) red[(grp * rpc32 + r) * (LB / 2) + c] = acc[c];
   __syncthreads();
   if (grp == 0 && row_ok) {
     for (int g2 = 1; g2 < G; ++g2)
 #pragma unroll
-      for (int c = 0; c < LMAX; ++c) acc[c] += red[(g2 * rpc32 + r) * LMAX + c];
+      for (int c = 0; c < LB / 2; ++c) {
+        const float2 o = red[(g2 * rpc32 + r) * (LB / 2) + c];
+        acc[c].x += o.x;
+        acc[c].y += o.y;
+      }
 #pragma unroll
-    for (int c = 0; c < LMAX; ++c)
-      if (c < l) part[((int64_t)by * l + c) * v.I + i] = (double)acc[c];
+    for (int c = 0; c < LB / 2; ++c) {
+      if (2 * c < l) part[((int64_t)by * l + 2 * c) * v.I + i] = (double)acc[c].x;
+      if (2 * c + 1 < l) part[((int64_t)by * l + 2 * c + 1) * v.I + i] = (double)acc[c].y;
+    }
   }
   if (NORM) {
-    __shared__ double nred[256];
     nred[tid] = nrm;
     __syncthreads();
     for (int s2 = 128; s2 > 0; s2 >>= 1) {
@@ -597,11 +615,17 @@ __device__ __forceinline__ void row_sweep_body_grouped(const float* __restrict__
     if (tid == 0) normpart[(int64_t)by * gx + bx] = nred[0];
   }
 }
-template <int LMAX, int SRC>
-__global__ void __launch_bounds__(256)
+// U: loads in flight per thread (a tile-shape choice of the autotuner; the FMA
+// order, and so every sum, is the same for each U).
+template <int LMAX, int SRC, int U>
+__global__ void __launch_bounds__(256, 3)
 k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
               unsigned* counter, const float* const* __restrict__ xptrs) {
   __shared__ int item_sh;
+  __shared__ __align__(16) float vs[kRowGroups * kRowTile * LMAX];
+  __shared__ int64_t offs[kRowGroups * kRowTile];
+  __shared__ int64_t offw[kRowGroups * kRowTile];
+  __shared__ double nred[256];
   for (;;) {
     if (threadIdx.x == 0) item_sh = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -611,63 +635,109 @@ k_b_row_sweep(const BRowSweep* __restrict__ P, const BItem* __restrict__ items, 
     const BItem w = items[it];
     const BRowSweep p = P[w.b];
     const float* T = p.T ? p.T : xptrs[w.b];  // mode 1 reads the caller's tensor
-    row_sweep_body_grouped<LMAX, SRC>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid, p.W, p.jchunk,
-                                      p.part, p.normpart, w.bx, w.by, p.gx);
+    // each tensor runs at its own padded width (FMAs on padding are wasted work)
+    if (LMAX > 16 && p.l <= 16)
+      row_sweep_body_grouped<16, SRC, U>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid, p.W,
+                                         p.jchunk, p.part, p.normpart, w.bx, w.by, p.gx, vs,
+                                         offs, offw, nred);
+    else if (LMAX > 24 && p.l <= 24)
+      row_sweep_body_grouped<24, SRC, U>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid, p.W,
+                                         p.jchunk, p.part, p.normpart, w.bx, w.by, p.gx, vs,
+                                         offs, offw, nred);
+    else
+      row_sweep_body_grouped<LMAX, SRC, U>(T, p.v, p.rows_per_cta, p.l, p.seed, p.sid, p.W,
+                                           p.jchunk, p.part, p.normpart, w.bx, w.by, p.gx, vs,
+                                           offs, offw, nred);
     __syncthreads();
   }
 }
 
 // Column sweep over the mode-1 unfolding of an FP32 tensor (L = 1: column j is
 // the contiguous fibre X[:, j]): W[j, c] = sum_i X[i, j] Q[i, c] for the
-// kProjThreads columns of block jb.  Rows are taken 32 at a time: warp w loads
-// the 32-row segments of columns w, w + 8, ... (128 contiguous bytes per load
-// instruction) into a padded shared tile, and thread t then reads column t of
-// the tile (conflict-free) against the staged rows of Q.
-template <int LMAX>
+// kProjThreads columns of block jb.  Q is staged in shared memory as FP32 rows
+// of LB, once per call when I <= kBatchQRows, else kBatchQRows rows at a time.
+// Rows of X are taken 16 at a time: each warp load covers the 16-row segments
+// (64 contiguous bytes) of two columns; a thread holds the next chunk's 16
+// values in registers while the current chunk, stored in a padded shared tile,
+// is multiplied: thread t reads column t of the tile against the staged rows of
+// Q, two columns of Q per packed FMA.  Each W[j, c] is one FMA chain over
+// i = 0, 1, ...  sm holds kBatchQRows x LB floats of Q and the 16 x
+// (kProjThreads + 1) tile.
+constexpr int kFibRows = 16;
+template <int LB>
 __device__ __forceinline__ void col_sweep_fibres(const float* __restrict__ T, ModeView v, int l,
                                                  const double* __restrict__ Q,
-                                                 float* __restrict__ W, int bx, int nb) {
-  extern __shared__ double sm[];
-  constexpr int NT = kProjThreads, TP = kProjThreads + 1;
-  float* Qs = (float*)sm;          // 32 x LMAX
-  float* Xt = Qs + 32 * LMAX;      // 32 x TP
+                                                 float* __restrict__ W, int bx, int nb,
+                                                 float* sm) {
+  constexpr int NT = kProjThreads, TP = kProjThreads + 1, NW = NT / 32;
+  constexpr int RC = kFibRows, NU = NT * RC / NT;  // values staged per thread per chunk
+  float* Qs = sm;                     // kBatchQRows x LB
+  float* Xt = Qs + kBatchQRows * LB;  // RC x TP
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int xr_row = lane & (RC - 1), xr_col = 2 * warp + (lane >> 4);  // + 2 NW u
+  const int I = (int)v.I;
+  // rows [p0, p0 + np) of Q into Qs (columns l..LB-1 zero)
+  auto stage_q = [&](int p0, int np) {
+    for (int k = tid; k < np * LB; k += NT) {
+      const int c = k / np, ii = k - c * np;
+      Qs[ii * LB + c] = c < l ? (float)Q[(p0 + ii) + (int64_t)I * c] : 0.0f;
+    }
+  };
+  const bool qall = I <= kBatchQRows;
+  if (qall) {
+    __syncthreads();
+    stage_q(0, I);
+  }
   for (int64_t jb = bx; jb * NT < v.J; jb += nb) {
     const int64_t j0 = jb * NT, j = j0 + tid;
-    float acc[LMAX];
+    float2 acc[LB / 2];
 #pragma unroll
-    for (int c = 0; c < LMAX; ++c) acc[c] = 0.0f;
-    for (int64_t i0 = 0; i0 < v.I; i0 += 32) {
-      const int ni = (int)min((int64_t)32, v.I - i0);
-      __syncthreads();
-      for (int k = tid; k < 32 * LMAX; k += NT) {
-        const int ii = k / LMAX, c = k - ii * LMAX;
-        Qs[k] = (ii < ni && c < l) ? (float)Q[(i0 + ii) + v.I * c] : 0.0f;
-      }
-#pragma unroll 4
-      for (int jj = warp; jj < NT; jj += NT / 32) {
-        const int64_t col = j0 + jj;
-        Xt[lane * TP + jj] = (col < v.J && lane < ni) ? __ldg(T + col * v.I + i0 + lane) : 0.0f;
-      }
-      __syncthreads();
-      for (int ii = 0; ii < ni; ++ii) {
-        const float x = Xt[ii * TP + tid];
+    for (int c = 0; c < LB / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
+    auto load_x = [&](int i0, int iend, float (&xr)[NU]) {
+      const bool row_ok = i0 + xr_row < iend;
 #pragma unroll
-        for (int c = 0; c < LMAX; ++c) acc[c] = fmaf(x, Qs[ii * LMAX + c], acc[c]);
+      for (int u = 0; u < NU; ++u) {
+        const int64_t col = j0 + xr_col + 2 * NW * u;
+        xr[u] = (col < v.J && row_ok) ? __ldg(T + col * v.I + i0 + xr_row) : 0.0f;
+      }
+    };
+    for (int p0 = 0; p0 < I; p0 += kBatchQRows) {
+      const int np = min(kBatchQRows, I - p0);
+      if (!qall) {
+        __syncthreads();
+        stage_q(p0, np);
+      }
+      float xr[NU];
+      load_x(p0, p0 + np, xr);
+      for (int i0 = 0; i0 < np; i0 += RC) {
+        const int ni = min(RC, np - i0);
+        __syncthreads();  // the previous chunk's tile reads (and Qs) are done
+#pragma unroll
+        for (int u = 0; u < NU; ++u) Xt[xr_row * TP + xr_col + 2 * NW * u] = xr[u];
+        __syncthreads();
+        if (i0 + RC < np) load_x(p0 + i0 + RC, p0 + np, xr);  // next chunk in flight
+        const float* qrow = Qs + (qall ? p0 + i0 : i0) * LB;
+        for (int ii = 0; ii < ni; ++ii) fma_row2<LB>(acc, Xt[ii * TP + tid], qrow + ii * LB);
       }
     }
     if (j < v.J) {
 #pragma unroll
-      for (int c = 0; c < LMAX; ++c)
-        if (c < l) W[c + (int64_t)l * j] = acc[c];
+      for (int c = 0; c < LB / 2; ++c) {
+        if (2 * c < l) W[2 * c + (int64_t)l * j] = acc[c].x;
+        if (2 * c + 1 < l) W[2 * c + 1 + (int64_t)l * j] = acc[c].y;
+      }
     }
   }
 }
 
-template <int LMAX>
-__global__ void __launch_bounds__(kProjThreads)
+// One launch covers one mode of every tensor.  Mode 1 (FIB) reads contiguous fibres,
+// each tensor at its own padded width; the other modes take the staged-Q column
+// body (any L).
+template <int LMAX, bool FIB>
+__global__ void __launch_bounds__(kProjThreads, FIB ? 2 : 3)
 k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, int nitems,
               unsigned* counter, const float* const* __restrict__ xptrs) {
+  extern __shared__ __align__(16) double b_col_sm[];
   __shared__ int item_sh;
   for (;;) {
     if (threadIdx.x == 0) item_sh = (int)atomicAdd(counter, 1u);
@@ -677,13 +747,19 @@ k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, 
     if (it >= nitems) break;
     const BItem w = items[it];
     const BColSweep p = P[w.b];
-    if (p.v.L == 1) {
-      // mode 1: columns are contiguous fibres, staged as coalesced tiles
-      col_sweep_fibres<LMAX>(p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, w.bx, p.nb);
+    const float* T = p.T ? p.T : xptrs[w.b];
+    float* sm = reinterpret_cast<float*>(b_col_sm);
+    if (FIB) {
+      if (LMAX > 16 && p.l <= 16)
+        col_sweep_fibres<16>(T, p.v, p.l, p.Q, p.W, w.bx, w.by, sm);
+      else if (LMAX > 24 && p.l <= 24)
+        col_sweep_fibres<24>(T, p.v, p.l, p.Q, p.W, w.bx, w.by, sm);
+      else
+        col_sweep_fibres<LMAX>(T, p.v, p.l, p.Q, p.W, w.bx, w.by, sm);
     } else {
       // Q staged 256 rows at a time: once per column block for I <= 256
       col_sweep_body<LMAX, float, float, false, kProjThreads, kBatchQRows>(
-          p.T ? p.T : xptrs[w.b], p.v, p.l, p.Q, p.W, nullptr, w.bx, p.nb);
+          T, p.v, p.l, p.Q, p.W, nullptr, w.bx, w.by);
     }
     __syncthreads();
   }
@@ -692,45 +768,64 @@ k_b_col_sweep(const BColSweep* __restrict__ P, const BItem* __restrict__ items, 
 }  // namespace
 
 cudaError_t launch_b_row_sweep(const BRowSweep* P, const BItem* items, int nitems, unsigned* counter,
-                               int lmax, bool use_w, const float* const* xptrs, int grid,
-                               cudaStream_t s) {
+                               int lmax, bool use_w, int depth, const float* const* xptrs,
+                               int grid, cudaStream_t s) {
   count_launches(1);
   // the batch's widths l <= 32 in buckets of 16, 24 and 32 columns (each thread
-  // multiplies every staged column, so padding costs FMAs)
+  // multiplies every staged column, so padding costs FMAs); depth 4 or 8 loads
+  // in flight per thread
   const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
+  if (b == 0 || (depth != 4 && depth != 8)) return cudaErrorInvalidValue;
+#define RCP_B_ROW(BB, SRC, U) k_b_row_sweep<BB, SRC, U><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs)
+#define RCP_B_ROW_U(BB, SRC)      \
+  if (depth == 4) RCP_B_ROW(BB, SRC, 4); \
+  else RCP_B_ROW(BB, SRC, 8);
   if (use_w) {
-    if (b == 16) k_b_row_sweep<16, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else if (b == 24) k_b_row_sweep<24, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else if (b == 32) k_b_row_sweep<32, kSrcW><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else return cudaErrorInvalidValue;
+    if (b == 16) { RCP_B_ROW_U(16, kSrcW) }
+    else if (b == 24) { RCP_B_ROW_U(24, kSrcW) }
+    else { RCP_B_ROW_U(32, kSrcW) }
   } else {
-    if (b == 16) k_b_row_sweep<16, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else if (b == 24) k_b_row_sweep<24, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else if (b == 32) k_b_row_sweep<32, kSrcOmega><<<grid, 256, 0, s>>>(P, items, nitems, counter, xptrs);
-    else return cudaErrorInvalidValue;
+    if (b == 16) { RCP_B_ROW_U(16, kSrcOmega) }
+    else if (b == 24) { RCP_B_ROW_U(24, kSrcOmega) }
+    else { RCP_B_ROW_U(32, kSrcOmega) }
   }
+#undef RCP_B_ROW_U
+#undef RCP_B_ROW
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_col_sweep(const BColSweep* P, const BItem* items, int nitems, unsigned* counter,
-                               int lmax, const float* const* xptrs, int grid, cudaStream_t s) {
+                               int lmax, bool mode1, const float* const* xptrs, int grid,
+                               cudaStream_t s) {
   count_launches(1);
   const int b = lmax <= 16 ? 16 : lmax <= 24 ? 24 : lmax <= 32 ? 32 : 0;
-  // dynamic shared memory: the staged rows of Q (kBatchQRows x b), or for mode 1
-  // 32 rows of Q and a 32 x (kProjThreads + 1) tile of X, whichever is larger
+  // dynamic shared memory: the staged rows of Q (kBatchQRows x b) and, for the
+  // fibre path, a kFibRows x (kProjThreads + 1) tile of X
   auto smem_for = [](int bb) {
-    return std::max((size_t)kBatchQRows * bb, (size_t)32 * bb + (size_t)32 * (kProjThreads + 1)) *
-           sizeof(float);
+    return ((size_t)kBatchQRows * bb + (size_t)kFibRows * (kProjThreads + 1)) * sizeof(float);
   };
-  if (b == 16) {
-    k_b_col_sweep<16><<<grid, kProjThreads, smem_for(16), s>>>(P, items, nitems, counter, xptrs);
-  } else if (b == 24) {
-    k_b_col_sweep<24><<<grid, kProjThreads, smem_for(24), s>>>(P, items, nitems, counter, xptrs);
-  } else if (b == 32) {
-    k_b_col_sweep<32><<<grid, kProjThreads, smem_for(32), s>>>(P, items, nitems, counter, xptrs);
-  } else {
-    return cudaErrorInvalidValue;
-  }
+  cudaError_t e = cudaSuccess;
+#define RCP_B_COL(BB)                                                                          \
+  do {                                                                                         \
+    const size_t sm = smem_for(BB);                                                            \
+    if (mode1) {                                                                               \
+      e = cudaFuncSetAttribute(k_b_col_sweep<BB, true>,                                        \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);          \
+      if (e == cudaSuccess)                                                                    \
+        k_b_col_sweep<BB, true><<<grid, kProjThreads, sm, s>>>(P, items, nitems, counter, xptrs); \
+    } else {                                                                                   \
+      e = cudaFuncSetAttribute(k_b_col_sweep<BB, false>,                                       \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);          \
+      if (e == cudaSuccess)                                                                    \
+        k_b_col_sweep<BB, false><<<grid, kProjThreads, sm, s>>>(P, items, nitems, counter, xptrs); \
+    }                                                                                          \
+  } while (0)
+  if (b == 16) RCP_B_COL(16);
+  else if (b == 24) RCP_B_COL(24);
+  else if (b == 32) RCP_B_COL(32);
+  else return cudaErrorInvalidValue;
+#undef RCP_B_COL
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
