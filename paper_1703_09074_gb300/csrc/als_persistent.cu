@@ -356,6 +356,9 @@ __device__ void als_body(const PersArgs& a, int g) {
               a.nbp[gi] = sb;
             }
           }
+          // the row owners write no part of S_c: they invert V (which needs only the
+          // Grams) while the others form it
+          if (gw0 > 0 && g < ln) prepare_solve(n0);
           // every CTA's part of S_c is written before any CTA reduces it
           if (!phase_sync(a, G, epoch)) { ok = false; break; }
         }
@@ -608,7 +611,7 @@ __device__ void als_body(const PersArgs& a, int g) {
         }
       }
       }
-      if (gw0 > 0 && g < ln) prepare_solve(n0);
+      if (gw0 > 0 && g < ln && !(kMixed && a.S != nullptr && n0 <= 1)) prepare_solve(n0);
       if (!phase_sync(a, G, epoch)) { ok = false; break; }
 
       // ---- phase B: rows owned by this CTA (rows i = g, g + G, ...)

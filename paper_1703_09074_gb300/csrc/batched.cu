@@ -6,14 +6,16 @@
 //     counter, largest tensor first (sweeps_simt.cu, FP32 CUDA cores: with
 //     l <= 24 these sweeps have <= 12 FLOP per byte and stay memory-bound);
 //   - sketch orthonormalisation: one CTA per tensor reduces the split
-//     partials and runs CholeskyQR2 (shifted CholeskyQR3 fallback) in FP64;
-//   - ALS: one CTA per tensor runs every sweep of its own problem
-//     (als_persistent.cu, FP32 MTTKRP, FP64-refined Gram solves);
+//     partials (double-word FP32 sums of FP32 values) and runs CholeskyQR2: the
+//     first round in FP32 from a shared-memory copy of Y (FP64 factorisation),
+//     the second in FP64 (shifted CholeskyQR3 fallback in FP64);
+//   - ALS: one single-CTA cluster per tensor, the body of the one-cluster
+//     kernel (als_cluster.cu: core in shared memory, double-word Gram inverse);
 //   - recovery: one CTA per (tensor, mode), then lambda per tensor.
 // The whole sequence is captured once into a CUDA graph and replayed; the
 // input pointers reach the graph through a pinned host array copied by the
-// graph itself.  The launch shapes (CTAs per SM of the persistent sweeps and
-// columns per work item) are chosen by timing candidates on the batch.
+// graph itself.  The launch and tile shapes of the sweeps (CTAs per SM, loads
+// in flight, columns per work item) are chosen by timing candidates on the batch.
 #include <math.h>
 #include <string.h>
 
@@ -24,6 +26,7 @@
 
 #include <stddef.h>
 
+#include "dw_arith.cuh"
 #include "mlp_internal.cuh"
 #include "small_la.cuh"
 
@@ -58,14 +61,22 @@ struct BProj {
 namespace {
 
 constexpr int kQrThreads = 256;
+constexpr int kQrStageBytes = 48 * 1024;  // largest FP32 copy of Y staged in shared memory
 
-// CTA per tensor: reduce partials, then CholeskyQR2 (+ a third round after a
-// shifted first round), all in FP64.  Y is I x l column-major in global memory.
-// The factorisation of each round is chol_elim: the elimination on [G | I]
-// that yields R^{-1} with the pivot chain on warp 0 (no serial back
-// substitution).
-__global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) {
+// CTA per tensor (l <= 32): reduce the split partials, then CholeskyQR2 (+ a third
+// round after a shifted first round).  Y is I x l column-major in global memory
+// (FP64).  The partials are FP32 values: their sums are double-word FP32 (TwoSum),
+// exact to far below FP32 rounding.  The first round, when Y fits the stage
+// (I l floats <= stage_floats), forms the Gram and Y R^{-1} in FP32 from a copy
+// of Y in shared memory: it only conditions Y (the span is kept up to FP32
+// rounding of the product), and the second round, in FP64, orthonormalises.
+// The factorisation of each round is chol_elim in FP64: the elimination on
+// [G | I] that yields R^{-1} with the pivot chain on warp 0.  Gram entries are
+// one warp each: lanes split the rows, then a butterfly.
+__global__ void __launch_bounds__(kQrThreads, 2) k_b_qr(const BQr* __restrict__ P, int stage_floats) {
+  extern __shared__ float Ys[];           // I x l FP32 copy of Y (first round)
   __shared__ double S[kMaxL][kMaxL + 1];  // Gram / Schur complement; then R^{-1} (upper)
+  __shared__ float Sf[32][33];            // FP32 copy of R^{-1} (first round)
   __shared__ double tdiag[kMaxL];
   __shared__ double rowb[2][kMaxL];
   __shared__ double tb[2][kMaxL];
@@ -76,10 +87,16 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
   const int64_t I = p.I;
   const int l = p.l;
   const int64_t n = I * l;
+  const bool f32r = n <= stage_floats;
   for (int64_t e = tid; e < n; e += kQrThreads) {
-    double s = 0.0;
-    for (int k = 0; k < p.nsplit; ++k) s += p.part[(int64_t)k * n + e];
-    p.Y[e] = s;
+    float hi = 0.0f, lo = 0.0f;
+    for (int k = 0; k < p.nsplit; ++k) {
+      const dwf t = dw_two_sum(hi, (float)p.part[(int64_t)k * n + e]);
+      hi = t.hi;
+      lo = __fadd_rn(lo, t.lo);
+    }
+    p.Y[e] = (double)hi + (double)lo;
+    if (f32r) Ys[e] = hi + lo;
   }
   if (p.nnorm > 0) {
     double s = 0.0;
@@ -94,26 +111,47 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
     }
   }
   __syncthreads();
-  // S = Y^T Y in the upper triangle (plus shift on the diagonal), zero below
-  auto gram = [&](double shift) {
-    for (int q = tid; q < l * (l + 1) / 2; q += kQrThreads) {
+  // S = Y^T Y in the upper triangle (plus shift on the diagonal), zero below; from
+  // the FP32 copy (f32) or from Y in FP64
+  auto gram = [&](bool f32, double shift) {
+    for (int q = warp; q < l * (l + 1) / 2; q += kQrThreads / 32) {
       int c = 0, rem = q;
       while (rem > c) {
         rem -= c + 1;
         ++c;
       }
       const int r = rem;
-      const double* y1 = p.Y + I * r;
-      const double* y2 = p.Y + I * c;
-      double s0 = 0.0, s1 = 0.0;
-      int64_t i = 0;
-      for (; i + 1 < I; i += 2) {
-        s0 = fma(y1[i], y2[i], s0);
-        s1 = fma(y1[i + 1], y2[i + 1], s1);
+      double s;
+      if (f32) {
+        const float* y1 = Ys + I * r;
+        const float* y2 = Ys + I * c;
+        float s0 = 0.0f, s1 = 0.0f;
+        int64_t i = lane;
+        for (; i + 32 < I; i += 64) {
+          s0 = fmaf(y1[i], y2[i], s0);
+          s1 = fmaf(y1[i + 32], y2[i + 32], s1);
+        }
+        if (i < I) s0 = fmaf(y1[i], y2[i], s0);
+        float t = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        s = (double)t;
+      } else {
+        const double* y1 = p.Y + I * r;
+        const double* y2 = p.Y + I * c;
+        double s0 = 0.0, s1 = 0.0;
+        int64_t i = lane;
+        for (; i + 32 < I; i += 64) {
+          s0 = fma(y1[i], y2[i], s0);
+          s1 = fma(y1[i + 32], y2[i + 32], s1);
+        }
+        if (i < I) s0 = fma(y1[i], y2[i], s0);
+        s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       }
-      if (i < I) s0 = fma(y1[i], y2[i], s0);
-      S[r][c] = (s0 + s1) + (r == c ? shift : 0.0);
-      if (r != c) S[c][r] = 0.0;
+      if (lane == 0) {
+        S[r][c] = s + (r == c ? shift : 0.0);
+        if (r != c) S[c][r] = 0.0;
+      }
     }
     __syncthreads();
   };
@@ -121,7 +159,8 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
   for (int round = 0; round < 3; ++round) {
     __syncthreads();
     if (round == 2 && !flag[0]) break;
-    gram(0.0);
+    bool r32 = round == 0 && f32r;
+    gram(r32, 0.0);
     // trace and finiteness of the diagonal (warp 0), the shifted-CholeskyQR3 shift
     if (warp == 0) {
       const double d = lane < l ? S[lane][lane] : 0.0;
@@ -142,9 +181,10 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
     const double shift = red[0];
     bool ok = chol_elim<double>(S, tdiag, rowb, tb, l, round == 0 ? shift : 0.0, &fail_sh);
     if (!ok && round == 0) {
-      // shifted CholeskyQR3: factor G + s I, then one more plain round
+      // shifted CholeskyQR3 in FP64: factor G + s I, then one more plain round
       __syncthreads();
-      gram(shift);
+      r32 = false;
+      gram(false, shift);
       ok = chol_elim<double>(S, tdiag, rowb, tb, l, 0.0, &fail_sh);
       if (tid == 0) {
         flag[0] = 1;
@@ -162,16 +202,48 @@ __global__ void __launch_bounds__(kQrThreads) k_b_qr(const BQr* __restrict__ P) 
       else if (k == c) S[k][k] = tdiag[k];
     }
     __syncthreads();
-    // Y <- Y R^{-1}, one thread per row, in place
-    for (int64_t i = tid; i < I; i += kQrThreads) {
-      double y[kMaxL];
-      for (int k = 0; k < l; ++k) y[k] = p.Y[i + I * k];
-      for (int c = l - 1; c >= 0; --c) {
-        double s = 0.0;
-        for (int k = 0; k <= c; ++k) s = fma(y[k], S[k][c], s);
-        y[c] = s;  // y[k] for k < c still holds the input row
+    if (r32) {
+      for (int q = tid; q < l * l; q += kQrThreads) {
+        const int k = q / l, c = q - k * l;
+        Sf[k][c] = k <= c ? (float)S[k][c] : 0.0f;
       }
-      for (int c = 0; c < l; ++c) p.Y[i + I * c] = y[c];
+      __syncthreads();
+    }
+    // Y <- Y R^{-1}, one thread per row, the row in registers (l <= 32)
+    for (int64_t i = tid; i < I; i += kQrThreads) {
+      if (r32) {
+        float y[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) y[k] = k < l ? Ys[i + I * k] : 0.0f;
+#pragma unroll
+        for (int c = 31; c >= 0; --c) {
+          if (c < l) {
+            float sc = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= c; ++k) sc = fmaf(y[k], Sf[k][c], sc);
+            y[c] = sc;  // y[k] for k < c still holds the input row
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < l) p.Y[i + I * c] = (double)y[c];
+      } else {
+        double y[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) y[k] = k < l ? p.Y[i + I * k] : 0.0;
+#pragma unroll
+        for (int c = 31; c >= 0; --c) {
+          if (c < l) {
+            double sc = 0.0;
+#pragma unroll
+            for (int k = 0; k <= c; ++k) sc = fma(y[k], S[k][c], sc);
+            y[c] = sc;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < l) p.Y[i + I * c] = y[c];
+      }
     }
   }
   __syncthreads();
@@ -295,6 +367,8 @@ struct rcp_batched_s {
   // launch and tile shapes of the batched sweeps, chosen by rcp_batched_autotune:
   // persistent CTAs per SM, row-sweep loads in flight, column blocks per item
   int row_grid_mult = 4, col_grid_mult = 4, row_depth = 8, col_blocks_idx = 2;
+  // dynamic shared memory of k_b_qr: the largest I_n l_n FP32 copy of Y, capped
+  size_t qr_smem = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t gstream = nullptr;    // own stream: the graph is captured and replayed here
@@ -376,7 +450,8 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
     RCPB_TRY(launch_b_row_sweep(rO, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, false,
                                 p->row_depth, p->xptrs_dev, rgrid, s));
     count_launches(1);
-    k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (q == 0 ? 2 : 0)) * C);
+    k_b_qr<<<C, kQrThreads, p->qr_smem, s>>>(p->qrP + ((size_t)n * 3 + (q == 0 ? 2 : 0)) * C,
+                                              (int)(p->qr_smem / sizeof(float)));
     RCPB_TRY(cudaGetLastError());
     for (int it = 0; it < q; ++it) {
       RCPB_TRY(launch_b_col_sweep(cW, ci, ncol, p->counters + ctr++, p->lmax,
@@ -384,7 +459,8 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
       RCPB_TRY(launch_b_row_sweep(rW, ri, p->rowItemCnt[n], p->counters + ctr++, p->lmax, true,
                                   p->row_depth, p->xptrs_dev, rgrid, s));
       count_launches(1);
-      k_b_qr<<<C, kQrThreads, 0, s>>>(p->qrP + ((size_t)n * 3 + (it == q - 1 ? 2 : 1)) * C);
+      k_b_qr<<<C, kQrThreads, p->qr_smem, s>>>(
+          p->qrP + ((size_t)n * 3 + (it == q - 1 ? 2 : 1)) * C, (int)(p->qr_smem / sizeof(float)));
       RCPB_TRY(cudaGetLastError());
     }
     RCPB_TRY(launch_b_col_sweep(cT, ci, ncol, p->counters + ctr++, p->lmax,
@@ -542,6 +618,17 @@ rcp_status build_tables(rcp_batched_t p) {
       !up(&p->colItems, cItems) || !up(&p->alsP, als) || !up(&p->projP, proj) || !up(&p->stPtrs, sts))
     return RCP_ENOMEM;
   p->als_host = als;
+  // the first QR round's FP32 copy of Y: the largest I_n l_n of the batch, capped
+  {
+    size_t mx = 0;
+    for (int b = 0; b < C; ++b)
+      for (int n = 0; n < N; ++n)
+        mx = std::max(mx, (size_t)p->t[b].view[n].I * p->t[b].l[n] * sizeof(float));
+    p->qr_smem = std::min(mx, (size_t)kQrStageBytes);
+    if (cudaFuncSetAttribute(k_b_qr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)p->qr_smem) != cudaSuccess)
+      return RCP_ECUDA;
+  }
   // the one-cluster ALS arguments (clusters of one CTA); the learned start sets the
   // user_init word of the PersArgs table, which these arguments point at
   {
