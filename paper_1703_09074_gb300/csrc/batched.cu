@@ -482,6 +482,26 @@ rcp_status enqueue_batched(rcp_batched_t p, cudaStream_t s) {
   return RCP_OK;
 }
 
+// Block order of a one-CTA-per-tensor launch (block s serves tensor order[s]): the
+// kernel lasts as long as its busiest SM.  With one CTA per SM, largest work first.
+// With two, blocks s and s + nsm usually share an SM: the largest tensors take the
+// SMs that hold one block, and the rest pair a large tensor with a small one.
+std::vector<int> block_order(const std::vector<double>& work, int nsm, int per_sm) {
+  const int C = (int)work.size();
+  std::vector<int> byw(C);
+  std::iota(byw.begin(), byw.end(), 0);
+  std::stable_sort(byw.begin(), byw.end(), [&](int a, int b) { return work[a] > work[b]; });
+  if (per_sm < 2 || C <= nsm || C > 2 * nsm) return byw;
+  const int pairs = C - nsm, singles = nsm - pairs;
+  std::vector<int> order(C);
+  for (int k = 0; k < singles; ++k) order[pairs + k] = byw[k];
+  for (int k = 0; k < pairs; ++k) {
+    order[k] = byw[singles + k];
+    order[nsm + k] = byw[C - 1 - k];
+  }
+  return order;
+}
+
 rcp_status build_tables(rcp_batched_t p) {
   const int C = p->count, N = p->N;
   std::vector<BRowSweep> rowP((size_t)N * 2 * C);
@@ -546,6 +566,20 @@ rcp_status build_tables(rcp_batched_t p) {
         qr.nnorm = (n == 0 && kind != 1) ? t.nsplit[0] * gx : 0;
         qr.st = t.st;
         qrP[((size_t)n * 3 + kind) * C + b] = qr;
+      }
+    }
+    // QR blocks (two CTAs per SM): work I_n l_n (l_n + splits)
+    {
+      std::vector<double> work(C);
+      for (int b = 0; b < C; ++b) {
+        const auto& t = p->t[b];
+        work[b] = (double)t.view[n].I * t.l[n] * (t.l[n] + t.nsplit[n]);
+      }
+      const std::vector<int> order = block_order(work, p->nsm, 2);
+      for (int kind = 0; kind < 3; ++kind) {
+        BQr* row = qrP.data() + ((size_t)n * 3 + kind) * C;
+        std::vector<BQr> tmp(row, row + C);
+        for (int sl = 0; sl < C; ++sl) row[sl] = tmp[order[sl]];
       }
     }
     p->rowItemCnt[n] = (int)rItems.size() - p->rowItemOff[n];
@@ -640,13 +674,22 @@ rcp_status build_tables(rcp_batched_t p) {
         cudaMalloc(&p->cluArgs, host.size()) != cudaSuccess)
       return RCP_ENOMEM;
     size_t smax = 0;
+    // ALS blocks (one CTA per SM): largest core x rank first
+    std::vector<double> work(C);
     for (int b = 0; b < C; ++b) {
+      double w = p->t[b].R;
+      for (int n = 0; n < N; ++n) w *= p->t[b].l[n];
+      work[b] = w;
+    }
+    const std::vector<int> order = block_order(work, p->nsm, 1);
+    for (int sl = 0; sl < C; ++sl) {
+      const int b = order[sl];
       auto& t = p->t[b];
       const size_t sm = cluster_batched_args(
           N, t.R, t.l, rmax, t.buf[(N - 1) % 2], t.At, t.lam_t, p->facdw + (size_t)b * N * 1024,
           t.st, p->cfg[b].seed, p->cfg[b].tol, p->cfg[b].max_iters,
           (const int*)((const char*)(p->alsP + b) + offsetof(PersArgs, user_init)),
-          host.data() + (size_t)b * cluster_args_bytes());
+          host.data() + (size_t)sl * cluster_args_bytes());
       if (sm == 0) return RCP_EINVAL;
       smax = std::max(smax, sm);
     }
