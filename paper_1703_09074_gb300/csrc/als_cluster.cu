@@ -374,9 +374,14 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
                                          int lane) {
   const bool on = lane < R;
   const int cz = on ? lane : 0;  // lanes >= R read a valid column and are zeroed below
+  // The k loops run to the compile-time bound KR with no guard, so that their
+  // shuffles and shared loads issue ahead of the dependent arithmetic (one solving
+  // warp per sub-partition leaves nothing else to hide their latency).  For k >= R
+  // every operand is zero (lanes >= R hold zeros; rows >= R of Z and V are zeroed
+  // at the start), and the sums are unchanged.
   float xa = 0.0f, xb = 0.0f;
-#pragma unroll 4
-  for (int k = 0; k < R; ++k) {
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
     const float mk = __shfl_sync(kFull, m.hi, k);
     if (k & 1) xb = fmaf(mk, Z[k * kGP + cz], xb);
     else xa = fmaf(mk, Z[k * kGP + cz], xa);
@@ -385,8 +390,8 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
 #pragma unroll 1
   for (int step = 0; step < 2; ++step) {
     float s = m.hi, c0 = m.lo, c1 = 0.0f;
-#pragma unroll 4
-    for (int k = 0; k < R; ++k) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
       const float xh = __shfl_sync(kFull, x.hi, k);
       const float xl = __shfl_sync(kFull, x.lo, k);
       const float2 v = Vdw[k * kFP + cz];
@@ -400,8 +405,8 @@ __device__ __forceinline__ dwf solve_row(dwf m, const float* Z, const float2* Vd
     }
     const dwf r = on ? dw_two_sum(s, __fadd_rn(c0, c1)) : dwf{0.0f, 0.0f};  // s may have cancelled below c
     float da = 0.0f, db = 0.0f;
-#pragma unroll 4
-    for (int k = 0; k < R; ++k) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
       const float rk = __shfl_sync(kFull, r.hi, k);
       if (k & 1) db = fmaf(rk, Z[k * kGP + cz], db);
       else da = fmaf(rk, Z[k * kGP + cz], da);
@@ -466,6 +471,9 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   // MTTKRP warps: the nine warps of sub-partitions 1-3
   const int mw = (warp & 3) ? (warp >> 2) * 3 + (warp & 3) - 1 : -1;
 
+  // rows and columns of Z and V at or beyond R stay zero (the row solves run over them)
+  for (int e = tid; e < 32 * kGP; e += kCThreads) Z[e] = 0.0f;
+  for (int e = tid; e < 32 * kFP; e += kCThreads) Vdw[e] = make_float2(0.0f, 0.0f);
   // remote stores below need every CTA of the cluster to be running
   cluster_sync();
 
