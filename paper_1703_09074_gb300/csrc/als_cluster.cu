@@ -278,17 +278,19 @@ template <int KR, int K>
 __device__ __forceinline__ void gj_steps(float (&a)[KR], float (&z)[KR], int R, float floor_,
                                          int lane, bool& ok) {
   if constexpr (K < KR) {
-    if (K < R) {
-      const float piv = __shfl_sync(kFull, a[K], K);
-      ok = ok && piv > floor_;
-      const float rp = fast_rcp(piv);
-      const float f = lane == K ? 1.0f - rp : a[K] * rp;
+    // Steps K >= R (at most 3: KR is R rounded up to a multiple of 4) act on the
+    // identity padding with every multiplier forced to zero: exact no-ops.  Running
+    // them unguarded keeps the steps one straight line, so the shuffles of step K + 1
+    // can issue while step K finishes.
+    const float piv = __shfl_sync(kFull, a[K], K);
+    ok = ok && (K >= R || piv > floor_);
+    const float rp = fast_rcp(piv);
+    const float f = K >= R ? 0.0f : (lane == K ? 1.0f - rp : a[K] * rp);
 #pragma unroll
-      for (int c = K + 1; c < KR; ++c) a[c] = fmaf(-f, __shfl_sync(kFull, a[c], K), a[c]);
+    for (int c = K + 1; c < KR; ++c) a[c] = fmaf(-f, __shfl_sync(kFull, a[c], K), a[c]);
 #pragma unroll
-      for (int c = 0; c <= K; ++c) z[c] = fmaf(-f, __shfl_sync(kFull, z[c], K), z[c]);
-      gj_steps<KR, K + 1>(a, z, R, floor_, lane, ok);
-    }
+    for (int c = 0; c <= K; ++c) z[c] = fmaf(-f, __shfl_sync(kFull, z[c], K), z[c]);
+    gj_steps<KR, K + 1>(a, z, R, floor_, lane, ok);
   }
 }
 
@@ -712,7 +714,11 @@ int pad_strides(const int* l, int N, int* S) {
   return s;
 }
 
-int kr_for(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 24 ? 24 : 32; }
+// Width KR of the register blocks over the rank (every loop over r runs to KR): R
+// rounded up to a multiple of 4 (the float4 loads), at least 8.  The batched kernel
+// keeps buckets of 8, for fewer instantiations.
+int kr_for(int R) { return R <= 8 ? 8 : (R + 3) & ~3; }
+int kr_batched(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 24 ? 24 : 32; }
 
 // Shape-dependent fields of the arguments (widths, cluster size, padded
 // strides, work-item slots) and the dynamic shared memory for KR accumulators.
@@ -796,14 +802,17 @@ cudaError_t launch_als_cluster(rcp_plan_s* p, const float* B, const int* user_in
   a.user_init = p->user_init ? 1 : 0;
   switch (kr_for(p->R)) {
     case 8: return launch_kr<8>(a, smem, s);
+    case 12: return launch_kr<12>(a, smem, s);
     case 16: return launch_kr<16>(a, smem, s);
+    case 20: return launch_kr<20>(a, smem, s);
     case 24: return launch_kr<24>(a, smem, s);
+    case 28: return launch_kr<28>(a, smem, s);
     default: return launch_kr<32>(a, smem, s);
   }
 }
 
 // Arguments of problem b of a batch for k_als_cluster_batched: written into
-// *out (host); returns its shared-memory need for KR = kr_for(rmax), or 0 when
+// *out (host); returns its shared-memory need for KR = kr_batched(rmax), or 0 when
 // the problem is beyond the kernel (some l_n > 32).
 size_t cluster_batched_args(int N, int R, const int* l, int rmax, const float* B,
                             double* const* At, double* lam, float2* facdw, DevState* st,
@@ -812,7 +821,7 @@ size_t cluster_batched_args(int N, int R, const int* l, int rmax, const float* B
   for (int m = 0; m < N; ++m)
     if (l[m] > 32) return 0;
   ClusterArgs a{};
-  const size_t smem = cluster_shape(N, R, l, 1, &a, kr_for(rmax));
+  const size_t smem = cluster_shape(N, R, l, 1, &a, kr_batched(rmax));
   for (int m = 0; m < N; ++m) a.At[m] = At[m];
   a.B = B;
   a.lam = lam;
@@ -832,7 +841,7 @@ size_t cluster_args_bytes() { return sizeof(ClusterArgs); }
 // Shared-memory limit of the batched kernel for this batch (once, at plan time:
 // the launch below may be captured into a graph).
 cudaError_t prepare_als_cluster_batched(int rmax, size_t smem) {
-  const int kr = kr_for(rmax);
+  const int kr = kr_batched(rmax);
   const void* kern = kr == 8 ? (const void*)k_als_cluster_batched<8>
                    : kr == 16 ? (const void*)k_als_cluster_batched<16>
                    : kr == 24 ? (const void*)k_als_cluster_batched<24>
@@ -843,7 +852,7 @@ cudaError_t prepare_als_cluster_batched(int rmax, size_t smem) {
 cudaError_t launch_als_cluster_batched(const void* dev_args, int count, int rmax, size_t smem,
                                        cudaStream_t s) {
   const ClusterArgs* args = (const ClusterArgs*)dev_args;
-  const int kr = kr_for(rmax);
+  const int kr = kr_batched(rmax);
   count_launches(1);
   if (kr == 8) k_als_cluster_batched<8><<<count, kCThreads, smem, s>>>(args);
   else if (kr == 16) k_als_cluster_batched<16><<<count, kCThreads, smem, s>>>(args);
