@@ -431,8 +431,10 @@ __device__ __forceinline__ void gram_f32(const float* F32, float* G32, int m, in
   for (int e = tid; e < nb * nb; e += kCThreads) {
     const int br = e / nb, bc = e - br * nb;
     float s00 = 0.0f, s01 = 0.0f, s10 = 0.0f, s11 = 0.0f;
-#pragma unroll 4
-    for (int i = 0; i < lm; ++i) {
+    // all 32 rows, unguarded: rows >= lm are zero, so the sums are unchanged, and the
+    // loads of later rows issue ahead of the dependent FMAs
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
       const float2 u = *(const float2*)(F + i * KR + 2 * br);
       const float2 v = *(const float2*)(F + i * KR + 2 * bc);
       s00 = fmaf(u.x, v.x, s00);
@@ -498,7 +500,9 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   // ---- initial factors of modes 2..N: the caller's, or the seeded N(0,1)
   // stream drawn row-major (l_m x R), as FP32 copies (entries r >= R zero;
   // mode 1 starts at zero and is computed first)
-  for (int e = tid; e < 32 * KR; e += kCThreads) F32[e] = 0.0f;
+  // (rows i >= l_m of every mode stay zero too: the Gram runs over all 32 rows)
+  for (int e = tid; e < N * 32 * KR; e += kCThreads) F32[e] = 0.0f;
+  __syncthreads();
   const int user_init = a.user_init_dev ? *a.user_init_dev : a.user_init;
   for (int m = 1; m < N; ++m) {
     const int lm = a.l[m];
