@@ -195,19 +195,16 @@ __host__ __device__ inline void mttkrp_items(const int* l, int N, int n, int nro
 // range) are spread over the kMW MTTKRP warps; item t leaves its partial row
 // (lane r: its part of M[i, r]) in slot t of Mpart; the items of row j are the
 // PC S consecutive slots from j PC S.
+// The item shape of mode n for this CTA (mttkrp_items: PC, S; P = the count of
+// multi-indices p; seglen = ceil(l_am / S)) comes precomputed in mi.
 template <int KR>
 __device__ void mttkrp_rows(const ClusterArgs& a, int n, int nrows, int crank, const float* Bs,
-                            const float* F32, float* Mpart, int warp, int lane) {
+                            const float* F32, float* Mpart, int warp, int lane, const int* mi) {
   const int N = a.N, C = a.C;
   const int am = n == 0 ? 1 : 0;  // the inner (first other) mode
   const int la = a.l[am];
-  int P = 1;
-  for (int m = 0; m < N; ++m)
-    if (m != n && m != am) P *= a.l[m];
-  int PC, S;
-  mttkrp_items(a.l, N, n, nrows, &PC, &S);
+  const int PC = mi[0], S = mi[1], P = mi[2], seglen = mi[3];
   const int nitems = nrows * PC * S;
-  const int seglen = (la + S - 1) / S;
   const int sa = a.S[am];
   for (int item = warp; item < nitems; item += kMW) {
     const int j = item / (PC * S);
@@ -309,8 +306,13 @@ __device__ bool gj_warp(float (&a)[KR], float (&z)[KR], int R, float floor_, int
 // solver warp of the next phase 1 starts from it.
 __device__ __forceinline__ void build_V(int N, int R, int n, const float* G32, float2* Vdw,
                                         int tid) {
-  for (int e = tid; e < R * R; e += kCThreads) {
-    const int r = e / R, c = e - r * R;
+  // the Grams are exactly symmetric (gram_f32), so V is: its upper triangle (at most
+  // 528 entries: one or two per thread), each entry stored twice
+  for (int e = tid; e < R * (R + 1) / 2; e += kCThreads) {
+    int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (c * (c + 1) / 2 > e) --c;
+    while ((c + 1) * (c + 2) / 2 <= e) ++c;
+    const int r = e - c * (c + 1) / 2;  // r <= c
     dwf w = {1.0f, 0.0f};
     bool first = true;
     for (int m = 0; m < N; ++m) {
@@ -320,6 +322,7 @@ __device__ __forceinline__ void build_V(int N, int R, int n, const float* G32, f
       first = false;
     }
     st_dw(&Vdw[r * kFP + c], w);
+    if (r != c) st_dw(&Vdw[c * kFP + r], w);
   }
 }
 
@@ -481,6 +484,23 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   // remote stores below need every CTA of the cluster to be running
   cluster_sync();
 
+  // per mode, this CTA's owned rows and MTTKRP item shape (mttkrp_rows), formed once
+  __shared__ int mish[kMaxN][5];  // PC, S, P, seglen, nrows
+  if (tid < N) {
+    const int n = tid, ln = a.l[n];
+    const int nrows = ln > crank ? (ln - crank + C - 1) / C : 0;
+    int PC, S;
+    mttkrp_items(a.l, N, n, nrows, &PC, &S);
+    const int am = n == 0 ? 1 : 0;
+    int P = 1;
+    for (int m = 0; m < N; ++m)
+      if (m != n && m != am) P *= a.l[m];
+    mish[n][0] = PC;
+    mish[n][1] = S;
+    mish[n][2] = P;
+    mish[n][3] = (a.l[am] + S - 1) / S;
+    mish[n][4] = nrows;
+  }
   // ---- the core, into the padded layout; |B|^2 in double word
   int total = 1;
   for (int m = 0; m < N; ++m) total *= a.l[m];
@@ -551,10 +571,10 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
   for (int it = 1; it <= a.max_iters && !done; ++it) {
     for (int n = 0; n < N; ++n) {
       const int ln = a.l[n];
-      const int nrows = ln > crank ? (ln - crank + C - 1) / C : 0;
+      const int nrows = mish[n][4];
       // ---- phase 1: MTTKRP of the owned rows || V and its inverse
       if (mw >= 0) {
-        mttkrp_rows<KR>(a, n, nrows, crank, Bs, F32, Mpart, mw, lane);
+        mttkrp_rows<KR>(a, n, nrows, crank, Bs, F32, Mpart, mw, lane, mish[n]);
       } else if (warp == 0) {
         const int inf = build_and_invert<KR>(a, n, G32, Z, Vdw, lane);
         if (lane == 0) {
@@ -565,9 +585,7 @@ __device__ __forceinline__ void als_cluster_body(const ClusterArgs& a) {
       __syncthreads();
       // ---- phase 2 + 3: warp w solves owned rows w, w + 12, ... and stores them into every CTA
       float2* fd = Fdw + buf * 32 * kFP;
-      int PCn, Sn;
-      mttkrp_items(a.l, N, n, nrows, &PCn, &Sn);
-      const int per_row = PCn * Sn;
+      const int per_row = mish[n][0] * mish[n][1];
       for (int j = warp; j < nrows; j += kWarps) {
         const int i = crank + j * C;
         dwf m = {0.0f, 0.0f};
