@@ -321,6 +321,15 @@ enum rcp_arith_op {
 rcp_status rcp_test_arith(int32_t op, const double* x_dev, const double* y_dev, int64_t n,
                           double* out_hi_dev, double* out_lo_dev, void* cuda_stream);
 
+/* FP64 (fp64 = 1) or FP32 (fp64 = 0) FMA rate of the current device in TFLOP/s
+ * (2 FLOP per FMA): 8 independent FMA chains per thread on 8 (FP64) or 16
+ * (FP32) CTAs of 256 threads per SM, the second of two launches timed with CUDA
+ * events on cuda_stream.  This is the arithmetic peak that the FP64 path's
+ * sweeps are measured against (the paper has no counterpart: it is a
+ * measurement aid).  Synchronises the stream.  Errors: RCP_EINVAL for a null
+ * tflops or fp64 not 0/1; RCP_ECUDA. */
+rcp_status rcp_measure_fma_rate(int32_t fp64, double* tflops, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Batched form: many tensors of uneven shapes decomposed together.  Every
  * step of Algorithm 1 (per mode), Algorithm 2 and the recovery of Eq. (qbs)

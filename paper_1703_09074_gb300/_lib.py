@@ -109,6 +109,8 @@ SIGNATURES = {
     "rcp_sketch_mode1_static": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_uint64, P, P, P]),
+    "rcp_measure_fma_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.c_void_p]),
     "rcp_test_arith": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),

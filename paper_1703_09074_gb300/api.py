@@ -229,6 +229,17 @@ def test_normals(seed, stream, purpose, first, count, device="cuda"):
     return z, w, f
 
 
+def measure_fma_rate(fp64=True, device="cuda"):
+    """The device's FP64 (or FP32) FMA rate in TFLOP/s, from a timed FMA-chain kernel."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    with torch.cuda.device(device):
+        s = torch.cuda.current_stream()
+        check(lib.rcp_measure_fma_rate(1 if fp64 else 0, ctypes.byref(out),
+                                       ctypes.c_void_p(s.cuda_stream)), "rcp_measure_fma_rate")
+    return out.value
+
+
 class BatchedPlan:
     """Many decompositions of uneven shapes run together (one CUDA graph per batch).
 

@@ -126,3 +126,13 @@ def test_fp64_reciprocal_square_root():
         exact = 1 / Decimal(float(x[i])).sqrt()
         worst = max(worst, abs(Decimal(float(hi[i])) - exact) / exact)
     assert worst <= Decimal(2.0 ** -51), worst
+
+
+@pytest.mark.gpu
+def test_fma_rate_measurement():
+    """The FMA-rate kernel behind the FP64 path's roofline peak: positive rates, and
+    FP32 well above FP64 on this part (FP64 issues at a small fraction of FP32)."""
+    from paper_1703_09074_gb300 import measure_fma_rate
+    f64 = measure_fma_rate(fp64=True)
+    f32 = measure_fma_rate(fp64=False)
+    assert f64 > 0.1 and f32 > 10.0 * f64
